@@ -1,0 +1,314 @@
+#!/usr/bin/env python
+"""Throughput of the forest-closeness hot path on GB300.
+
+One step = the whole path on one batch: build G* from the CSR (validation,
+degrees, start order, selector thresholds), sample tau = 1024 uniform spanning
+trees of G* (Algorithm 2, one persistent launch), aggregate the u*-edge and
+control-variate counts, Algorithm 1's pivot solve (CG on I + alpha L, FP32
+inner / FP64 refinement to 1e-9), combination + farness + closeness (Eq. 3,
+Def. 2) and the top-100 ranking.
+
+Workload: Barabasi-Albert n = 2^20, m = 8 (seed clique K_9, seed 2),
+unweighted, alpha = 1, tau = 1024 trees per step (synthetic stand-in for the
+paper's complex networks).  Metric: USTs/s (trees per second, whole job).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) each rank samples its own 1024 trees (tree_offset =
+rank * 1024; no data-path collective, weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_LOG2, BA_M, BA_SEED, ALPHA, TAU, TOPK = 20, 8, 2, 1.0, 1024, 100
+WORKLOAD = f"BA n=2^{N_LOG2} m={BA_M} (seed {BA_SEED}) unweighted, alpha={ALPHA:g}, tau={TAU} trees/step"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tau", type=int, default=TAU)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = max(smax, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_trees_per_s(g, trees_per_core: int = 4):
+    """The oracle's sequential sampler (as it stands), one tree range per host
+    core in parallel threads (ctypes releases the GIL)."""
+    import concurrent.futures as cf
+    from oracle import native
+    native.build()
+    cores = os.cpu_count() or 1
+    total = trees_per_core * cores
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        futs = [ex.submit(native.wilson, g, ALPHA, 7, trees_per_core, c * trees_per_core, 0, None, False,
+                          False, False) for c in range(cores)]
+        for f in futs:
+            f.result()
+    dt = time.perf_counter() - t0
+    return total / dt, cores, total, dt
+
+
+def run_reference(args, g):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import dense
+    trees_per_core = 2
+    vals = []
+    cores = os.cpu_count() or 1
+    for i in range(args.warmup + args.steps):
+        rate, cores, total, dt = cpu_trees_per_s(g, trees_per_core)
+        if i >= args.warmup:
+            vals.append(rate)
+    value = statistics.median(vals)
+    line = {
+        "metric": "USTs/s", "value": value, "unit": "trees/s", "impl": "reference", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * TAU / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n": g.n, "m_edges": g.m, "tau": TAU},
+        "cpu_baseline": {"value": value, "unit": "trees/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{trees_per_core * cores} trees of the workload per step, "
+                                   f"{trees_per_core} per core, sequential Wilson per thread"},
+        "e2e": {"value": value, "unit": "trees/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    import numpy as np
+    import synth
+    g = synth.barabasi_albert(1 << N_LOG2, BA_M, BA_SEED)
+    if args.impl == "reference":
+        run_reference(args, g)
+        return
+
+    import torch
+    from paper_2101_06192_gb300 import fc
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    tau = args.tau
+    n, nnz = g.n, g.nnz
+    rowptr_d = torch.from_numpy(g.rowptr).to(dev)
+    colidx_d = torch.from_numpy(g.colidx).to(dev)
+    rowptr_h = torch.from_numpy(g.rowptr).pin_memory()
+    colidx_h = torch.from_numpy(g.colidx).pin_memory()
+    R = torch.zeros(n, dtype=torch.int32, device=dev)
+    C = torch.zeros(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    tree_offset = rank * tau
+
+    def step(seed, host_inputs=False, samp_ev=None, stats=None):
+        if host_inputs:
+            G = fc.Graph(rowptr_h.numpy(), colidx_h.numpy(), None, [ALPHA])
+        else:
+            G = fc.Graph(rowptr_d, colidx_d, None, [ALPHA])
+        R.zero_()
+        C.zero_()
+        if samp_ev is not None:
+            samp_ev[0].record(stream)
+        G.sample(seed, tau, tree_offset=tree_offset, R=R, C=C)
+        if samp_ev is not None:
+            samp_ev[1].record(stream)
+        if stats is not None:
+            stats.append(G.sampler_stats())
+        x, _ = G.pivot_solve(rel_tol=1e-9)
+        diag, far, clo = G.farness(R, tau, x_pivot=x)
+        top = fc.top_k(diag, TOPK)
+        G.close()
+        if host_inputs:
+            return clo.cpu(), top.cpu()
+        return clo, top
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for i in range(args.warmup):
+        step(1000 + i)
+    torch.cuda.synchronize()
+
+    # ---- device-resident inputs ----
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms, samp_ms, stats = [], [], []
+    launches0 = fc.launch_count()
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sa, sb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(2000 + i, samp_ev=(sa, sb), stats=stats)
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        step_ms.append(a.elapsed_time(b))
+        samp_ms.append(sa.elapsed_time(sb))
+    launches = fc.launch_count() - launches0
+    clk = clocks.stop()
+    R_sum = int(R.sum().item())
+
+    # ---- end to end through the public API with host buffers ----
+    e2e_ms = []
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        step(3000 + i, host_inputs=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+        barrier()
+
+    tot_ms = sum(step_ms)
+    tot_e2e = sum(e2e_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([tot_ms, tot_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms, tot_e2e = float(t[0]), float(t[1])
+    ms_per_step = tot_ms / args.steps
+    value = world * tau * args.steps / (tot_ms / 1000.0)
+    e2e_value = world * tau * args.steps / (tot_e2e / 1000.0)
+
+    # roofline of the dominant kernel (the persistent Wilson sampler)
+    peaks, peak_kind = load_peaks()
+    pops = statistics.mean(s[0] for s in stats)
+    deps = statistics.mean(s[1] for s in stats)
+    alg_bytes = deps * 40 + pops * 20 + tau * n * (16 + 4) + R_sum * 8
+    samp_s = statistics.mean(samp_ms) / 1000.0
+    achieved = alg_bytes / samp_s / 1e9
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_wilson<false>",
+                "peak_source": peak_kind, "kernel_ms": 1000.0 * samp_s,
+                "departures_per_launch": deps, "pops_per_launch": pops}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, total, dt = cpu_trees_per_s(g, trees_per_core=4)
+        cpu = {"value": rate, "unit": "trees/s", "cores": cores, "kind": "oracle",
+               "sample": f"{total} trees of the workload ({dt:.1f} s wall), 4 per host core, "
+                         f"sequential Wilson (Algorithm 2) per thread"}
+
+    if rank == 0:
+        line = {
+            "metric": "USTs/s", "value": value, "unit": "trees/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32/f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "m_edges": g.m, "nnz": nnz, "tau": tau,
+                       "l2": "flushed before every timed step (512 MB write); per-step working set "
+                             f"{tau * n * 16 / 1e9:.1f} GB of tree state > L2",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": "trees/s", "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz,
+                    "d2h_bytes_per_step": 8 * n + 4 * TOPK},
+            "gpu_launches": int(launches),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "sampling_ms_per_step": statistics.mean(samp_ms),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * fc -- forest closeness on GB300 (sm_103a): C ABI.
+ *
+ * Estimates diag(Omega), Omega = (I + alpha L)^{-1}, the forest farness and the
+ * forest closeness of every vertex of a simple undirected graph by sampling
+ * uniform spanning trees of the augmented graph G* with Wilson's algorithm, as
+ * in van der Grinten, Angriman, Predari, Meyerhenke, "New Approximation
+ * Algorithms for Forest Closeness Centrality" (arXiv 2101.06192):
+ *   forest matrix / distance / closeness    Sec. 2, Def. 1, Def. 2
+ *   augmented graph G*, pivot u*            Sec. 4.1, Prop. 2
+ *   estimator and its parameters            Algorithm 1, Prop. 1, Thm. 1 (Sec. 4.2)
+ *   tree sampler                            Algorithm 2 (App. B)
+ *   farness from the diagonal               Eq. 3
+ *
+ * Conventions (all entry points):
+ *   - Graphs are CSR: rowptr int64[n+1], colidx int32[nnz], optional weights
+ *     float32[nnz].  Rows sorted ascending, no self-loops, no duplicates,
+ *     symmetric (with equal weights both ways), weights finite and >= 0
+ *     (Sec. 2: finite simple undirected graphs with non-negative weights).
+ *   - The universal vertex u* has index n.
+ *   - Unless a flag says otherwise every pointer argument is a DEVICE pointer
+ *     owned by the caller; the library never frees caller memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued on it; calls that report device-side errors synchronise the
+ *     stream before returning, as stated per function.
+ *   - No function throws; every failure is a status code.  On failure the
+ *     outputs are unspecified unless stated otherwise.
+ *   - fc_graph is not thread-safe: use one graph per host thread or serialise.
+ */
+#ifndef FC_H_
+#define FC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fc_graph fc_graph;
+
+typedef enum {
+  FC_OK = 0,
+  FC_EINVAL = 1,     /* bad argument or input graph violates the CSR contract */
+  FC_ENOMEM = 2,     /* device or host allocation failed                      */
+  FC_ECUDA = 3,      /* a CUDA runtime call failed                            */
+  FC_ENOCONV = 4,    /* solver hit max_iter before rel_tol (best x written)   */
+  FC_ETIMEOUT = 5,   /* sampler watchdog: iteration budget exhausted          */
+  FC_EOVERFLOW = 6   /* a per-vertex visit counter exceeded 2^24 - 1          */
+} fc_status;
+
+/* flags for fc_build_augmented */
+#define FC_HOST_PTRS 0u   /* rowptr/colidx/w/alphas are host pointers   */
+#define FC_DEVICE_PTRS 1u /* rowptr/colidx/w are device pointers (alphas: host) */
+
+/*
+ * Build G* (Sec. 4.1; first step of Algorithm 1) for n_alpha values of alpha
+ * over one CSR graph G.  Copies the CSR into memory owned by the returned graph
+ * and derives, on the device: degrees, weighted degrees d_w (FP64, summed left
+ * to right per row), the per-row FP64 prefix sums of the weights, the
+ * ascending-degree start order of Algorithm 2 (ties by vertex id), and, per
+ * alpha, the integer selection thresholds of the random-stack selector.
+ * Selector (one stack entry of v with degree d, Philox words o0..o3):
+ *   u53 = (o0 << 21) | (o1 >> 11);  U = u53 * 2^-53;
+ *   unweighted: t = fl(1 + fl(alpha d)); x = fl(U t), clamped to the largest
+ *     double below t; x < 1 selects u*, else neighbour floor(o2 d / 2^32);
+ *   weighted: t_0 = 1, t_j = fl(1 + fl(alpha S_j)) with S_j the FP64 prefix of
+ *     the row's weights; x = fl(U t_d) clamped below t_d; slot = first j with
+ *     x < t_j (slot 0 = u*, slot j = j-th neighbour).
+ * The thresholds are the exact integer boundaries of these FP64 comparisons,
+ * so the walk itself compares integers only.
+ *   n >= 1 and n < 2^30; 0 <= nnz < 2^32; 1 <= n_alpha <= 64;
+ *   alphas[i] finite and > 0 (alphas is always a host pointer);
+ *   w == NULL means unweighted (every edge weight 1).
+ * Validates the CSR contract above on the device; FC_EINVAL if violated.
+ * Synchronises `stream`.  On success *out owns device memory until fc_destroy.
+ */
+fc_status fc_build_augmented(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
+                             const float* w, const double* alphas, int32_t n_alpha, uint32_t flags,
+                             void* stream, fc_graph** out);
+
+/* Graph metadata (host pointers; any may be NULL). */
+fc_status fc_graph_info(const fc_graph* g, int32_t* n, int64_t* nnz, int32_t* n_alpha,
+                        int32_t* weighted);
+
+/*
+ * Sampler launch shape.  walkers_per_tree: concurrent Wilson walkers sharing
+ * one tree (a multiple of 32 in [32, 1024], 0 = automatic); max_trees_resident:
+ * cap on trees in flight (0 = fill the GPU); smem: 0 = automatic, 1 = force
+ * global-memory tree state, 2 = force shared-memory tree state (FC_EINVAL if
+ * it does not fit).  Affects speed only, never results.
+ */
+fc_status fc_set_sampler_shape(fc_graph* g, int32_t walkers_per_tree, int32_t max_trees_resident,
+                               int32_t smem);
+
+/*
+ * Sample tau spanning trees of G* rooted at u* for EVERY alpha of the graph
+ * (Algorithm 1's sampling loop; Algorithm 2 per tree) and aggregate them.
+ * Tree t of alpha index a uses the random stacks
+ *   Philox4x32-10(counter = (k, v, tree_offset + t, a), key = (seed_lo, seed_hi)),
+ * so the trees, and therefore every output, are a pure function of
+ * (graph, alphas, seed, tree index) -- independent of launch shape and of how
+ * trees are split across calls or GPUs.
+ * Outputs (device; NULL skips an optional one):
+ *   R        uint32[n_alpha * n]   R[a*n + v] += #trees containing edge {u*, v}
+ *            (Prop. 1; accumulated, NOT cleared: zero it before the first call)
+ *   C        uint32[n_alpha * n]   C[a*n + v] += #trees whose first stack entry
+ *            of v selects u* (control-variate covariate; accumulated) -- optional
+ *   parents  int32[n_alpha * tau * n] parent of v in tree t of alpha a at
+ *            [(a*tau + t)*n + v], u* = n -- optional (test / analysis mode)
+ *   steps_out uint64[n_alpha * tau] stack entries consumed by each tree
+ *            (= departures of the sequential algorithm) -- optional
+ * max_steps_per_tree: watchdog on the iterations of each walker (0 = default
+ * 8 n + 2^20); exceeding it aborts the launch with FC_ETIMEOUT.
+ * Requires tau >= 0, tree_offset >= 0, tree_offset + tau <= 2^32.
+ * Synchronises `stream` (reads the device error word).
+ */
+fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R,
+                         uint32_t* C, int32_t* parents, uint64_t max_steps_per_tree,
+                         uint64_t* steps_out, void* stream);
+
+/*
+ * Solve (I + alpha_a L) x_j = b_j for n_rhs right-hand sides by Jacobi-
+ * preconditioned CG with FP32 inner iterations and FP64 residual / iterative
+ * refinement (the paper's ground truth uses CG at tolerance 1e-9, Sec. 6.1;
+ * Algorithm 1's pivot solve is a system in the same matrix, see
+ * fc_pivot_solve).  b, x: FP64 [n_rhs * n], column j at offset j*n.  x is
+ * used as the initial guess (zero it for x0 = 0).  Stops when every
+ * ||b_j - A x_j||_2 <= rel_tol ||b_j||_2 (FP64 residual) or after max_iter
+ * total inner iterations (FC_ENOCONV; best x kept).  iters_out (host, may be
+ * NULL) receives the inner iterations used.  Synchronises `stream`.
+ */
+fc_status fc_solve(fc_graph* g, int32_t alpha_idx, const double* b, double* x, int32_t n_rhs,
+                   double rel_tol, int32_t max_iter, int32_t* iters_out, void* stream);
+
+/*
+ * Algorithm 1's pivot solve: x = L*^+ (e_{u*} - 1/(n+1) 1), the mean-zero
+ * solution of L* x = e_{u*} - 1/(n+1) 1 on G*.  Computed as the grounded
+ * system (I + alpha L) y = -1/(n+1) 1 (x(u*) := 0, via fc_solve) followed by
+ * the shift to zero mean.  x: FP64 device [n+1], x[n] = x(u*).
+ * Synchronises `stream`.
+ */
+fc_status fc_pivot_solve(fc_graph* g, int32_t alpha_idx, double* x, double rel_tol, int32_t max_iter,
+                         int32_t* iters_out, void* stream);
+
+/*
+ * Combination, farness and closeness for alpha index a (Algorithm 1's fill
+ * step, Eq. 3, Def. 2), FP64 throughout:
+ *   plain:      d_v = R[v]/tau                                  (Prop. 1)
+ *   with pivot: d_v = R[v]/tau - x(u*) + 2 x(v) + (n+2)/(n+1)^2
+ *               (the fill step yields diag(L*^+) on V; (L*^+)[V,V] =
+ *                Omega - (n+2)/(n+1)^2 J adds the constant back)
+ *   with C and g_pred (control variate, not in the paper):
+ *               d_v -= beta_v (C[v]/tau - p_v),
+ *               beta_v = (1 - clip(g_v, p_v, 1)) / (1 - p_v)
+ *   farness_v = n d_v + sum_w d_w - 2;   closeness_v = n / farness_v.
+ * R, C: the alpha-a slices (n entries each).  C, g_pred (float[n]) and x_pivot
+ * (double[n+1]) may be NULL; C and g_pred must be both set or both NULL.
+ * diag_out/farness_out/closeness_out: FP64 device [n] (farness/closeness may be
+ * NULL).  tau >= 1.  Asynchronous (no sync).
+ */
+fc_status fc_forest_farness(fc_graph* g, int32_t alpha_idx, const uint32_t* R, const uint32_t* C,
+                            const float* g_pred, const double* x_pivot, int64_t tau, double* diag_out,
+                            double* farness_out, double* closeness_out, void* stream);
+
+/*
+ * Exact probability p_v that one stack entry of v selects u* (the selector's
+ * discrete probability, 1/deg*(v) up to 2^-52), FP64 device [n].  Asynchronous.
+ */
+fc_status fc_p_root(fc_graph* g, int32_t alpha_idx, double* p_out, void* stream);
+
+/*
+ * Top-k ranking (Sec. 6.1): the k vertices with the smallest diag values
+ * (= highest forest closeness by Eq. 3), ascending, ties by ascending vertex
+ * id.  diag: FP64 device [n]; idx_out: int32 device [k]; 1 <= k <= n.
+ * Allocates temporary device memory.  Synchronises `stream`.
+ */
+fc_status fc_top_k(const double* diag, int32_t n, int32_t k, int32_t* idx_out, void* stream);
+
+/*
+ * Number of trees of Algorithm 1: ceil(log(2m/delta) / (2 (1-kappa)^2 eps^2)),
+ * natural log (Hoeffding, proof of Thm. 1).  Returns -1 for arguments outside
+ * 0 < eps < 1, 0 < delta < 1, 0 < kappa < 1, m >= 1.
+ */
+int64_t fc_tau_for(double eps, double delta, double kappa, int64_t m);
+
+/*
+ * Diagnostic: out[i] = the vertex selected by stack entry ks[i] of vertex
+ * verts[i] in tree `tree` of alpha index a (same random stacks and selector as
+ * fc_sample_usts; n = u*).  verts: int32 device [count] (each in [0, n)),
+ * ks: uint32 device [count], out: int32 device [count].  Asynchronous.
+ */
+fc_status fc_stack_entries(fc_graph* g, int32_t alpha_idx, uint64_t seed, uint32_t tree, int64_t count,
+                           const int32_t* verts, const uint32_t* ks, int32_t* out, void* stream);
+
+/*
+ * Work counters of the last fc_sample_usts call on g (host pointers, either may
+ * be NULL): stack pops summed over the trees, and departures actually executed
+ * (including walk steps repeated after a walker released its path).
+ * Synchronous.
+ */
+fc_status fc_sampler_stats(fc_graph* g, uint64_t* pops, uint64_t* departures);
+
+/*
+ * Number of CUDA kernels this library has launched in the process so far
+ * (diagnostic: count launches in a region by differencing).
+ */
+uint64_t fc_launch_count(void);
+
+/*
+ * fc_sample_usts keeps its per-tree state in one process-wide device buffer
+ * per GPU, grown on demand and reused by every graph.  This frees those
+ * buffers (synchronises the device).  Graphs stay valid.
+ */
+fc_status fc_release_scratch(void);
+
+/* Release the graph and all device memory it owns (NULL is a no-op). */
+void fc_destroy(fc_graph* g);
+
+/* Static description of a status code. */
+const char* fc_status_str(fc_status s);
+
+/* Detail of the last failure on the calling host thread ("" if none). */
+const char* fc_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FC_H_ */

@@ -1,0 +1,517 @@
+// G* builder (Sec. 4.1; first step of Algorithm 1): CSR validation, degrees,
+// FP64 weight prefixes, ascending-degree start order (Algorithm 2) and the
+// integer thresholds of the random-stack selector.  Also the shared error
+// plumbing and the small graph-management entry points of the C ABI.
+#include <cmath>
+#include <cstdio>
+#include <atomic>
+#include <mutex>
+
+#include "fc_internal.cuh"
+
+namespace fcx {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+struct Scratch {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+static std::mutex g_scratch_mu;
+static Scratch g_scratch[64];
+
+fc_status sampler_scratch(int device, size_t bytes, cudaStream_t st, void** out) {
+  if (device < 0 || device >= 64) return FC_EINVAL;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  Scratch& sc = g_scratch[device];
+  if (sc.bytes < bytes) {
+    if (sc.ptr) {
+      FC_CK(cudaDeviceSynchronize());
+      FC_CK(cudaFree(sc.ptr));
+      sc.ptr = nullptr;
+      sc.bytes = 0;
+    }
+    FC_CK(cudaMalloc(&sc.ptr, bytes));
+    sc.bytes = bytes;
+  }
+  (void)st;
+  *out = sc.ptr;
+  return FC_OK;
+}
+
+static bool g_pool_set[64] = {};
+void retain_pool(int device) {
+  if (device < 0 || device >= 64 || g_pool_set[device]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  g_pool_set[device] = true;
+}
+
+fc_status cuda_fail(cudaError_t e, const char* what) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  set_error(buf);
+  return e == cudaErrorMemoryAllocation ? FC_ENOMEM : FC_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Validation: one warp per row.  Every index is bounds-checked before use, so
+// a malformed CSR sets the error word instead of touching memory out of range.
+// ---------------------------------------------------------------------------
+__global__ void k_validate(int32_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
+                           const int32_t* __restrict__ colidx, const float* __restrict__ w,
+                           uint32_t* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nwarps) {
+    const int64_t b = rowptr[v], e = rowptr[v + 1];
+    bool bad = false;
+    if (v == 0 && b != 0) bad = true;
+    if (v == n - 1 && e != nnz) bad = true;
+    if (b < 0 || e < b || e > nnz) bad = true;
+    if (bad) {
+      if (lane == 0) atomicOr(err, ERR_INVAL);
+      continue;
+    }
+    for (int64_t i = b + lane; i < e; i += 32) {
+      const int32_t c = colidx[i];
+      bool ok = c >= 0 && c < n && c != v;
+      if (ok && i > b && colidx[i - 1] >= c) ok = false;  // sorted, no duplicates
+      float wv = 1.0f;
+      if (ok && w != nullptr) {
+        wv = w[i];
+        if (!(isfinite(wv) && wv >= 0.0f)) ok = false;
+      }
+      if (ok) {  // symmetric: v must appear in row c with the same weight
+        int64_t lo = rowptr[c], hi = rowptr[c + 1];
+        if (lo < 0) lo = 0;
+        if (hi > nnz) hi = nnz;
+        bool found = false;
+        for (int it = 0; it < 64 && lo < hi; ++it) {
+          const int64_t mid = lo + (hi - lo) / 2;
+          const int32_t cm = colidx[mid];
+          if (cm == v) {
+            found = (w == nullptr) || (w[mid] == wv);
+            break;
+          }
+          if (cm < v) lo = mid + 1; else hi = mid;
+        }
+        ok = found;
+      }
+      if (!ok) atomicOr(err, ERR_INVAL);
+    }
+  }
+}
+
+// Degrees, weighted degrees and the per-row prefix of the weights, summed left
+// to right in FP64 (one thread per row keeps the summation order fixed).
+__global__ void k_degrees(int32_t n, const int64_t* __restrict__ rowptr, const float* __restrict__ w,
+                          int32_t* __restrict__ deg, double* __restrict__ dw, double* __restrict__ S,
+                          int32_t* max_deg) {
+  int32_t local_max = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = rowptr[v], e = rowptr[v + 1];
+    const int32_t d = (int32_t)(e - b);
+    deg[v] = d;
+    if (w != nullptr) {
+      double s = 0.0;
+      for (int64_t i = b; i < e; ++i) {
+        s = __dadd_rn(s, (double)w[i]);
+        S[i] = s;
+      }
+      dw[v] = s;
+    } else {
+      dw[v] = (double)d;
+    }
+    local_max = max(local_max, d);
+  }
+  local_max = __reduce_max_sync(0xffffffffu, local_max);
+  if ((threadIdx.x & 31) == 0 && local_max > 0) atomicMax(max_deg, local_max);
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort of (degree, vertex) by degree, 8-bit digits.  One warp
+// per tile of 1024 items, processed as 32 consecutive chunks so that equal
+// digits keep their input (= vertex id) order.
+// ---------------------------------------------------------------------------
+constexpr int RS_TILE = 1024;
+
+__global__ void k_rs_hist(int32_t n, const uint32_t* __restrict__ keys, int shift,
+                          uint32_t* __restrict__ hist, int32_t nblk) {
+  __shared__ uint32_t cnt[256];
+  const int lane = threadIdx.x;
+  for (int d = lane; d < 256; d += 32) cnt[d] = 0;
+  __syncwarp();
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int c = 0; c < RS_TILE / 32; ++c) {
+    const int64_t i = base + c * 32 + lane;
+    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncwarp();
+  for (int d = lane; d < 256; d += 32) hist[(int64_t)d * nblk + blockIdx.x] = cnt[d];
+}
+
+__global__ void k_rs_scatter(int32_t n, const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin,
+                             uint32_t* __restrict__ kout, int32_t* __restrict__ vout, int shift,
+                             const uint32_t* __restrict__ offs, int32_t nblk) {
+  __shared__ uint32_t run[256];
+  const int lane = threadIdx.x;
+  for (int d = lane; d < 256; d += 32) run[d] = offs[(int64_t)d * nblk + blockIdx.x];
+  __syncwarp();
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int c = 0; c < RS_TILE / 32; ++c) {
+    const int64_t i = base + c * 32 + lane;
+    const bool valid = i < n;
+    uint32_t key = 0;
+    int32_t val = 0;
+    uint32_t d = 256u + lane;  // unique dummy digit for padding lanes
+    if (valid) {
+      key = kin[i];
+      val = vin[i];
+      d = (key >> shift) & 255u;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t rank = __popc(peers & lt);
+    if (valid) {
+      const uint32_t pos = run[d] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) run[d] += __popc(peers);
+    __syncwarp();
+  }
+}
+
+// Exclusive scan of uint32 (block of 1024 threads per 1024 items).
+__global__ void k_scan_block(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t len,
+                             uint32_t* __restrict__ sums) {
+  __shared__ uint32_t wsum[32];
+  const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+  const uint32_t x = i < len ? in[i] : 0u;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t s = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+    if (lane >= o) s += y;
+  }
+  if (lane == 31) wsum[wid] = s;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t t = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    wsum[lane] = t;
+  }
+  __syncthreads();
+  const uint32_t incl = s + (wid > 0 ? wsum[wid - 1] : 0u);
+  if (i < len) out[i] = incl - x;
+  if (threadIdx.x == 1023 && sums != nullptr) sums[blockIdx.x] = incl;
+}
+
+__global__ void k_scan_add(uint32_t* __restrict__ out, int64_t len, const uint32_t* __restrict__ add) {
+  const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+  if (i < len) out[i] += add[blockIdx.x];
+}
+
+fc_status exclusive_scan(const uint32_t* in, uint32_t* out, int64_t len, cudaStream_t st) {
+  const int64_t nb = (len + 1023) / 1024;
+  if (nb <= 1) {
+    k_scan_block<<<1, 1024, 0, st>>>(in, out, len, nullptr);
+    FC_LAUNCHED();
+    return FC_OK;
+  }
+  uint32_t *sums = nullptr, *sums_x = nullptr;
+  FC_CK(cudaMallocAsync((void**)&sums, nb * sizeof(uint32_t), st));
+  FC_CK(cudaMallocAsync((void**)&sums_x, nb * sizeof(uint32_t), st));
+  k_scan_block<<<(unsigned)nb, 1024, 0, st>>>(in, out, len, sums);
+  FC_LAUNCHED();
+  fc_status r = exclusive_scan(sums, sums_x, nb, st);
+  if (r == FC_OK) {
+    k_scan_add<<<(unsigned)nb, 1024, 0, st>>>(out, len, sums_x);
+    FC_LAUNCHED();
+  }
+  FC_CK(cudaFreeAsync(sums, st));
+  FC_CK(cudaFreeAsync(sums_x, st));
+  return r;
+}
+
+__global__ void k_iota_keys(int32_t n, const int32_t* __restrict__ deg, uint32_t* __restrict__ keys,
+                            int32_t* __restrict__ vals) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    keys[v] = (uint32_t)deg[v];
+    vals[v] = (int32_t)v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Selector thresholds for one alpha.
+//   T_v = count_below(1, t_v): stack entries selecting u* (slot 0),
+//   B_e = count_below(t_j, t_v) for the entry e of slot j (weighted rows),
+// with t_v = fl(1 + fl(alpha s_v)), s_v = d_v (unweighted) or d_w(v) (weighted).
+// ---------------------------------------------------------------------------
+__global__ void k_thr_vertex(int32_t n, double alpha, bool weighted, const int64_t* __restrict__ rowptr,
+                             const int32_t* __restrict__ deg, const double* __restrict__ dw,
+                             uint4* __restrict__ rowinfo) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t d = deg[v];
+    const double t = deg_star(alpha, weighted ? dw[v] : (double)d);
+    const uint64_t T = count_below(1.0, t);
+    rowinfo[v] = make_uint4((uint32_t)rowptr[v], (uint32_t)d, (uint32_t)T, (uint32_t)(T >> 32));
+  }
+}
+
+__global__ void k_thr_nnz(int32_t n, double alpha, const int64_t* __restrict__ rowptr,
+                          const double* __restrict__ S, const double* __restrict__ dw,
+                          uint64_t* __restrict__ B) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nwarps) {
+    const double t = deg_star(alpha, dw[v]);
+    for (int64_t e = rowptr[v] + lane; e < rowptr[v + 1]; e += 32)
+      B[e] = count_below(deg_star(alpha, S[e]), t);
+  }
+}
+
+static int grid_for(int64_t items, int threads) {
+  int64_t b = (items + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 152 * 64) b = 152 * 64;
+  return (int)b;
+}
+
+static void free_graph_arrays(fc_graph* g, cudaStream_t st) {
+  void* ptrs[] = {g->rowptr, g->colidx, g->w, g->deg, g->dw, g->S, g->order, g->rowinfo, g->B,
+                  g->alphas_d, g->d_err, g->d_counter, g->d_stats};
+  for (void* p : ptrs)
+    if (p) cudaFreeAsync(p, st);
+  if (g->ws) cudaFree(g->ws);
+  if (g->sv) cudaFree(g->sv);
+}
+
+}  // namespace fcx
+
+using namespace fcx;
+
+extern "C" const char* fc_status_str(fc_status s) {
+  switch (s) {
+    case FC_OK: return "ok";
+    case FC_EINVAL: return "invalid argument or input graph";
+    case FC_ENOMEM: return "out of memory";
+    case FC_ECUDA: return "CUDA error";
+    case FC_ENOCONV: return "solver did not converge";
+    case FC_ETIMEOUT: return "sampler watchdog expired";
+    case FC_EOVERFLOW: return "visit counter overflow";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* fc_last_error_message(void) { return g_last_error.c_str(); }
+
+extern "C" uint64_t fc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+extern "C" fc_status fc_release_scratch(void) {
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  for (auto& sc : g_scratch) {
+    if (sc.ptr) {
+      FC_CK(cudaDeviceSynchronize());
+      FC_CK(cudaFree(sc.ptr));
+      sc.ptr = nullptr;
+      sc.bytes = 0;
+    }
+  }
+  return FC_OK;
+}
+
+#define BUILD_CK(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) {                             \
+      fc_status s_ = cuda_fail(e_, #call);               \
+      free_graph_arrays(g, st);                          \
+      delete g;                                          \
+      return s_;                                         \
+    }                                                    \
+  } while (0)
+
+extern "C" fc_status fc_build_augmented(int32_t n, int64_t nnz, const int64_t* rowptr,
+                                        const int32_t* colidx, const float* w, const double* alphas,
+                                        int32_t n_alpha, uint32_t flags, void* stream, fc_graph** out) {
+  if (out == nullptr) return FC_EINVAL;
+  *out = nullptr;
+  if (n < 1 || n >= (1 << 30) || nnz < 0 || nnz >= (int64_t(1) << 32) || n_alpha < 1 || n_alpha > 64 ||
+      rowptr == nullptr || (nnz > 0 && colidx == nullptr) || alphas == nullptr ||
+      (flags != FC_HOST_PTRS && flags != FC_DEVICE_PTRS)) {
+    set_error("fc_build_augmented: argument out of range");
+    return FC_EINVAL;
+  }
+  for (int i = 0; i < n_alpha; ++i) {
+    if (!(std::isfinite(alphas[i]) && alphas[i] > 0.0)) {
+      set_error("fc_build_augmented: alpha must be finite and > 0");
+      return FC_EINVAL;
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  fc_graph* g = new fc_graph();
+  g->n = n;
+  g->nnz = nnz;
+  g->n_alpha = n_alpha;
+  g->weighted = (w != nullptr);
+  g->alphas.assign(alphas, alphas + n_alpha);
+  BUILD_CK(cudaGetDevice(&g->device));
+  retain_pool(g->device);
+  const size_t nz = (size_t)(nnz > 0 ? nnz : 1);
+  BUILD_CK(cudaMallocAsync((void**)&g->rowptr, (n + 1) * sizeof(int64_t), st));
+  BUILD_CK(cudaMallocAsync((void**)&g->colidx, nz * sizeof(int32_t), st));
+  if (g->weighted) {
+    BUILD_CK(cudaMallocAsync((void**)&g->w, nz * sizeof(float), st));
+    BUILD_CK(cudaMallocAsync((void**)&g->S, nz * sizeof(double), st));
+    BUILD_CK(cudaMallocAsync((void**)&g->B, nz * n_alpha * sizeof(uint64_t), st));
+  }
+  BUILD_CK(cudaMallocAsync((void**)&g->deg, n * sizeof(int32_t), st));
+  BUILD_CK(cudaMallocAsync((void**)&g->dw, n * sizeof(double), st));
+  BUILD_CK(cudaMallocAsync((void**)&g->order, n * sizeof(int32_t), st));
+  BUILD_CK(cudaMallocAsync((void**)&g->rowinfo, (size_t)n * n_alpha * sizeof(uint4), st));
+  BUILD_CK(cudaMallocAsync((void**)&g->alphas_d, n_alpha * sizeof(double), st));
+  BUILD_CK(cudaMallocAsync((void**)&g->d_err, 4 * sizeof(uint32_t), st));
+  BUILD_CK(cudaMallocAsync((void**)&g->d_counter, 2 * sizeof(unsigned long long), st));
+  BUILD_CK(cudaMallocAsync((void**)&g->d_stats, 4 * sizeof(unsigned long long), st));
+
+  const cudaMemcpyKind kind = flags == FC_DEVICE_PTRS ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  BUILD_CK(cudaMemcpyAsync(g->rowptr, rowptr, (n + 1) * sizeof(int64_t), kind, st));
+  if (nnz > 0) BUILD_CK(cudaMemcpyAsync(g->colidx, colidx, nnz * sizeof(int32_t), kind, st));
+  if (g->weighted && nnz > 0) BUILD_CK(cudaMemcpyAsync(g->w, w, nnz * sizeof(float), kind, st));
+  BUILD_CK(cudaMemcpyAsync(g->alphas_d, alphas, n_alpha * sizeof(double), cudaMemcpyHostToDevice, st));
+  BUILD_CK(cudaMemsetAsync(g->d_err, 0, 4 * sizeof(uint32_t), st));
+
+  k_validate<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(n, nnz, g->rowptr, g->colidx, g->w, g->d_err);
+  BUILD_CK((fcx::note_launch(), cudaGetLastError()));
+  uint32_t hs[4] = {0, 0, 0, 0};
+  BUILD_CK(cudaMemcpyAsync(hs, g->d_err, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  BUILD_CK(cudaStreamSynchronize(st));
+  if (hs[0] != 0) {
+    set_error("fc_build_augmented: CSR violates the input contract (range, sorted rows, no self-loops/"
+              "duplicates, symmetry, finite non-negative weights)");
+    free_graph_arrays(g, st);
+    cudaStreamSynchronize(st);
+    delete g;
+    return FC_EINVAL;
+  }
+  // rowptr is now known to be in range and monotone
+  k_degrees<<<grid_for(n, 256), 256, 0, st>>>(n, g->rowptr, g->w, g->deg, g->dw, g->S,
+                                              (int32_t*)(g->d_err + 1));
+  BUILD_CK((fcx::note_launch(), cudaGetLastError()));
+  BUILD_CK(cudaMemcpyAsync(hs, g->d_err, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  BUILD_CK(cudaStreamSynchronize(st));
+  g->max_deg = (int32_t)hs[1];
+  BUILD_CK(cudaMemsetAsync(g->d_err, 0, 4 * sizeof(uint32_t), st));
+
+  // ascending-degree order, ties by id (stable LSD radix sort)
+  {
+    const int32_t nblk = (int32_t)((n + RS_TILE - 1) / RS_TILE);
+    uint32_t *k0 = nullptr, *k1 = nullptr, *hist = nullptr, *offs = nullptr;
+    int32_t* v1 = nullptr;
+    BUILD_CK(cudaMallocAsync((void**)&k0, n * sizeof(uint32_t), st));
+    BUILD_CK(cudaMallocAsync((void**)&k1, n * sizeof(uint32_t), st));
+    BUILD_CK(cudaMallocAsync((void**)&v1, n * sizeof(int32_t), st));
+    BUILD_CK(cudaMallocAsync((void**)&hist, (size_t)256 * nblk * sizeof(uint32_t), st));
+    BUILD_CK(cudaMallocAsync((void**)&offs, (size_t)256 * nblk * sizeof(uint32_t), st));
+    k_iota_keys<<<grid_for(n, 256), 256, 0, st>>>(n, g->deg, k0, g->order);
+    BUILD_CK((fcx::note_launch(), cudaGetLastError()));
+    int passes = 1;
+    while (passes < 4 && (uint32_t)g->max_deg >> (8 * passes)) ++passes;
+    uint32_t* kin = k0;
+    uint32_t* kout = k1;
+    int32_t* vin = g->order;
+    int32_t* vout = v1;
+    for (int p = 0; p < passes; ++p) {
+      k_rs_hist<<<nblk, 32, 0, st>>>(n, kin, 8 * p, hist, nblk);
+      BUILD_CK((fcx::note_launch(), cudaGetLastError()));
+      fc_status r = exclusive_scan(hist, offs, (int64_t)256 * nblk, st);
+      if (r != FC_OK) {
+        free_graph_arrays(g, st);
+        delete g;
+        return r;
+      }
+      k_rs_scatter<<<nblk, 32, 0, st>>>(n, kin, vin, kout, vout, 8 * p, offs, nblk);
+      BUILD_CK((fcx::note_launch(), cudaGetLastError()));
+      std::swap(kin, kout);
+      std::swap(vin, vout);
+    }
+    if (vin != g->order)
+      BUILD_CK(cudaMemcpyAsync(g->order, vin, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    BUILD_CK(cudaFreeAsync(k0, st));
+    BUILD_CK(cudaFreeAsync(k1, st));
+    BUILD_CK(cudaFreeAsync(v1, st));
+    BUILD_CK(cudaFreeAsync(hist, st));
+    BUILD_CK(cudaFreeAsync(offs, st));
+  }
+
+  for (int a = 0; a < n_alpha; ++a) {
+    k_thr_vertex<<<grid_for(n, 256), 256, 0, st>>>(n, g->alphas[a], g->weighted, g->rowptr, g->deg,
+                                                   g->dw, g->rowinfo + (size_t)a * n);
+    BUILD_CK((fcx::note_launch(), cudaGetLastError()));
+    if (g->weighted && nnz > 0) {
+      k_thr_nnz<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(n, g->alphas[a], g->rowptr, g->S, g->dw,
+                                                                g->B + (size_t)a * nnz);
+      BUILD_CK((fcx::note_launch(), cudaGetLastError()));
+    }
+  }
+  BUILD_CK(cudaStreamSynchronize(st));
+  *out = g;
+  return FC_OK;
+}
+
+extern "C" fc_status fc_graph_info(const fc_graph* g, int32_t* n, int64_t* nnz, int32_t* n_alpha,
+                                   int32_t* weighted) {
+  if (g == nullptr) return FC_EINVAL;
+  if (n) *n = g->n;
+  if (nnz) *nnz = g->nnz;
+  if (n_alpha) *n_alpha = g->n_alpha;
+  if (weighted) *weighted = g->weighted ? 1 : 0;
+  return FC_OK;
+}
+
+extern "C" fc_status fc_set_sampler_shape(fc_graph* g, int32_t walkers_per_tree, int32_t max_trees_resident,
+                                          int32_t smem) {
+  if (g == nullptr || walkers_per_tree < 0 || walkers_per_tree > 1024 || (walkers_per_tree % 32) != 0 ||
+      max_trees_resident < 0 || smem < 0 || smem > 2)
+    return FC_EINVAL;
+  g->walkers = walkers_per_tree;
+  g->max_trees = max_trees_resident;
+  g->smem_mode = smem;
+  return FC_OK;
+}
+
+extern "C" void fc_destroy(fc_graph* g) {
+  if (g == nullptr) return;
+  cudaStream_t st = 0;
+  cudaDeviceSynchronize();
+  free_graph_arrays(g, st);
+  cudaStreamSynchronize(st);
+  delete g;
+}
+
+extern "C" int64_t fc_tau_for(double eps, double delta, double kappa, int64_t m) {
+  if (!(eps > 0 && eps < 1 && delta > 0 && delta < 1 && kappa > 0 && kappa < 1 && m >= 1)) return -1;
+  const double e = (1.0 - kappa) * eps;
+  return (int64_t)std::ceil(std::log(2.0 * (double)m / delta) / (2.0 * e * e));
+}

@@ -1,0 +1,394 @@
+// Linear solves in A = I + alpha L (the matrix of the grounded pivot system of
+// Algorithm 1, and of the CG ground truth of Sec. 6.1).
+//
+// Mixed precision: the outer loop is iterative refinement in FP64
+// (r = b - A x with FP64 x and FP64 arithmetic, x += correction); the
+// correction solves A d = r / ||r|| with Jacobi-preconditioned CG in FP32.
+// Several right-hand sides run side by side (column j of an [m][n] block),
+// each with its own CG scalars; reductions are two-pass and fixed-order, so
+// results do not depend on scheduling.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "fc_internal.cuh"
+
+namespace fcx {
+
+constexpr int SV_T = 256;
+
+// ---- FP64 residual r = b - A x, partial sums of r.r and b.b ---------------
+__global__ void k_resid64(int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                          const float* __restrict__ w, const double* __restrict__ dw, double alpha,
+                          const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ r,
+                          double* __restrict__ prr, double* __restrict__ pbb, int nb) {
+  __shared__ double s1[SV_T], s2[SV_T];
+  const int j = blockIdx.y;
+  const int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x;
+  const size_t off = (size_t)j * n;
+  double rr = 0.0, bb = 0.0;
+  if (v < n) {
+    double acc = 0.0;
+    for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+      const double we = w ? (double)w[e] : 1.0;
+      acc += we * x[off + colidx[e]];
+    }
+    const double ax = x[off + v] * (1.0 + alpha * dw[v]) - alpha * acc;
+    const double rv = b[off + v] - ax;
+    r[off + v] = rv;
+    rr = rv * rv;
+    bb = b[off + v] * b[off + v];
+  }
+  s1[threadIdx.x] = rr;
+  s2[threadIdx.x] = bb;
+  __syncthreads();
+  for (int s = SV_T / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      s1[threadIdx.x] += s1[threadIdx.x + s];
+      s2[threadIdx.x] += s2[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    prr[(size_t)j * nb + blockIdx.x] = s1[0];
+    pbb[(size_t)j * nb + blockIdx.x] = s2[0];
+  }
+}
+
+// per-column fixed-order sum of nb partials: out[j] = sum_i part[j][i]
+__global__ void k_colsum(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  __shared__ double red[SV_T];
+  const int j = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += SV_T) s += part[(size_t)j * nb + i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = SV_T / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = red[0];
+}
+
+// ---- FP32 inner PCG ---------------------------------------------------------
+struct Inner {
+  float* r;   // residual of the correction system
+  float* p;
+  float* q;
+  float* d;   // correction
+  double* scal;  // per column: [0] rz, [1] pq, [2] rz_new, [3] rr, [4] scale, [5] active
+};
+
+// r32 = r64 * inv_scale; d = 0; p = z = r32 / diag; partial r.z and r.r
+__global__ void k_inner_init(int32_t n, const double* __restrict__ r64, const float* __restrict__ diag32,
+                             const double* __restrict__ scal, Inner in, double* __restrict__ prz,
+                             double* __restrict__ prr, int nb) {
+  __shared__ double s1[SV_T], s2[SV_T];
+  const int j = blockIdx.y;
+  const int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x;
+  const size_t off = (size_t)j * n;
+  double rz = 0.0, rr = 0.0;
+  if (v < n) {
+    const double sc = scal[j * 8 + 4];
+    const float rv = (float)(r64[off + v] * sc);
+    const float z = rv / diag32[v];
+    in.r[off + v] = rv;
+    in.p[off + v] = z;
+    in.d[off + v] = 0.0f;
+    rz = (double)rv * (double)z;
+    rr = (double)rv * (double)rv;
+  }
+  s1[threadIdx.x] = rz;
+  s2[threadIdx.x] = rr;
+  __syncthreads();
+  for (int s = SV_T / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      s1[threadIdx.x] += s1[threadIdx.x + s];
+      s2[threadIdx.x] += s2[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    prz[(size_t)j * nb + blockIdx.x] = s1[0];
+    prr[(size_t)j * nb + blockIdx.x] = s2[0];
+  }
+}
+
+// q = A p (FP32), partial p.q
+__global__ void k_spmv_pq(int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                          const float* __restrict__ w, const float* __restrict__ diag32, float alpha, Inner in,
+                          double* __restrict__ ppq, int nb) {
+  __shared__ double s1[SV_T];
+  const int j = blockIdx.y;
+  const int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x;
+  const size_t off = (size_t)j * n;
+  double pq = 0.0;
+  if (v < n) {
+    float acc = 0.0f;
+    const float* pj = in.p + off;
+    for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) acc += (w ? w[e] : 1.0f) * pj[colidx[e]];
+    const float pv = pj[v];
+    const float qv = pv * diag32[v] - alpha * acc;
+    in.q[off + v] = qv;
+    pq = (double)pv * (double)qv;
+  }
+  s1[threadIdx.x] = pq;
+  __syncthreads();
+  for (int s = SV_T / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) s1[threadIdx.x] += s1[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ppq[(size_t)j * nb + blockIdx.x] = s1[0];
+}
+
+// d += a p; r -= a q; partial r.z, r.r with z = r / diag
+__global__ void k_inner_update(int32_t n, const float* __restrict__ diag32, const double* __restrict__ scal,
+                               Inner in, double* __restrict__ prz, double* __restrict__ prr, int nb) {
+  __shared__ double s1[SV_T], s2[SV_T];
+  const int j = blockIdx.y;
+  const int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x;
+  const size_t off = (size_t)j * n;
+  double rz = 0.0, rr = 0.0;
+  if (v < n) {
+    const double* sc = scal + j * 8;
+    const float a = (sc[5] != 0.0 && sc[1] != 0.0) ? (float)(sc[0] / sc[1]) : 0.0f;
+    in.d[off + v] += a * in.p[off + v];
+    const float rv = in.r[off + v] - a * in.q[off + v];
+    in.r[off + v] = rv;
+    const float z = rv / diag32[v];
+    rz = (double)rv * (double)z;
+    rr = (double)rv * (double)rv;
+  }
+  s1[threadIdx.x] = rz;
+  s2[threadIdx.x] = rr;
+  __syncthreads();
+  for (int s = SV_T / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      s1[threadIdx.x] += s1[threadIdx.x + s];
+      s2[threadIdx.x] += s2[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    prz[(size_t)j * nb + blockIdx.x] = s1[0];
+    prr[(size_t)j * nb + blockIdx.x] = s2[0];
+  }
+}
+
+// p = z + beta p with beta = rz_new / rz
+__global__ void k_inner_p(int32_t n, const float* __restrict__ diag32, const double* __restrict__ scal, Inner in) {
+  const int j = blockIdx.y;
+  const int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x;
+  if (v >= n) return;
+  const size_t off = (size_t)j * n;
+  const double* sc = scal + j * 8;
+  const float beta = sc[0] != 0.0 ? (float)(sc[2] / sc[0]) : 0.0f;
+  in.p[off + v] = in.r[off + v] / diag32[v] + beta * in.p[off + v];
+}
+
+// scalar bookkeeping after k_inner_update: rz <- rz_new (done after k_inner_p
+// has used both), rr stored
+__global__ void k_scal_shift(int m, double* scal) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < m) scal[j * 8 + 0] = scal[j * 8 + 2];
+}
+
+// x += (1/scale) d (FP64), only for active columns
+__global__ void k_correct(int32_t n, const double* __restrict__ scal, const float* __restrict__ d,
+                          double* __restrict__ x) {
+  const int j = blockIdx.y;
+  const int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x;
+  if (v >= n) return;
+  const double* sc = scal + j * 8;
+  if (sc[5] == 0.0) return;
+  const size_t off = (size_t)j * n;
+  x[off + v] += (double)d[off + v] / sc[4];
+}
+
+__global__ void k_diag32(int32_t n, const double* __restrict__ dw, double alpha, float* __restrict__ diag32) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) diag32[v] = (float)(1.0 + alpha * dw[v]);
+}
+
+__global__ void k_fill(int64_t len, double val, double* __restrict__ a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < len) a[i] = val;
+}
+
+// x over V' (n+1 entries, x[n] = x(u*) = 0 on entry) -> mean-zero gauge
+__global__ void k_shift(int64_t len, const double* __restrict__ sum, double* __restrict__ x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < len) x[i] -= *sum / (double)len;
+}
+
+__global__ void k_partial_sum(int64_t len, const double* __restrict__ a, double* __restrict__ part) {
+  __shared__ double red[SV_T];
+  const int64_t i = (int64_t)blockIdx.x * SV_T + threadIdx.x;
+  red[threadIdx.x] = i < len ? a[i] : 0.0;
+  __syncthreads();
+  for (int s = SV_T / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+}  // namespace fcx
+
+using namespace fcx;
+
+extern "C" fc_status fc_solve(fc_graph* g, int32_t alpha_idx, const double* b, double* x, int32_t n_rhs,
+                              double rel_tol, int32_t max_iter, int32_t* iters_out, void* stream) {
+  if (g == nullptr || b == nullptr || x == nullptr || n_rhs < 1 || n_rhs > 65535 || alpha_idx < 0 ||
+      alpha_idx >= g->n_alpha || !(rel_tol > 0.0) || max_iter < 1) {
+    set_error("fc_solve: bad argument");
+    return FC_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int32_t n = g->n;
+  const int m = n_rhs;
+  const double alpha = g->alphas[alpha_idx];
+  const int nb = (n + SV_T - 1) / SV_T;
+  const size_t nm = (size_t)n * m;
+  // scratch: FP64 r64, FP32 r/p/q/d, diag32, partials, scalars
+  double* r64 = nullptr;
+  float* f32 = nullptr;
+  double* part = nullptr;
+  double* scal = nullptr;
+  FC_CK(cudaMallocAsync((void**)&r64, nm * sizeof(double), st));
+  FC_CK(cudaMallocAsync((void**)&f32, (4 * nm + n) * sizeof(float), st));
+  FC_CK(cudaMallocAsync((void**)&part, (size_t)2 * m * nb * sizeof(double) + 4 * m * sizeof(double), st));
+  FC_CK(cudaMallocAsync((void**)&scal, (size_t)8 * m * sizeof(double), st));
+  Inner in;
+  in.r = f32;
+  in.p = f32 + nm;
+  in.q = f32 + 2 * nm;
+  in.d = f32 + 3 * nm;
+  in.scal = scal;
+  float* diag32 = f32 + 4 * nm;
+  double* pA = part;
+  double* pB = part + (size_t)m * nb;
+  double* sums = part + (size_t)2 * m * nb;  // [0..m): rr, [m..2m): bb
+  k_diag32<<<(n + 255) / 256, 256, 0, st>>>(n, g->dw, alpha, diag32);
+  FC_LAUNCHED();
+  const dim3 grid(nb, m);
+  const double inner_tol = 1e-4;
+  const int check_every = 8;
+  std::vector<double> h_rr(m), h_bb(m), h_scal((size_t)8 * m, 0.0), h_in(m);
+  int used = 0;
+  fc_status result = FC_ENOCONV;
+  for (int outer = 0; outer < 64; ++outer) {
+    k_resid64<<<grid, SV_T, 0, st>>>(n, g->rowptr, g->colidx, g->w, g->dw, alpha, b, x, r64, pA, pB, nb);
+    FC_LAUNCHED();
+    k_colsum<<<m, SV_T, 0, st>>>(pA, nb, sums);
+    fcx::note_launch();
+    k_colsum<<<m, SV_T, 0, st>>>(pB, nb, sums + m);
+    fcx::note_launch();
+    FC_CK(cudaMemcpyAsync(h_rr.data(), sums, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    FC_CK(cudaMemcpyAsync(h_bb.data(), sums + m, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    FC_CK(cudaStreamSynchronize(st));
+    bool all_ok = true;
+    for (int j = 0; j < m; ++j) {
+      const double rn = std::sqrt(h_rr[j]), bn = std::sqrt(h_bb[j]);
+      const bool ok = rn <= rel_tol * bn || rn == 0.0;
+      h_scal[(size_t)j * 8 + 5] = ok ? 0.0 : 1.0;
+      h_scal[(size_t)j * 8 + 4] = rn > 0.0 ? 1.0 / rn : 1.0;
+      all_ok = all_ok && ok;
+    }
+    if (all_ok) {
+      result = FC_OK;
+      break;
+    }
+    if (used >= max_iter) break;
+    FC_CK(cudaMemcpyAsync(scal, h_scal.data(), (size_t)8 * m * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_inner_init<<<grid, SV_T, 0, st>>>(n, r64, diag32, scal, in, pA, pB, nb);
+    FC_LAUNCHED();
+    k_colsum<<<m, SV_T, 0, st>>>(pA, nb, sums);
+    fcx::note_launch();
+    k_colsum<<<m, SV_T, 0, st>>>(pB, nb, sums + m);
+    fcx::note_launch();
+    FC_CK(cudaMemcpyAsync(h_in.data(), sums, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    FC_CK(cudaMemcpyAsync(h_rr.data(), sums + m, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    FC_CK(cudaStreamSynchronize(st));
+    std::vector<double> rr0(h_rr);
+    for (int j = 0; j < m; ++j) h_scal[(size_t)j * 8 + 0] = h_in[j];
+    FC_CK(cudaMemcpyAsync(scal, h_scal.data(), (size_t)8 * m * sizeof(double), cudaMemcpyHostToDevice, st));
+    int it = 0;
+    while (used < max_iter) {
+      k_spmv_pq<<<grid, SV_T, 0, st>>>(n, g->rowptr, g->colidx, g->w, diag32, (float)alpha, in, pA, nb);
+      FC_LAUNCHED();
+      // pq -> scal[j*8+1]
+      k_colsum<<<m, SV_T, 0, st>>>(pA, nb, sums);
+      fcx::note_launch();
+      FC_CK(cudaMemcpy2DAsync(scal + 1, 8 * sizeof(double), sums, sizeof(double), sizeof(double), m,
+                              cudaMemcpyDeviceToDevice, st));
+      k_inner_update<<<grid, SV_T, 0, st>>>(n, diag32, scal, in, pA, pB, nb);
+      FC_LAUNCHED();
+      k_colsum<<<m, SV_T, 0, st>>>(pA, nb, sums);
+      fcx::note_launch();
+      k_colsum<<<m, SV_T, 0, st>>>(pB, nb, sums + m);
+      fcx::note_launch();
+      FC_CK(cudaMemcpy2DAsync(scal + 2, 8 * sizeof(double), sums, sizeof(double), sizeof(double), m,
+                              cudaMemcpyDeviceToDevice, st));
+      FC_CK(cudaMemcpy2DAsync(scal + 3, 8 * sizeof(double), sums + m, sizeof(double), sizeof(double), m,
+                              cudaMemcpyDeviceToDevice, st));
+      k_inner_p<<<grid, SV_T, 0, st>>>(n, diag32, scal, in);
+      FC_LAUNCHED();
+      k_scal_shift<<<(m + 127) / 128, 128, 0, st>>>(m, scal);
+      fcx::note_launch();
+      ++used;
+      ++it;
+      if (it % check_every == 0) {
+        FC_CK(cudaMemcpyAsync(h_rr.data(), sums + m, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+        FC_CK(cudaStreamSynchronize(st));
+        bool conv = true;
+        for (int j = 0; j < m; ++j)
+          if (h_scal[(size_t)j * 8 + 5] != 0.0 && std::sqrt(h_rr[j]) > inner_tol * std::sqrt(rr0[j])) conv = false;
+        if (conv) break;
+      }
+    }
+    k_correct<<<grid, SV_T, 0, st>>>(n, scal, in.d, x);
+    FC_LAUNCHED();
+  }
+  FC_CK(cudaFreeAsync(r64, st));
+  FC_CK(cudaFreeAsync(f32, st));
+  FC_CK(cudaFreeAsync(part, st));
+  FC_CK(cudaFreeAsync(scal, st));
+  FC_CK(cudaStreamSynchronize(st));
+  if (iters_out) *iters_out = used;
+  if (result != FC_OK) set_error("fc_solve: max_iter reached before rel_tol");
+  return result;
+}
+
+extern "C" fc_status fc_pivot_solve(fc_graph* g, int32_t alpha_idx, double* x, double rel_tol, int32_t max_iter,
+                                    int32_t* iters_out, void* stream) {
+  if (g == nullptr || x == nullptr || alpha_idx < 0 || alpha_idx >= g->n_alpha) {
+    set_error("fc_pivot_solve: bad argument");
+    return FC_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int32_t n = g->n;
+  double* rhs = nullptr;
+  double* part = nullptr;
+  const int64_t n1 = (int64_t)n + 1;
+  const int nb = (int)((n1 + SV_T - 1) / SV_T);
+  FC_CK(cudaMallocAsync((void**)&rhs, (size_t)n * sizeof(double), st));
+  FC_CK(cudaMallocAsync((void**)&part, (size_t)(nb + 1) * sizeof(double), st));
+  // grounded system: x(u*) = 0, (I + alpha L) x_V = -1/(n+1) 1
+  k_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, -1.0 / (double)n1, rhs);
+  FC_LAUNCHED();
+  FC_CK(cudaMemsetAsync(x, 0, (size_t)n1 * sizeof(double), st));
+  const fc_status s = fc_solve(g, alpha_idx, rhs, x, 1, rel_tol, max_iter, iters_out, stream);
+  if (s != FC_OK && s != FC_ENOCONV) return s;
+  // shift to the mean-zero gauge of L*^+
+  k_partial_sum<<<nb, SV_T, 0, st>>>(n1, x, part);
+  fcx::note_launch();
+  k_colsum<<<1, SV_T, 0, st>>>(part, nb, part + nb);
+  fcx::note_launch();
+  k_shift<<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(n1, part + nb, x);
+  FC_LAUNCHED();
+  FC_CK(cudaFreeAsync(rhs, st));
+  FC_CK(cudaFreeAsync(part, st));
+  FC_CK(cudaStreamSynchronize(st));
+  return s;
+}

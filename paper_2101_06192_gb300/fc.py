@@ -1,0 +1,250 @@
+"""Thin ctypes binding of libfc.so (include/fc.h).  Argument marshalling only:
+every step of the computation runs in the library's CUDA kernels.  PyTorch is
+used for device memory and the current CUDA stream.
+
+Raises FcError on any non-OK status.  There is no CPU path: if the library
+cannot be built or loaded, importing the handle fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_lib = None
+
+FC_OK, FC_EINVAL, FC_ENOMEM, FC_ECUDA, FC_ENOCONV, FC_ETIMEOUT, FC_EOVERFLOW = range(7)
+FC_HOST_PTRS, FC_DEVICE_PTRS = 0, 1
+
+
+class FcError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status} ({detail})")
+        self.status = status
+
+
+def lib():
+    """Load (building first if stale) the in-tree libfc.so."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P, I32, I64, U32, U64, D = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                   ctypes.c_uint64, ctypes.c_double)
+        sig = {
+            "fc_build_augmented": ([I32, I64, P, P, P, P, I32, U32, P, ctypes.POINTER(P)], ctypes.c_int),
+            "fc_graph_info": ([P, P, P, P, P], ctypes.c_int),
+            "fc_set_sampler_shape": ([P, I32, I32, I32], ctypes.c_int),
+            "fc_sample_usts": ([P, U64, I64, I64, P, P, P, U64, P, P], ctypes.c_int),
+            "fc_sampler_stats": ([P, P, P], ctypes.c_int),
+            "fc_stack_entries": ([P, I32, U64, U32, I64, P, P, P, P], ctypes.c_int),
+            "fc_solve": ([P, I32, P, P, I32, D, I32, P, P], ctypes.c_int),
+            "fc_pivot_solve": ([P, I32, P, D, I32, P, P], ctypes.c_int),
+            "fc_forest_farness": ([P, I32, P, P, P, P, I64, P, P, P, P], ctypes.c_int),
+            "fc_p_root": ([P, I32, P, P], ctypes.c_int),
+            "fc_top_k": ([P, I32, I32, P, P], ctypes.c_int),
+            "fc_tau_for": ([D, D, D, I64], I64),
+            "fc_destroy": ([P], None),
+            "fc_status_str": ([ctypes.c_int], ctypes.c_char_p),
+            "fc_last_error_message": ([], ctypes.c_char_p),
+            "fc_launch_count": ([], ctypes.c_uint64),
+            "fc_release_scratch": ([], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != FC_OK:
+        L = lib()
+        detail = L.fc_last_error_message().decode() or L.fc_status_str(status).decode()
+        raise FcError(status, where, detail)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_tensor(t, dtype, n, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()
+            and t.numel() >= n):
+        raise ValueError(f"{name}: expected a contiguous CUDA {dtype} tensor with >= {n} elements")
+    return t
+
+
+class Graph:
+    """G* over one CSR graph for one or more alphas (fc_build_augmented)."""
+
+    def __init__(self, rowptr, colidx, w=None, alphas=(1.0,), stream=None):
+        L = lib()
+        alphas = np.ascontiguousarray(np.atleast_1d(np.asarray(alphas, dtype=np.float64)))
+        on_dev = isinstance(rowptr, torch.Tensor) and rowptr.is_cuda
+        if on_dev:
+            rp = rowptr.to(torch.int64).contiguous()
+            ci = colidx.to(torch.int32).contiguous()
+            ww = None if w is None else w.to(torch.float32).contiguous()
+            flags = FC_DEVICE_PTRS
+        else:
+            rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+            ci = np.ascontiguousarray(colidx, dtype=np.int32)
+            ww = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+            flags = FC_HOST_PTRS
+        n = int(rp.shape[0]) - 1
+        nnz = int(ci.shape[0])
+        h = ctypes.c_void_p()
+        _check(L.fc_build_augmented(n, nnz, _ptr(rp), _ptr(ci), _ptr(ww), _ptr(alphas), int(alphas.size),
+                                    flags, _stream(stream), ctypes.byref(h)), "fc_build_augmented")
+        self._h = h
+        self.n = n
+        self.nnz = nnz
+        self.alphas = alphas.copy()
+        self.n_alpha = int(alphas.size)
+        self.weighted = w is not None
+
+    @classmethod
+    def from_csr(cls, g, alphas=(1.0,), stream=None):
+        """From any object with rowptr/colidx/w numpy arrays (host copy path)."""
+        return cls(g.rowptr, g.colidx, g.w, alphas, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fc_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_shape(self, walkers_per_tree: int = 0, max_trees_resident: int = 0, smem: int = 0):
+        _check(lib().fc_set_sampler_shape(self._h, walkers_per_tree, max_trees_resident, smem),
+               "fc_set_sampler_shape")
+
+    def sample(self, seed: int, tau: int, tree_offset: int = 0, R=None, C=None, with_C: bool = True,
+               want_parents: bool = False, want_steps: bool = False, max_steps_per_tree: int = 0,
+               stream=None):
+        """fc_sample_usts.  R/C accumulate (allocated zeroed when not given)."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        na, n = self.n_alpha, self.n
+        if R is None:
+            R = torch.zeros(na * n, dtype=torch.int32, device=dev)
+        _dev_tensor(R, torch.int32, na * n, "R")
+        if C is None and with_C:
+            C = torch.zeros(na * n, dtype=torch.int32, device=dev)
+        if C is not None:
+            _dev_tensor(C, torch.int32, na * n, "C")
+        parents = torch.empty(na * tau * n, dtype=torch.int32, device=dev) if want_parents else None
+        steps = torch.zeros(na * tau, dtype=torch.int64, device=dev) if want_steps else None
+        _check(lib().fc_sample_usts(self._h, int(seed) & (2**64 - 1), int(tau), int(tree_offset), _ptr(R),
+                                    _ptr(C), _ptr(parents), int(max_steps_per_tree), _ptr(steps),
+                                    _stream(stream)), "fc_sample_usts")
+        out = {"R": R, "C": C}
+        if want_parents:
+            out["parents"] = parents.view(na, tau, n)
+        if want_steps:
+            out["steps"] = steps.view(na, tau)
+        return out
+
+    def stack_entries(self, seed: int, tree: int, verts, ks, alpha_idx: int = 0, stream=None):
+        """fc_stack_entries (diagnostic): vertex chosen by stack entry ks[i] of verts[i]."""
+        verts = verts.to(torch.int32).contiguous()
+        ks = ks.to(torch.int32).contiguous()
+        out = torch.empty_like(verts)
+        _check(lib().fc_stack_entries(self._h, alpha_idx, int(seed) & (2**64 - 1), int(tree), verts.numel(),
+                                      _ptr(verts), _ptr(ks), _ptr(out), _stream(stream)), "fc_stack_entries")
+        return out
+
+    def sampler_stats(self):
+        pops = ctypes.c_uint64()
+        deps = ctypes.c_uint64()
+        _check(lib().fc_sampler_stats(self._h, ctypes.byref(pops), ctypes.byref(deps)), "fc_sampler_stats")
+        return int(pops.value), int(deps.value)
+
+    def solve(self, b, alpha_idx: int = 0, x=None, rel_tol: float = 1e-9, max_iter: int = 20000,
+              stream=None):
+        """fc_solve for b of shape [n] or [m, n] (FP64, CUDA).  Returns (x, iters)."""
+        b2 = b.reshape(-1, self.n).contiguous()
+        m = b2.shape[0]
+        _dev_tensor(b2, torch.float64, m * self.n, "b")
+        if x is None:
+            x = torch.zeros_like(b2)
+        _dev_tensor(x, torch.float64, m * self.n, "x")
+        it = ctypes.c_int32()
+        _check(lib().fc_solve(self._h, alpha_idx, _ptr(b2), _ptr(x), m, float(rel_tol), int(max_iter),
+                              ctypes.byref(it), _stream(stream)), "fc_solve")
+        return x.reshape(b.shape), int(it.value)
+
+    def pivot_solve(self, alpha_idx: int = 0, rel_tol: float = 1e-9, max_iter: int = 20000, stream=None):
+        """Algorithm 1's pivot solve, x of length n+1 (x[n] = x(u*))."""
+        x = torch.empty(self.n + 1, dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))
+        it = ctypes.c_int32()
+        _check(lib().fc_pivot_solve(self._h, alpha_idx, _ptr(x), float(rel_tol), int(max_iter), ctypes.byref(it),
+                                    _stream(stream)), "fc_pivot_solve")
+        return x, int(it.value)
+
+    def farness(self, R, tau: int, alpha_idx: int = 0, C=None, g_pred=None, x_pivot=None, stream=None):
+        """fc_forest_farness on the alpha slices of R (and C).  Returns diag, farness, closeness."""
+        n = self.n
+        dev = torch.device("cuda", torch.cuda.current_device())
+        Ra = R.view(-1)[alpha_idx * n:(alpha_idx + 1) * n] if R.numel() > n else R
+        Ca = None
+        if C is not None:
+            Ca = C.view(-1)[alpha_idx * n:(alpha_idx + 1) * n] if C.numel() > n else C
+        diag = torch.empty(n, dtype=torch.float64, device=dev)
+        far = torch.empty(n, dtype=torch.float64, device=dev)
+        clo = torch.empty(n, dtype=torch.float64, device=dev)
+        if g_pred is not None:
+            _dev_tensor(g_pred, torch.float32, n, "g_pred")
+        _check(lib().fc_forest_farness(self._h, alpha_idx, _ptr(Ra), _ptr(Ca), _ptr(g_pred), _ptr(x_pivot),
+                                       int(tau), _ptr(diag), _ptr(far), _ptr(clo), _stream(stream)),
+               "fc_forest_farness")
+        return diag, far, clo
+
+    def p_root(self, alpha_idx: int = 0, stream=None):
+        p = torch.empty(self.n, dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))
+        _check(lib().fc_p_root(self._h, alpha_idx, _ptr(p), _stream(stream)), "fc_p_root")
+        return p
+
+
+def top_k(diag, k: int, stream=None):
+    _dev_tensor(diag, torch.float64, diag.numel(), "diag")
+    out = torch.empty(k, dtype=torch.int32, device=diag.device)
+    _check(lib().fc_top_k(_ptr(diag), int(diag.numel()), int(k), _ptr(out), _stream(stream)), "fc_top_k")
+    return out
+
+
+def launch_count() -> int:
+    """Kernel launches made by libfc.so in this process so far."""
+    return int(lib().fc_launch_count())
+
+
+def tau_for(eps: float, delta: float, kappa: float, m: int) -> int:
+    return int(lib().fc_tau_for(float(eps), float(delta), float(kappa), int(m)))
+
+
+def declared_symbols():
+    """Entry points declared in include/fc.h (parsed from the header)."""
+    import re
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fc.h")
+    txt = open(hdr).read()
+    return sorted(set(re.findall(r"\b(fc_[a-z0-9_]+)\s*\(", txt)))

@@ -1,0 +1,288 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bars: bit-exact for trees, counts and step counters (integer work, identical
+random stacks); 1e-9 relative for FP64 per-vertex values computed from identical
+counts; the paper's absolute eps for the estimate against dense inversion.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import cg as ocg
+from oracle import cv as ocv
+from oracle import dense, native
+
+pytestmark = pytest.mark.gpu
+
+fc = pytest.importorskip("paper_2101_06192_gb300.fc")
+
+
+def _np32(t):
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+def _oracle_trees(g, alphas, seed, tau, tree_offset=0):
+    outs = []
+    for a, al in enumerate(alphas):
+        outs.append(native.wilson(g, al, seed=seed, tau=tau, tree_offset=tree_offset, alpha_idx=a,
+                                  want_parents=True))
+    return outs
+
+
+def _check_trees(G, g, alphas, seed, tau, tree_offset=0):
+    out = G.sample(seed, tau, tree_offset=tree_offset, want_parents=True, want_steps=True)
+    torch.cuda.synchronize()
+    ref = _oracle_trees(g, alphas, seed, tau, tree_offset)
+    n = g.n
+    R = _np32(out["R"]).reshape(len(alphas), n)
+    C = _np32(out["C"]).reshape(len(alphas), n)
+    par = out["parents"].cpu().numpy()
+    steps = out["steps"].cpu().numpy()
+    for a in range(len(alphas)):
+        np.testing.assert_array_equal(par[a], ref[a]["parents"], err_msg=f"parents alpha {a}")
+        np.testing.assert_array_equal(R[a], ref[a]["R"], err_msg=f"R alpha {a}")
+        np.testing.assert_array_equal(C[a], ref[a]["C"], err_msg=f"C alpha {a}")
+        np.testing.assert_array_equal(steps[a].astype(np.uint64), ref[a]["steps"], err_msg=f"steps alpha {a}")
+    return out, ref
+
+
+@pytest.mark.parametrize("weighted,alphas", [(False, [1.0]), (False, [0.3, 4.0]), (True, [0.1, 1.0, 10.0])])
+def test_stack_entries_bit_exact(weighted, alphas):
+    g = synth.barabasi_albert(500, 4, 3, weighted=weighted)
+    G = fc.Graph.from_csr(g, alphas)
+    rng = np.random.default_rng(0)
+    K = 20000
+    verts = rng.integers(0, g.n, K).astype(np.int32)
+    ks = rng.integers(0, 50, K).astype(np.uint32)
+    for a, al in enumerate(alphas):
+        for tree in (0, 7, 123456):
+            got = G.stack_entries(99, tree, torch.from_numpy(verts).cuda(),
+                                  torch.from_numpy(ks.view(np.int32)).cuda(), alpha_idx=a).cpu().numpy()
+            ref = native.stack_entries(g, al, 99, tree, verts, ks, alpha_idx=a)
+            np.testing.assert_array_equal(got, ref)
+    G.close()
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_p_root_bit_exact(weighted):
+    g = synth.perturbed_grid(20, 15, 4, weighted=weighted)
+    for alpha in (0.1, 1.0, 7.3):
+        G = fc.Graph.from_csr(g, [alpha])
+        got = G.p_root().cpu().numpy()
+        np.testing.assert_array_equal(got, ocv.p_root(g, alpha))
+        G.close()
+
+
+@pytest.mark.parametrize("walkers,smem", [(0, 0), (32, 2), (64, 1), (256, 1), (1024, 2)])
+def test_trees_bit_exact_er1000(walkers, smem):
+    """Small configuration: ER G(1000, avg deg 8), alpha = 1, tau = 2000, every
+    launch shape gives the oracle's trees."""
+    g = synth.erdos_renyi(1000, 8, 1)
+    G = fc.Graph.from_csr(g, [1.0])
+    G.set_shape(walkers, 0, smem)
+    tau = 2000 if walkers in (0, 64) else 300
+    _check_trees(G, g, [1.0], seed=2021, tau=tau)
+    G.close()
+
+
+def test_trees_bit_exact_weighted_grid_three_alphas():
+    g = synth.perturbed_grid(48, 40, 3)
+    alphas = [0.1, 1.0, 10.0]
+    G = fc.Graph.from_csr(g, alphas)
+    for walkers, smem in ((0, 0), (128, 1)):
+        G.set_shape(walkers, 0, smem)
+        _check_trees(G, g, alphas, seed=7, tau=40)
+    G.close()
+
+
+@pytest.mark.parametrize("name", ["single", "empty", "star", "K8", "path", "two_parts", "isolated_mix"])
+def test_trees_edge_cases(name):
+    if name == "single":
+        g = synth.empty(1)
+    elif name == "empty":
+        g = synth.empty(37)
+    elif name == "star":
+        g = synth.star(300)
+    elif name == "K8":
+        g = synth.complete(8, weight=2.5)
+    elif name == "path":
+        g = synth.path(500)
+    elif name == "two_parts":
+        g = synth.from_edges(6, [0, 1, 3, 4], [1, 2, 4, 5], [1.0, 2.0, 0.5, 3.0])
+    else:
+        base = synth.barabasi_albert(400, 2, 9)
+        u, v, _ = base.edges()
+        g = synth.from_edges(1000, u, v)  # vertices 400..999 isolated
+    alphas = [0.5, 2.0]
+    G = fc.Graph.from_csr(g, alphas)
+    for walkers, smem in ((32, 2), (64, 1)):
+        G.set_shape(walkers, 0, smem)
+        out, ref = _check_trees(G, g, alphas, seed=11, tau=50)
+    iso = g.degrees() == 0
+    R = _np32(out["R"]).reshape(2, g.n)
+    assert np.all(R[:, iso] == 50)
+    G.close()
+
+
+def test_tree_offset_split_equals_single_call():
+    """Trees are indexed globally (resume / sharding identity)."""
+    g = synth.barabasi_albert(3000, 3, 5)
+    G = fc.Graph.from_csr(g, [1.0])
+    full = G.sample(5, 96)
+    R = torch.zeros_like(full["R"])
+    C = torch.zeros_like(full["C"])
+    G.sample(5, 40, tree_offset=0, R=R, C=C)
+    G.sample(5, 56, tree_offset=40, R=R, C=C)
+    assert torch.equal(R, full["R"]) and torch.equal(C, full["C"])
+    G.close()
+
+
+def test_ba_full_size_trees_bit_exact():
+    """BA n = 2^20, m = 8, alpha = 1 in the default (benchmark) launch shape:
+    the first trees of the run are the oracle's, bit for bit."""
+    g = synth.barabasi_albert(1 << 20, 8, 2)
+    G = fc.Graph.from_csr(g, [1.0])
+    _check_trees(G, g, [1.0], seed=12345, tau=3)
+    # trees deep into the run (offset) as well
+    _check_trees(G, g, [1.0], seed=12345, tau=1, tree_offset=1000)
+    G.close()
+
+
+def test_grid_full_size_trees_bit_exact():
+    """2048 x 2048 road-like grid, weights U[1, 10], alpha in {0.1, 1, 10}."""
+    g = synth.perturbed_grid(2048, 2048, 3)
+    alphas = [0.1, 1.0, 10.0]
+    G = fc.Graph.from_csr(g, alphas)
+    _check_trees(G, g, alphas, seed=3, tau=1)
+    G.close()
+
+
+def test_farness_and_closeness_vs_oracle_and_dense():
+    g = synth.erdos_renyi(1000, 8, 1)
+    tau = 2000
+    G = fc.Graph.from_csr(g, [1.0])
+    out = G.sample(2021, tau)
+    diag, far, clo = G.farness(out["R"], tau)
+    ref = native.wilson(g, 1.0, seed=2021, tau=tau)
+    d_or = dense.diag_from_counts(ref["R"], tau)
+    np.testing.assert_allclose(diag.cpu().numpy(), d_or, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(far.cpu().numpy(), dense.farness_eq3(d_or), rtol=1e-9)
+    np.testing.assert_allclose(clo.cpu().numpy(), dense.closeness(dense.farness_eq3(d_or)), rtol=1e-9)
+    # against the exact target (Thm. 1 with eps = 0.1)
+    om = np.diag(dense.forest_matrix(g, 1.0))
+    assert np.max(np.abs(diag.cpu().numpy() - om)) <= 0.1
+    # the paper's fill step with the pivot solve reproduces R/tau
+    x, _ = G.pivot_solve()
+    diag2, _, _ = G.farness(out["R"], tau, x_pivot=x)
+    np.testing.assert_allclose(diag2.cpu().numpy(), d_or, rtol=0, atol=1e-9)
+    G.close()
+
+
+def test_control_variate_combination_vs_oracle():
+    g = synth.barabasi_albert(2000, 2, 8)
+    tau = 500
+    G = fc.Graph.from_csr(g, [1.0])
+    out = G.sample(77, tau)
+    gp = np.random.default_rng(1).random(g.n).astype(np.float32)
+    diag, _, _ = G.farness(out["R"], tau, C=out["C"], g_pred=torch.from_numpy(gp).cuda())
+    p = ocv.p_root(g, 1.0)
+    ref = native.wilson(g, 1.0, seed=77, tau=tau)
+    exp = ocv.combine(ref["R"], ref["C"], tau, p, ocv.beta_from_prediction(gp.astype(np.float64), p))
+    np.testing.assert_allclose(diag.cpu().numpy(), exp, rtol=1e-9, atol=1e-12)
+    G.close()
+
+
+@pytest.mark.parametrize("kind,alpha", [("ba", 1.0), ("grid", 10.0), ("grid", 0.1)])
+def test_solve_vs_oracle(kind, alpha):
+    if kind == "ba":
+        g = synth.barabasi_albert(3000, 4, 6, weighted=True)
+    else:
+        g = synth.perturbed_grid(50, 40, 2)
+    G = fc.Graph.from_csr(g, [alpha])
+    vs = np.array([0, 17, g.n // 2, g.n - 1])
+    B = np.zeros((vs.size, g.n))
+    B[np.arange(vs.size), vs] = 1.0
+    X, iters = G.solve(torch.from_numpy(B).cuda(), rel_tol=1e-10)
+    ref = ocg.omega_columns(g, alpha, vs).T
+    np.testing.assert_allclose(X.cpu().numpy(), ref, atol=1e-9 * np.abs(ref).max())
+    A = ocg.system_matrix(g, alpha)
+    res = B.T - A @ X.cpu().numpy().T
+    assert np.all(np.linalg.norm(res, axis=0) <= 1e-10 * np.linalg.norm(B.T, axis=0) * 1.01)
+    G.close()
+
+
+def test_pivot_solve_closed_form():
+    g = synth.barabasi_albert(5000, 3, 4, weighted=True)
+    G = fc.Graph.from_csr(g, [2.0])
+    x, _ = G.pivot_solve(rel_tol=1e-12)
+    x = x.cpu().numpy()
+    n = g.n
+    np.testing.assert_allclose(x[:n] - x[n], -1.0 / (n + 1), atol=1e-12)
+    assert abs(x.sum()) < 1e-9
+    G.close()
+
+
+def test_top_k_matches_oracle_with_ties():
+    g = synth.erdos_renyi(1000, 8, 1)
+    G = fc.Graph.from_csr(g, [1.0])
+    tau = 64  # coarse counts: many exact ties
+    out = G.sample(1, tau)
+    diag, _, _ = G.farness(out["R"], tau)
+    d = diag.cpu().numpy()
+    for k in (1, 10, 500, 1000):
+        np.testing.assert_array_equal(fc.top_k(diag, k).cpu().numpy(), dense.top_k(d, k))
+    dd = torch.tensor([-1.0, 2.0, -3.5, -0.0, 0.0, 2.0, float("inf"), float("nan")], dtype=torch.float64,
+                      device="cuda")
+    assert fc.top_k(dd, 8).cpu().tolist() == [2, 0, 3, 4, 1, 5, 6, 7]
+    np.testing.assert_array_equal(fc.top_k(dd, 8).cpu().numpy(), dense.top_k(dd.cpu().numpy(), 8))
+    G.close()
+
+
+@pytest.mark.parametrize("bad", ["unsorted", "self_loop", "asym", "neg_w", "nan_w", "col_range", "rowptr"])
+def test_invalid_csr_rejected(bad):
+    g = synth.random_small(8, 0.6, 1, weighted=True)
+    rp, ci, w = g.rowptr.copy(), g.colidx.copy(), g.w.copy()
+    if bad == "unsorted":
+        v = int(np.argmax(np.diff(rp) >= 2))
+        a = rp[v]
+        ci[a], ci[a + 1] = ci[a + 1], ci[a]
+    elif bad == "self_loop":
+        ci[rp[2]] = 2
+    elif bad == "asym":
+        w[0] = w[0] + 1.0
+    elif bad == "neg_w":
+        w[3] = -1.0
+    elif bad == "nan_w":
+        w[3] = np.nan
+    elif bad == "col_range":
+        ci[-1] = 8
+    else:
+        rp[3] = rp[-1] + 10
+    with pytest.raises(fc.FcError) as e:
+        fc.Graph(rp, ci, w, [1.0])
+    assert e.value.status == fc.FC_EINVAL
+    # the device is still usable
+    G = fc.Graph.from_csr(g, [1.0])
+    G.sample(1, 4)
+    G.close()
+
+
+def test_bad_alpha_rejected():
+    g = synth.path(5)
+    for al in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(fc.FcError):
+            fc.Graph.from_csr(g, [al])
+
+
+def test_watchdog_returns_timeout_and_device_recovers():
+    g = synth.barabasi_albert(20000, 4, 1)
+    G = fc.Graph.from_csr(g, [1.0])
+    G.set_shape(64, 0, 1)
+    with pytest.raises(fc.FcError) as e:
+        G.sample(3, 8, max_steps_per_tree=5)
+    assert e.value.status == fc.FC_ETIMEOUT
+    out = G.sample(3, 8, want_steps=True)
+    ref = native.wilson(g, 1.0, seed=3, tau=8)
+    np.testing.assert_array_equal(_np32(out["R"]), ref["R"])
+    G.close()
