@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tau", type=int, default=TAU)
+    ap.add_argument("--n-log2", type=int, default=N_LOG2,
+                    help="BA size 2^k (profiling cases only; the benchmark is 2^20)")
+    ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
@@ -167,7 +170,7 @@ def main():
     rank, world, local = dist_env()
     import numpy as np
     import synth
-    g = synth.barabasi_albert(1 << N_LOG2, BA_M, BA_SEED)
+    g = synth.barabasi_albert(1 << args.n_log2, BA_M, BA_SEED)
     if args.impl == "reference":
         run_reference(args, g)
         return
@@ -246,7 +249,7 @@ def main():
 
     # ---- end to end through the public API with host buffers ----
     e2e_ms = []
-    for i in range(args.steps):
+    for i in range(0 if args.no_e2e else args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         barrier()
@@ -257,7 +260,7 @@ def main():
         barrier()
 
     tot_ms = sum(step_ms)
-    tot_e2e = sum(e2e_ms)
+    tot_e2e = sum(e2e_ms) if e2e_ms else float("nan")
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([tot_ms, tot_e2e], dtype=torch.float64, device=dev)
@@ -292,7 +295,8 @@ def main():
             "metric": "USTs/s", "value": value, "unit": "trees/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32/f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "m_edges": g.m, "nnz": nnz, "tau": tau,
+            "config": {"workload": WORKLOAD if args.n_log2 == N_LOG2 and tau == TAU else
+                       f"BA n=2^{args.n_log2} m={BA_M}, alpha={ALPHA:g}, tau={tau} (profiling case)", "n": n, "m_edges": g.m, "nnz": nnz, "tau": tau,
                        "l2": "flushed before every timed step (512 MB write); per-step working set "
                              f"{tau * n * 16 / 1e9:.1f} GB of tree state > L2",
                        "parallelism": f"replicas x{world}"},
