@@ -163,6 +163,32 @@ fc_status fc_forest_farness(fc_graph* g, int32_t alpha_idx, const uint32_t* R, c
                             double* farness_out, double* closeness_out, void* stream);
 
 /*
+ * fc_forest_farness for callers that must not allocate device memory -- for
+ * example code that runs while a CUDA graph is being captured, or under a
+ * memory manager that forbids allocations behind its back.  Same arguments,
+ * layouts and results as fc_forest_farness; the only difference is where the
+ * temporary per-block sums live: fc_forest_farness takes them from the
+ * stream-ordered pool, this entry point uses a fixed device array compiled
+ * into the library (128 KiB, held on every GPU that loads the library until
+ * the process exits).  It calls no cudaMalloc/cudaFree or other allocating
+ * routine.  The paper has no counterpart: this is an engineering variant.
+ *   - n must be <= 4194304 (2^22); larger graphs get FC_EINVAL.
+ *   - The graph's device must be the current device.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any
+ *     stream capture begins.
+ *   - All calls share the one array: calls whose work overlaps on the GPU
+ *     (different streams, or several host threads) race and give wrong
+ *     results.  Serialise them (one stream, or events).
+ *   - The array needs no clearing: each call writes every entry it reads.
+ * Asynchronous (no sync).
+ */
+fc_status fc_forest_farness_noalloc(fc_graph* g, int32_t alpha_idx, const uint32_t* R, const uint32_t* C,
+                                    const float* g_pred, const double* x_pivot, int64_t tau,
+                                    double* diag_out, double* farness_out, double* closeness_out,
+                                    void* stream);
+
+/*
  * Exact probability p_v that one stack entry of v selects u* (the selector's
  * discrete probability, 1/deg*(v) up to 2^-52), FP64 device [n].  Asynchronous.
  */

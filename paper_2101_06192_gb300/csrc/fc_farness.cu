@@ -2,6 +2,7 @@
 // (Eq. 3), forest closeness (Def. 2), exact u*-selection probabilities, and
 // the top-k ranking (Sec. 6.1).
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "fc_internal.cuh"
@@ -232,5 +233,77 @@ extern "C" fc_status fc_top_k(const double* diag, int32_t n, int32_t k, int32_t*
   FC_CK(cudaFreeAsync(hist, st));
   FC_CK(cudaFreeAsync(offs, st));
   FC_CK(cudaStreamSynchronize(st));
+  return FC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of fc_forest_farness.  The per-block partial sums
+// and the trace live in a file-scope device array instead of stream-ordered
+// pool memory.  Host code must not pass the array's name to a kernel (on the
+// host it is only a stand-in symbol), so its device address is looked up once
+// per device with cudaGetSymbolAddress and cached.
+// ---------------------------------------------------------------------------
+namespace fcx {
+constexpr int32_t NOALLOC_MAX_N = 1 << 22;
+constexpr int64_t NOALLOC_MAX_BLOCKS = (NOALLOC_MAX_N + RED_THREADS - 1) / RED_THREADS;
+static __device__ __align__(256) double g_noalloc_partials[NOALLOC_MAX_BLOCKS + 1];
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[64] = {};
+
+static fc_status noalloc_scratch(int device, double** out) {
+  if (device < 0 || device >= 64) {
+    set_error("fc_forest_farness_noalloc: device index out of range");
+    return FC_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (g_noalloc_ptr[device] == nullptr) {
+    void* p = nullptr;
+    FC_CK(cudaGetSymbolAddress(&p, g_noalloc_partials));
+    g_noalloc_ptr[device] = (double*)p;
+  }
+  *out = g_noalloc_ptr[device];
+  return FC_OK;
+}
+}  // namespace fcx
+
+extern "C" fc_status fc_forest_farness_noalloc(fc_graph* g, int32_t alpha_idx, const uint32_t* R,
+                                               const uint32_t* C, const float* g_pred, const double* x_pivot,
+                                               int64_t tau, double* diag_out, double* farness_out,
+                                               double* closeness_out, void* stream) {
+  if (g == nullptr || R == nullptr || diag_out == nullptr || tau < 1 || alpha_idx < 0 ||
+      alpha_idx >= g->n_alpha || ((C == nullptr) != (g_pred == nullptr))) {
+    set_error("fc_forest_farness_noalloc: bad argument");
+    return FC_EINVAL;
+  }
+  if (g->n > NOALLOC_MAX_N) {
+    set_error("fc_forest_farness_noalloc: n exceeds the fixed scratch capacity of 4194304 vertices; "
+              "use fc_forest_farness");
+    return FC_EINVAL;
+  }
+  int dev = -1;
+  FC_CK(cudaGetDevice(&dev));
+  if (dev != g->device) {
+    set_error("fc_forest_farness_noalloc: the graph's device is not the current device");
+    return FC_EINVAL;
+  }
+  double* partial = nullptr;
+  const fc_status s = noalloc_scratch(dev, &partial);
+  if (s != FC_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int32_t n = g->n;
+  const int64_t nb = (n + RED_THREADS - 1) / RED_THREADS;
+  const uint4* rinfo = g->rowinfo + (size_t)alpha_idx * n;
+  // k_combine writes partial[0, nb) and k_sum_partials writes partial[nb]
+  // before anything reads them, so no clearing is needed between calls.
+  k_combine<<<(unsigned)nb, RED_THREADS, 0, st>>>(n, R, C, g_pred, rinfo, x_pivot, 1.0 / (double)tau, diag_out,
+                                                  partial);
+  FC_LAUNCHED();
+  k_sum_partials<<<1, 1024, 0, st>>>(partial, nb, partial + nb);
+  FC_LAUNCHED();
+  if (farness_out || closeness_out) {
+    k_farness<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, diag_out, partial + nb, farness_out, closeness_out);
+    FC_LAUNCHED();
+  }
   return FC_OK;
 }

@@ -45,6 +45,7 @@ def lib():
             "fc_solve": ([P, I32, P, P, I32, D, I32, P, P], ctypes.c_int),
             "fc_pivot_solve": ([P, I32, P, D, I32, P, P], ctypes.c_int),
             "fc_forest_farness": ([P, I32, P, P, P, P, I64, P, P, P, P], ctypes.c_int),
+            "fc_forest_farness_noalloc": ([P, I32, P, P, P, P, I64, P, P, P, P], ctypes.c_int),
             "fc_p_root": ([P, I32, P, P], ctypes.c_int),
             "fc_top_k": ([P, I32, I32, P, P], ctypes.c_int),
             "fc_tau_for": ([D, D, D, I64], I64),
