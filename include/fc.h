@@ -87,10 +87,34 @@ fc_status fc_graph_info(const fc_graph* g, int32_t* n, int64_t* nnz, int32_t* n_
  * one tree (a multiple of 32 in [32, 1024], 0 = automatic); max_trees_resident:
  * cap on trees in flight (0 = fill the GPU); smem: 0 = automatic, 1 = force
  * global-memory tree state, 2 = force shared-memory tree state (FC_EINVAL if
- * it does not fit).  Affects speed only, never results.
+ * it does not fit); regs: register cap of the kernel variant (32, 40 or 64;
+ * 0 = automatic).  Affects speed only, never results.
  */
 fc_status fc_set_sampler_shape(fc_graph* g, int32_t walkers_per_tree, int32_t max_trees_resident,
-                               int32_t smem);
+                               int32_t smem, int32_t regs);
+
+/*
+ * Order in which the sampler's walkers take start vertices: 0 = ascending
+ * degree (Algorithm 2's order, the default), 1 = descending degree.  The trees
+ * do not depend on it (cycle popping); only the amount of waiting between
+ * concurrent walkers does.
+ */
+fc_status fc_set_start_order(fc_graph* g, int32_t descending);
+
+/*
+ * Diagnostic per-iteration counters of the last fc_sample_usts on g, summed
+ * over walkers and trees: [0] walker iterations, [1] claims at stack entry 0,
+ * [2] tree hits, [3] tree-hit confirmations, [4] conflict waits, [5] waits
+ * after a release, [6] releases, [7] pop steps, [8] tops computed at entry
+ * k > 0, [9] idle-lane iterations.  out: host uint64[count], count >= 10.
+ * The counters are compiled in only when the library is built with
+ * FC_WILSON_COUNTERS=1 (they cost registers); otherwise they read 0.
+ * Synchronous.
+ */
+fc_status fc_sampler_counters(fc_graph* g, uint64_t* out, int32_t count);
+
+/* Launch shape used by the last fc_sample_usts on g (host pointers, may be NULL). */
+fc_status fc_sampler_last_shape(const fc_graph* g, int32_t* walkers_per_tree, int32_t* regs, int32_t* ctas);
 
 /*
  * Sample tau spanning trees of G* rooted at u* for EVERY alpha of the graph

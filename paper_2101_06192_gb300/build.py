@@ -38,8 +38,15 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
+def _flavour() -> str:
+    return "counters" if os.environ.get("FC_BUILD_COUNTERS") == "1" else "default"
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
+        return False
+    stamp = LIB + ".flavour"
+    if not os.path.exists(stamp) or open(stamp).read() != _flavour():
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(f) <= t for f in _deps())
@@ -54,6 +61,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
                      "-I", CSRC, "--expt-relaxed-constexpr"]
     if ptxas_v:
         common += ["-Xptxas", "-v"]
+    if os.environ.get("FC_BUILD_COUNTERS") == "1":
+        common += ["-DFC_WILSON_COUNTERS=1"]
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
@@ -75,6 +84,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(LIB + ".flavour", "w") as f:
+        f.write(_flavour())
     return LIB
 
 

@@ -393,7 +393,7 @@ extern "C" fc_status fc_build_augmented(int32_t n, int64_t nnz, const int64_t* r
   BUILD_CK(cudaMallocAsync((void**)&g->alphas_d, n_alpha * sizeof(double), st));
   BUILD_CK(cudaMallocAsync((void**)&g->d_err, 4 * sizeof(uint32_t), st));
   BUILD_CK(cudaMallocAsync((void**)&g->d_counter, 2 * sizeof(unsigned long long), st));
-  BUILD_CK(cudaMallocAsync((void**)&g->d_stats, 4 * sizeof(unsigned long long), st));
+  BUILD_CK(cudaMallocAsync((void**)&g->d_stats, 16 * sizeof(unsigned long long), st));
 
   const cudaMemcpyKind kind = flags == FC_DEVICE_PTRS ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   BUILD_CK(cudaMemcpyAsync(g->rowptr, rowptr, (n + 1) * sizeof(int64_t), kind, st));
@@ -491,13 +491,29 @@ extern "C" fc_status fc_graph_info(const fc_graph* g, int32_t* n, int64_t* nnz, 
 }
 
 extern "C" fc_status fc_set_sampler_shape(fc_graph* g, int32_t walkers_per_tree, int32_t max_trees_resident,
-                                          int32_t smem) {
+                                          int32_t smem, int32_t regs) {
   if (g == nullptr || walkers_per_tree < 0 || walkers_per_tree > 1024 || (walkers_per_tree % 32) != 0 ||
-      max_trees_resident < 0 || smem < 0 || smem > 2)
+      max_trees_resident < 0 || smem < 0 || smem > 2 || !(regs == 0 || regs == 32 || regs == 40 || regs == 64))
     return FC_EINVAL;
   g->walkers = walkers_per_tree;
   g->max_trees = max_trees_resident;
   g->smem_mode = smem;
+  g->regs = regs;
+  return FC_OK;
+}
+
+extern "C" fc_status fc_set_start_order(fc_graph* g, int32_t descending) {
+  if (g == nullptr || descending < 0 || descending > 1) return FC_EINVAL;
+  g->order_desc = descending;
+  return FC_OK;
+}
+
+extern "C" fc_status fc_sampler_last_shape(const fc_graph* g, int32_t* walkers_per_tree, int32_t* regs,
+                                           int32_t* ctas) {
+  if (g == nullptr) return FC_EINVAL;
+  if (walkers_per_tree) *walkers_per_tree = g->last_W;
+  if (regs) *regs = g->last_regs;
+  if (ctas) *ctas = g->last_grid;
   return FC_OK;
 }
 

@@ -163,6 +163,9 @@ struct fc_graph {
   int32_t walkers = 0;
   int32_t max_trees = 0;
   int32_t smem_mode = 0;
+  int32_t regs = 0;            // register cap of the sampler variant (0 = automatic)
+  int32_t order_desc = 0;      // sampler takes start vertices from the high-degree end
+  int32_t last_W = 0, last_regs = 0, last_grid = 0;  // shape of the last launch
   // scratch owned by the graph
   void* ws = nullptr;          // sampler per-tree state
   size_t ws_bytes = 0;

@@ -17,6 +17,23 @@ namespace fcx {
 
 constexpr int SV_T = 256;
 
+// Rows are processed by groups of RG consecutive lanes (strided over the
+// row's entries, then a shuffle reduction), so long rows do not serialise one
+// thread.  Each block covers SV_T / RG rows.
+constexpr int RG = 8;
+constexpr int ROWS_PER_BLOCK = SV_T / RG;
+
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+  for (int o = RG / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float group_sumf(float v) {
+#pragma unroll
+  for (int o = RG / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // ---- FP64 residual r = b - A x, partial sums of r.r and b.b ---------------
 __global__ void k_resid64(int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                           const float* __restrict__ w, const double* __restrict__ dw, double alpha,
@@ -24,15 +41,19 @@ __global__ void k_resid64(int32_t n, const int64_t* __restrict__ rowptr, const i
                           double* __restrict__ prr, double* __restrict__ pbb, int nb) {
   __shared__ double s1[SV_T], s2[SV_T];
   const int j = blockIdx.y;
-  const int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x;
+  const int gl = threadIdx.x % RG;
+  const int64_t v = (int64_t)blockIdx.x * ROWS_PER_BLOCK + threadIdx.x / RG;
   const size_t off = (size_t)j * n;
   double rr = 0.0, bb = 0.0;
+  double acc = 0.0;
   if (v < n) {
-    double acc = 0.0;
-    for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+    for (int64_t e = rowptr[v] + gl; e < rowptr[v + 1]; e += RG) {
       const double we = w ? (double)w[e] : 1.0;
       acc += we * x[off + colidx[e]];
     }
+  }
+  acc = group_sum(acc);
+  if (v < n && gl == 0) {
     const double ax = x[off + v] * (1.0 + alpha * dw[v]) - alpha * acc;
     const double rv = b[off + v] - ax;
     r[off + v] = rv;
@@ -80,7 +101,7 @@ struct Inner {
 };
 
 // r32 = r64 * inv_scale; d = 0; p = z = r32 / diag; partial r.z and r.r
-__global__ void k_inner_init(int32_t n, const double* __restrict__ r64, const float* __restrict__ diag32,
+__global__ void k_inner_init(int32_t n, const double* __restrict__ r64, const float* __restrict__ prec,
                              const double* __restrict__ scal, Inner in, double* __restrict__ prz,
                              double* __restrict__ prr, int nb) {
   __shared__ double s1[SV_T], s2[SV_T];
@@ -91,7 +112,7 @@ __global__ void k_inner_init(int32_t n, const double* __restrict__ r64, const fl
   if (v < n) {
     const double sc = scal[j * 8 + 4];
     const float rv = (float)(r64[off + v] * sc);
-    const float z = rv / diag32[v];
+    const float z = prec ? rv / prec[v] : rv;
     in.r[off + v] = rv;
     in.p[off + v] = z;
     in.d[off + v] = 0.0f;
@@ -120,13 +141,17 @@ __global__ void k_spmv_pq(int32_t n, const int64_t* __restrict__ rowptr, const i
                           double* __restrict__ ppq, int nb) {
   __shared__ double s1[SV_T];
   const int j = blockIdx.y;
-  const int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x;
+  const int gl = threadIdx.x % RG;
+  const int64_t v = (int64_t)blockIdx.x * ROWS_PER_BLOCK + threadIdx.x / RG;
   const size_t off = (size_t)j * n;
+  const float* pj = in.p + off;
   double pq = 0.0;
+  float acc = 0.0f;
   if (v < n) {
-    float acc = 0.0f;
-    const float* pj = in.p + off;
-    for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) acc += (w ? w[e] : 1.0f) * pj[colidx[e]];
+    for (int64_t e = rowptr[v] + gl; e < rowptr[v + 1]; e += RG) acc += (w ? w[e] : 1.0f) * pj[colidx[e]];
+  }
+  acc = group_sumf(acc);
+  if (v < n && gl == 0) {
     const float pv = pj[v];
     const float qv = pv * diag32[v] - alpha * acc;
     in.q[off + v] = qv;
@@ -142,7 +167,7 @@ __global__ void k_spmv_pq(int32_t n, const int64_t* __restrict__ rowptr, const i
 }
 
 // d += a p; r -= a q; partial r.z, r.r with z = r / diag
-__global__ void k_inner_update(int32_t n, const float* __restrict__ diag32, const double* __restrict__ scal,
+__global__ void k_inner_update(int32_t n, const float* __restrict__ prec, const double* __restrict__ scal,
                                Inner in, double* __restrict__ prz, double* __restrict__ prr, int nb) {
   __shared__ double s1[SV_T], s2[SV_T];
   const int j = blockIdx.y;
@@ -155,7 +180,7 @@ __global__ void k_inner_update(int32_t n, const float* __restrict__ diag32, cons
     in.d[off + v] += a * in.p[off + v];
     const float rv = in.r[off + v] - a * in.q[off + v];
     in.r[off + v] = rv;
-    const float z = rv / diag32[v];
+    const float z = prec ? rv / prec[v] : rv;
     rz = (double)rv * (double)z;
     rr = (double)rv * (double)rv;
   }
@@ -176,14 +201,15 @@ __global__ void k_inner_update(int32_t n, const float* __restrict__ diag32, cons
 }
 
 // p = z + beta p with beta = rz_new / rz
-__global__ void k_inner_p(int32_t n, const float* __restrict__ diag32, const double* __restrict__ scal, Inner in) {
+__global__ void k_inner_p(int32_t n, const float* __restrict__ prec, const double* __restrict__ scal, Inner in) {
   const int j = blockIdx.y;
   const int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x;
   if (v >= n) return;
   const size_t off = (size_t)j * n;
   const double* sc = scal + j * 8;
   const float beta = sc[0] != 0.0 ? (float)(sc[2] / sc[0]) : 0.0f;
-  in.p[off + v] = in.r[off + v] / diag32[v] + beta * in.p[off + v];
+  const float z = prec ? in.r[off + v] / prec[v] : in.r[off + v];
+  in.p[off + v] = z + beta * in.p[off + v];
 }
 
 // scalar bookkeeping after k_inner_update: rz <- rz_new (done after k_inner_p
@@ -237,18 +263,18 @@ __global__ void k_partial_sum(int64_t len, const double* __restrict__ a, double*
 
 using namespace fcx;
 
-extern "C" fc_status fc_solve(fc_graph* g, int32_t alpha_idx, const double* b, double* x, int32_t n_rhs,
-                              double rel_tol, int32_t max_iter, int32_t* iters_out, void* stream) {
+static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, double* x, int32_t n_rhs,
+                            double rel_tol, int32_t max_iter, int32_t* iters_out, cudaStream_t st, bool jacobi) {
   if (g == nullptr || b == nullptr || x == nullptr || n_rhs < 1 || n_rhs > 65535 || alpha_idx < 0 ||
       alpha_idx >= g->n_alpha || !(rel_tol > 0.0) || max_iter < 1) {
     set_error("fc_solve: bad argument");
     return FC_EINVAL;
   }
-  cudaStream_t st = (cudaStream_t)stream;
   const int32_t n = g->n;
   const int m = n_rhs;
   const double alpha = g->alphas[alpha_idx];
-  const int nb = (n + SV_T - 1) / SV_T;
+  const int nb = (n + SV_T - 1) / SV_T;              // blocks of the element-wise kernels
+  const int nbr = (n + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK;  // blocks of the row kernels
   const size_t nm = (size_t)n * m;
   // scratch: FP64 r64, FP32 r/p/q/d, diag32, partials, scalars
   double* r64 = nullptr;
@@ -257,7 +283,8 @@ extern "C" fc_status fc_solve(fc_graph* g, int32_t alpha_idx, const double* b, d
   double* scal = nullptr;
   FC_CK(cudaMallocAsync((void**)&r64, nm * sizeof(double), st));
   FC_CK(cudaMallocAsync((void**)&f32, (4 * nm + n) * sizeof(float), st));
-  FC_CK(cudaMallocAsync((void**)&part, (size_t)2 * m * nb * sizeof(double) + 4 * m * sizeof(double), st));
+  const int npart = std::max(nb, nbr);
+  FC_CK(cudaMallocAsync((void**)&part, (size_t)2 * m * npart * sizeof(double) + 4 * m * sizeof(double), st));
   FC_CK(cudaMallocAsync((void**)&scal, (size_t)8 * m * sizeof(double), st));
   Inner in;
   in.r = f32;
@@ -267,22 +294,24 @@ extern "C" fc_status fc_solve(fc_graph* g, int32_t alpha_idx, const double* b, d
   in.scal = scal;
   float* diag32 = f32 + 4 * nm;
   double* pA = part;
-  double* pB = part + (size_t)m * nb;
-  double* sums = part + (size_t)2 * m * nb;  // [0..m): rr, [m..2m): bb
+  double* pB = part + (size_t)m * npart;
+  double* sums = part + (size_t)2 * m * npart;  // [0..m): rr, [m..2m): bb
+  const float* prec = jacobi ? diag32 : nullptr;
   k_diag32<<<(n + 255) / 256, 256, 0, st>>>(n, g->dw, alpha, diag32);
   FC_LAUNCHED();
   const dim3 grid(nb, m);
+  const dim3 gridr(nbr, m);
   const double inner_tol = 1e-4;
   const int check_every = 8;
   std::vector<double> h_rr(m), h_bb(m), h_scal((size_t)8 * m, 0.0), h_in(m);
   int used = 0;
   fc_status result = FC_ENOCONV;
   for (int outer = 0; outer < 64; ++outer) {
-    k_resid64<<<grid, SV_T, 0, st>>>(n, g->rowptr, g->colidx, g->w, g->dw, alpha, b, x, r64, pA, pB, nb);
+    k_resid64<<<gridr, SV_T, 0, st>>>(n, g->rowptr, g->colidx, g->w, g->dw, alpha, b, x, r64, pA, pB, nbr);
     FC_LAUNCHED();
-    k_colsum<<<m, SV_T, 0, st>>>(pA, nb, sums);
+    k_colsum<<<m, SV_T, 0, st>>>(pA, nbr, sums);
     fcx::note_launch();
-    k_colsum<<<m, SV_T, 0, st>>>(pB, nb, sums + m);
+    k_colsum<<<m, SV_T, 0, st>>>(pB, nbr, sums + m);
     fcx::note_launch();
     FC_CK(cudaMemcpyAsync(h_rr.data(), sums, m * sizeof(double), cudaMemcpyDeviceToHost, st));
     FC_CK(cudaMemcpyAsync(h_bb.data(), sums + m, m * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -301,7 +330,7 @@ extern "C" fc_status fc_solve(fc_graph* g, int32_t alpha_idx, const double* b, d
     }
     if (used >= max_iter) break;
     FC_CK(cudaMemcpyAsync(scal, h_scal.data(), (size_t)8 * m * sizeof(double), cudaMemcpyHostToDevice, st));
-    k_inner_init<<<grid, SV_T, 0, st>>>(n, r64, diag32, scal, in, pA, pB, nb);
+    k_inner_init<<<grid, SV_T, 0, st>>>(n, r64, prec, scal, in, pA, pB, nb);
     FC_LAUNCHED();
     k_colsum<<<m, SV_T, 0, st>>>(pA, nb, sums);
     fcx::note_launch();
@@ -315,14 +344,14 @@ extern "C" fc_status fc_solve(fc_graph* g, int32_t alpha_idx, const double* b, d
     FC_CK(cudaMemcpyAsync(scal, h_scal.data(), (size_t)8 * m * sizeof(double), cudaMemcpyHostToDevice, st));
     int it = 0;
     while (used < max_iter) {
-      k_spmv_pq<<<grid, SV_T, 0, st>>>(n, g->rowptr, g->colidx, g->w, diag32, (float)alpha, in, pA, nb);
+      k_spmv_pq<<<gridr, SV_T, 0, st>>>(n, g->rowptr, g->colidx, g->w, diag32, (float)alpha, in, pA, nbr);
       FC_LAUNCHED();
       // pq -> scal[j*8+1]
-      k_colsum<<<m, SV_T, 0, st>>>(pA, nb, sums);
+      k_colsum<<<m, SV_T, 0, st>>>(pA, nbr, sums);
       fcx::note_launch();
       FC_CK(cudaMemcpy2DAsync(scal + 1, 8 * sizeof(double), sums, sizeof(double), sizeof(double), m,
                               cudaMemcpyDeviceToDevice, st));
-      k_inner_update<<<grid, SV_T, 0, st>>>(n, diag32, scal, in, pA, pB, nb);
+      k_inner_update<<<grid, SV_T, 0, st>>>(n, prec, scal, in, pA, pB, nb);
       FC_LAUNCHED();
       k_colsum<<<m, SV_T, 0, st>>>(pA, nb, sums);
       fcx::note_launch();
@@ -332,13 +361,13 @@ extern "C" fc_status fc_solve(fc_graph* g, int32_t alpha_idx, const double* b, d
                               cudaMemcpyDeviceToDevice, st));
       FC_CK(cudaMemcpy2DAsync(scal + 3, 8 * sizeof(double), sums + m, sizeof(double), sizeof(double), m,
                               cudaMemcpyDeviceToDevice, st));
-      k_inner_p<<<grid, SV_T, 0, st>>>(n, diag32, scal, in);
+      k_inner_p<<<grid, SV_T, 0, st>>>(n, prec, scal, in);
       FC_LAUNCHED();
       k_scal_shift<<<(m + 127) / 128, 128, 0, st>>>(m, scal);
       fcx::note_launch();
       ++used;
       ++it;
-      if (it % check_every == 0) {
+      if (it == 1 || it == 2 || it == 4 || it % check_every == 0) {
         FC_CK(cudaMemcpyAsync(h_rr.data(), sums + m, m * sizeof(double), cudaMemcpyDeviceToHost, st));
         FC_CK(cudaStreamSynchronize(st));
         bool conv = true;
@@ -360,6 +389,11 @@ extern "C" fc_status fc_solve(fc_graph* g, int32_t alpha_idx, const double* b, d
   return result;
 }
 
+extern "C" fc_status fc_solve(fc_graph* g, int32_t alpha_idx, const double* b, double* x, int32_t n_rhs,
+                              double rel_tol, int32_t max_iter, int32_t* iters_out, void* stream) {
+  return solve_impl(g, alpha_idx, b, x, n_rhs, rel_tol, max_iter, iters_out, (cudaStream_t)stream, true);
+}
+
 extern "C" fc_status fc_pivot_solve(fc_graph* g, int32_t alpha_idx, double* x, double rel_tol, int32_t max_iter,
                                     int32_t* iters_out, void* stream) {
   if (g == nullptr || x == nullptr || alpha_idx < 0 || alpha_idx >= g->n_alpha) {
@@ -378,7 +412,10 @@ extern "C" fc_status fc_pivot_solve(fc_graph* g, int32_t alpha_idx, double* x, d
   k_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, -1.0 / (double)n1, rhs);
   FC_LAUNCHED();
   FC_CK(cudaMemsetAsync(x, 0, (size_t)n1 * sizeof(double), st));
-  const fc_status s = fc_solve(g, alpha_idx, rhs, x, 1, rel_tol, max_iter, iters_out, stream);
+  // The right-hand side restricted to V is a multiple of 1, an eigenvector of
+  // I + alpha L with eigenvalue 1: unpreconditioned CG reaches it in one step
+  // (Jacobi scaling would break that), so the pivot system runs without it.
+  const fc_status s = solve_impl(g, alpha_idx, rhs, x, 1, rel_tol, max_iter, iters_out, st, false);
   if (s != FC_OK && s != FC_ENOCONV) return s;
   // shift to the mean-zero gauge of L*^+
   k_partial_sum<<<nb, SV_T, 0, st>>>(n1, x, part);

@@ -49,10 +49,10 @@ struct WParams {
   int32_t n;
   int32_t n_alpha;
   int64_t nnz;
-  const uint4* rowinfo;     // [n_alpha][n]
+  const uint4* rowinfo;     // [n_alpha][n] {row offset, degree, T lo, T hi}
   const int32_t* colidx;    // [nnz]
-  const uint64_t* B;        // [n_alpha][nnz] or null (unweighted)
-  const int32_t* order;     // [n]
+  const int32_t* order;     // [n] start order (ascending degree)
+  const uint64_t* B;        // [n_alpha][nnz] slot thresholds, or null (unweighted)
   int64_t tau;
   int64_t tree_offset;
   uint32_t key0, key1;
@@ -61,41 +61,89 @@ struct WParams {
   int32_t* parents;         // [n_alpha*tau][n] or null
   uint64_t* steps;          // [n_alpha*tau] or null
   VState* gstate;           // [gridDim.x][n] (global-state variant)
+  uint32_t* gbits;          // [gridDim.x][words] in-tree bitmaps (global-state variant)
+  int32_t words;            // bitmap words per tree: ceil(n / 32)
   unsigned long long* counter;
   uint32_t* err;
-  unsigned long long* stats;  // [0] pops, [1] departures
-  uint64_t max_iters;
+  unsigned long long* stats;  // [0] pops, [1] departures, [2..] iteration counters (N_CNT)
+  uint32_t max_iters;
+  int descending;           // take start vertices from the high-degree end
 };
 
-// Vertex selected by the stack entry with Philox words o at a vertex with row
-// info ri = {row offset, degree, T lo, T hi}.  n means u*.
-__device__ __forceinline__ uint32_t select_vertex(const WParams& p, const uint4& ri, const uint4& o,
-                                                  const uint64_t* __restrict__ Brow) {
+// Iteration counters (diagnostic), summed over walkers and trees.
+enum { CNT_ITER = 0, CNT_CLAIM_OK, CNT_TREE_HIT, CNT_CONFIRM, CNT_SPIN, CNT_WAIT, CNT_RELEASE, CNT_POP,
+       CNT_EDGE, CNT_IDLE_LANE, N_CNT };
+
+// Slot decision for one stack entry with Philox words o at a vertex with row
+// info ri = {row offset, degree, T lo, T hi}: returns true and sets *edge to
+// the CSR entry of the selected neighbour, or false when the entry selects u*
+// (u53 < T).  The neighbour is floor(o2 d / 2^32) (unweighted) or the first
+// entry of the row with u53 < B (weighted; the last B of a row is 2^53).
+__device__ __forceinline__ bool select_edge(const WParams& p, int a, const uint4& ri, const uint4& o,
+                                            uint32_t* edge) {
+  const uint32_t d = ri.y;
   const uint64_t u = stack_u53(o);
   const uint64_t T = (uint64_t)ri.z | ((uint64_t)ri.w << 32);
-  if (u < T) return (uint32_t)p.n;
-  if (Brow == nullptr) {
-    const uint32_t j = __umulhi(o.z, ri.y);  // floor(o2 d / 2^32)
-    return (uint32_t)__ldg(p.colidx + ri.x + j);
+  if (u < T) return false;
+  if (p.B == nullptr) {
+    *edge = ri.x + __umulhi(o.z, d);
+    return true;
   }
-  // first entry j of the row with u < B[j]; the last entry is 2^53 > u
-  uint32_t lo = 0, hi = ri.y - 1;
-  const uint64_t* b = Brow + ri.x;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (u < __ldg(b + mid)) hi = mid; else lo = mid + 1;
+  const uint64_t* b = p.B + (size_t)a * p.nnz + ri.x;
+  uint32_t lo = 0, hi = d - 1;
+  if (d <= 8) {
+    // short rows: all thresholds in flight at once
+    uint64_t bv[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) bv[j] = (j < (int)d - 1) ? __ldg(b + j) : ~0ull;
+#pragma unroll
+    for (int j = 7; j >= 0; --j)
+      if (u < bv[j]) lo = (uint32_t)j;
+    lo = min(lo, d - 1);
+  } else {
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (u < __ldg(b + mid)) hi = mid; else lo = mid + 1;
+    }
   }
-  return (uint32_t)__ldg(p.colidx + ri.x + lo);
+  *edge = ri.x + lo;
+  return true;
 }
 
-enum { M_IDLE = 0, M_CLAIM = 1, M_WAIT = 2 };
+enum { P_IDLE = 0, P_CHECK, P_CLAIM, P_CLAIM2, P_EDGE, P_NEXT, P_POP, P_RETRACE, P_RELEASE, P_WAIT,
+       P_DONE };
+constexpr uint32_t NO_START = 0xffffffffu;
+constexpr int PB = 8;  // path vertices remembered per walker (shared memory)
 
 __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* a) {
   return *(const volatile unsigned long long*)a;
 }
+__device__ __forceinline__ uint32_t ld_volatile32(const uint32_t* a) {
+  return *(const volatile uint32_t*)a;
+}
 
-template <bool SMEM>
-__global__ void __launch_bounds__(1024) k_wilson(WParams p) {
+// Per-iteration diagnostic counters (fc_sampler_counters) are compiled in only
+// with -DFC_WILSON_COUNTERS=1; they cost registers in the walk loop.
+#ifndef FC_WILSON_COUNTERS
+#define FC_WILSON_COUNTERS 0
+#endif
+#if FC_WILSON_COUNTERS
+#define CNT(q) (++cnt[q])
+#else
+#define CNT(q) ((void)0)
+#endif
+
+// One loop iteration = at most one dependent round trip to memory per walker:
+// the memory operations of the iteration are issued (predicated by the
+// walker's mode) before results are consumed, so the 32 walkers of a warp
+// overlap their waits whatever mix of modes they are in.  A departure takes
+// two iterations: CHECK (in-tree bit + row info, both L2-resident) and CLAIM
+// (CAS on the 16-byte state, with the stack entry for k = 0 computed
+// speculatively and its CSR target loaded alongside).  Tree membership lives
+// only in the bitmap, so tree hits and the marking of finished paths never
+// touch the state array.
+template <bool SMEM, int MAXREG>
+__global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long sh_tree, sh_pops, sh_deps;
   __shared__ uint32_t sh_next;
@@ -105,13 +153,19 @@ __global__ void __launch_bounds__(1024) k_wilson(WParams p) {
   const int lane = me & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   volatile uint32_t* sh_gen = (volatile uint32_t*)smem_raw;
-  VState* S;
-  if (SMEM) {
-    S = (VState*)(smem_raw + (((size_t)W * 4 + 15) & ~(size_t)15));
-  } else {
-    S = p.gstate + (size_t)blockIdx.x * p.n;
-  }
+  uint32_t* sh_pb = (uint32_t*)(smem_raw + (size_t)W * 4);  // [PB][W] path prefix of each walker
   const int32_t n = p.n;
+  const int32_t words = p.words;
+  VState* S;
+  uint32_t* bits;
+  if (SMEM) {
+    unsigned char* base = smem_raw + (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15);
+    S = (VState*)base;
+    bits = (uint32_t*)(base + (size_t)n * sizeof(VState));
+  } else {
+    S = p.gstate + (size_t)blockIdx.x * n;
+    bits = p.gbits + (size_t)blockIdx.x * words;
+  }
   const int64_t total = (int64_t)p.n_alpha * p.tau;
 
   for (;;) {
@@ -122,6 +176,7 @@ __global__ void __launch_bounds__(1024) k_wilson(WParams p) {
     const int a = (int)(tree / (unsigned long long)p.tau);
     const uint32_t tg = (uint32_t)(p.tree_offset + (int64_t)(tree % (unsigned long long)p.tau));
     for (int32_t v = me; v < n; v += W) reinterpret_cast<uint4*>(S)[v] = make_uint4(0u, 0u, 0u, 0u);
+    for (int32_t q = me; q < words; q += W) bits[q] = 0u;
     sh_gen[me] = 1u;
     if (me == 0) {
       sh_next = 0;
@@ -132,175 +187,295 @@ __global__ void __launch_bounds__(1024) k_wilson(WParams p) {
     __syncthreads();
 
     const uint4* __restrict__ rinfo = p.rowinfo + (size_t)a * n;
-    const uint64_t* Brow = p.B ? p.B + (size_t)a * p.nnz : nullptr;
-    uint32_t* Ra = p.R + (size_t)a * n;
-    uint32_t* Ca = p.C ? p.C + (size_t)a * n : nullptr;
 
-    int mode = M_IDLE;
-    bool done = false;
-    int32_t s = 0, x = 0, h = -1;
-    uint32_t gen = 1;
-    unsigned long long wait_tag = 0, confirm_tag = 0;
-    uint64_t iters = 0;
-    unsigned long long pops = 0, deps = 0;
+    int mode = P_IDLE;
+    int32_t x = 0, h = -1, c = 0, rh = 0, s = 0;
+    int32_t len = 0;           // vertices on the current path
+    bool rskip = false;        // the first walk step only loads (vertex already handled)
+    uint32_t sni = NO_START;
+    int32_t sn = -1;
+    uint4 xr = make_uint4(0u, 0u, 0u, 0u);  // row info of x
+    uint32_t enext = 0;        // CSR entry of h's selected neighbour (P_NEXT)
+    bool need = true;
+    uint32_t gen = 1, kx = 0, iters = 0, pops = 0, deps = 0;
+    unsigned long long wtag = 0, cexp = 0;
+#if FC_WILSON_COUNTERS
+    uint32_t cnt[N_CNT];
+#pragma unroll
+    for (int q = 0; q < N_CNT; ++q) cnt[q] = 0;
+#endif
 
     while (true) {
       __syncwarp();
-      const bool stop = done || (sh_abort != 0u);
-      if (__all_sync(FULL, stop)) break;
-      // hand consecutive start indices (ascending degree) to the idle lanes
-      const unsigned need = __ballot_sync(FULL, !stop && mode == M_IDLE);
-      if (need) {
-        const int leader = __ffs(need) - 1;
+      const bool fin = (mode == P_DONE) || (sh_abort != 0u);
+      if (__all_sync(FULL, fin)) break;
+      const unsigned want = __ballot_sync(FULL, need && !fin);
+      if (want) {
+        const int leader = __ffs(want) - 1;
         uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(&sh_next, (uint32_t)__popc(need));
+        if (lane == leader) base = atomicAdd(&sh_next, (uint32_t)__popc(want));
         base = __shfl_sync(FULL, base, leader);
-        if (!stop && mode == M_IDLE) {
-          const uint32_t i = base + __popc(need & lt_mask);
-          if (i >= (uint32_t)n) {
-            done = true;
-          } else {
-            s = __ldg(p.order + i);
-            x = s;
-            h = -1;
-            mode = M_CLAIM;
-            confirm_tag = 0;
-          }
+        if (need && !fin) {
+          sni = base + __popc(want & lt_mask);
+          sn = sni < (uint32_t)n ? __ldg(p.order + (p.descending ? (uint32_t)n - 1u - sni : sni)) : -1;
+          need = false;
         }
       }
-      if (stop || done) continue;
+      if (fin) {
+        CNT(CNT_IDLE_LANE);
+        continue;
+      }
+      CNT(CNT_ITER);
       if (++iters > p.max_iters) {
         atomicOr(p.err, ERR_TIMEOUT);
         sh_abort = 1u;
-        done = true;
+        mode = P_DONE;
         continue;
       }
-
-      if (mode == M_WAIT) {
-        // holding nothing: wait until x leaves the path it was blocked by
-        const unsigned long long cur = ld_volatile(&S[x].st) >> K_BITS;
-        const uint32_t ww = (uint32_t)(wait_tag & ((1u << W_BITS) - 1));
-        if (cur == wait_tag && sh_gen[ww] == (uint32_t)(wait_tag >> W_BITS)) continue;
-        mode = M_CLAIM;
+      if (mode == P_IDLE) {
+        if (sn < 0) {
+          mode = P_DONE;
+          continue;
+        }
+        s = sn;
         x = s;
         h = -1;
-        confirm_tag = 0;
+        len = 0;
+        mode = P_CHECK;
+        need = true;
       }
-
-      // ---- try to take x onto this walker's path ----
-      const uint4 ri = __ldg(rinfo + x);
       const unsigned long long mytag = ((unsigned long long)gen << W_BITS) | (unsigned)me;
-      const unsigned long long old = atomicCAS(&S[x].st, 0ull, mytag << K_BITS);
-      uint4 o = philox4x32_10(0u, (uint32_t)x, tg, (uint32_t)a, p.key0, p.key1);
-      uint32_t k = 0;
-      if (old != 0ull) {
-        const unsigned long long tag = old >> K_BITS;
-        if (tag == 0ull) {
-          // free vertex whose stack has been popped before
-          const unsigned long long want = (mytag << K_BITS) | (old & K_MASK);
-          if (atomicCAS(&S[x].st, old, want) != old) continue;  // raced: retry
-          k = (uint32_t)(old & K_MASK);
-          if (k >= (uint32_t)K_MASK) {
-            atomicOr(p.err, ERR_OVERFLOW);
-            sh_abort = 1u;
-            done = true;
-            continue;
+
+      // ---- issue ----
+      uint32_t bw = 0;
+      if (mode == P_CHECK) bw = ld_volatile32(bits + (x >> 5));
+      if (mode == P_CHECK) xr = __ldg(rinfo + x);
+      unsigned long long old = 0ull;
+      if (mode == P_CLAIM) old = atomicCAS(&S[x].st, 0ull, mytag << K_BITS);
+      else if (mode == P_CLAIM2) old = atomicCAS(&S[x].st, cexp, (mytag << K_BITS) | (cexp & K_MASK));
+      else if (mode == P_WAIT) old = ld_volatile(&S[x].st);
+      const bool walk = (mode == P_POP) || (mode == P_RETRACE) || (mode == P_RELEASE);
+      uint32_t nc = 0;
+      if (walk) nc = S[c].nxt;
+      // the stack entry: k = 0 speculatively while claiming, kx when computing a top
+      const bool topc = (mode == P_CLAIM) || (mode == P_EDGE);
+      uint32_t e = 0;
+      bool nb = false;
+      if (topc) {
+        const uint4 o = philox4x32_10(mode == P_EDGE ? kx : 0u, (uint32_t)x, tg, (uint32_t)a, p.key0, p.key1);
+        nb = select_edge(p, a, xr, o, &e);
+      }
+      int32_t t = n;
+      if (topc && nb) t = __ldg(p.colidx + e);
+      else if (mode == P_NEXT) t = __ldg(p.colidx + enext);
+
+      // ---- consume ----
+      bool finished = false;  // the path reached the tree or u*
+      switch (mode) {
+        case P_CHECK: {
+          if ((bw >> (x & 31)) & 1u) {
+            CNT(CNT_TREE_HIT);
+            finished = true;
+          } else {
+            mode = P_CLAIM;
           }
-          o = philox4x32_10(k, (uint32_t)x, tg, (uint32_t)a, p.key0, p.key1);
-        } else {
+          break;
+        }
+        case P_CLAIM:
+        case P_CLAIM2: {
+          if (mode == P_CLAIM ? (old == 0ull) : (old == cexp)) {
+            // x joins this walker's path
+            h = x;
+            if (len < PB) sh_pb[len * W + me] = (uint32_t)x;
+            ++len;
+            if (mode == P_CLAIM2) {
+              kx = (uint32_t)(cexp & K_MASK);
+              if (kx >= (uint32_t)K_MASK - 1u) {
+                atomicOr(p.err, ERR_OVERFLOW);
+                sh_abort = 1u;
+                mode = P_DONE;
+                break;
+              }
+              mode = P_EDGE;  // its top at entry k > 0 is computed next iteration
+              break;
+            }
+            CNT(CNT_CLAIM_OK);
+            ++deps;
+            S[h].nxt = (uint32_t)t;
+            if (!nb) {
+              atomicAdd(p.R + (size_t)a * n + h, 1u);
+              if (p.C != nullptr) atomicAdd(p.C + (size_t)a * n + h, 1u);
+              finished = true;
+              break;
+            }
+            x = t;
+            mode = P_CHECK;
+            break;
+          }
+          if (mode == P_CLAIM2) {
+            mode = P_CHECK;  // the state changed under us: look again
+            break;
+          }
+          const unsigned long long tag = old >> K_BITS;
+          if (tag == 0ull) {
+            cexp = old;  // free with k > 0
+            mode = P_CLAIM2;
+            break;
+          }
           const uint32_t w = (uint32_t)(tag & ((1u << W_BITS) - 1));
           const uint32_t tgen = (uint32_t)(tag >> W_BITS);
-          bool in_tree = false;
-          if (w == (uint32_t)me) {
-            if (tgen == gen) {
-              // x is on this walker's own path: pop the cycle x -> ... -> h -> x
-              uint32_t v = S[x].nxt;
-              int32_t guard = 0;
-              while (v != (uint32_t)x && guard++ <= n) {
-                const uint32_t nv = S[v].nxt;
-                atomicAdd(&S[v].st, 1ull - (mytag << K_BITS));  // free, next entry
-                ++pops;
-                v = nv;
-              }
-              k = (uint32_t)(old & K_MASK) + 1u;
-              if (k >= (uint32_t)K_MASK || v != (uint32_t)x) {
-                atomicOr(p.err, k >= (uint32_t)K_MASK ? ERR_OVERFLOW : ERR_INVAL);
-                sh_abort = 1u;
-                done = true;
-                continue;
-              }
-              atomicAdd(&S[x].st, 1ull);
-              ++pops;
-              o = philox4x32_10(k, (uint32_t)x, tg, (uint32_t)a, p.key0, p.key1);
-            } else {
-              in_tree = true;  // a finished path of this walker
-            }
+          if (w >= (uint32_t)W) {
+            atomicOr(p.err, ERR_INVAL);
+            sh_abort = 1u;
+            mode = P_DONE;
+            break;
+          }
+          if (w == (uint32_t)me && tgen == gen) {
+            // x closes a cycle on this walker's path: pop it
+            kx = (uint32_t)(old & K_MASK);
+            c = x;
+            rskip = true;
+            mode = P_POP;
+            break;
+          }
+          if (sh_gen[w] != tgen) {
+            // w finished that path (x is being marked in the tree) or gave x up
+            // after our read: look again, starting with the bit
+            CNT(CNT_SPIN);
+            mode = P_CHECK;
+            break;
+          }
+          if (h < 0 || (uint32_t)me < w) {
+            CNT(CNT_SPIN);  // wait-die: wait
+            break;
+          }
+          // die: give the path back without popping anything; vertices whose
+          // nxt the release walk still needs are freed only after it is read
+          CNT(CNT_RELEASE);
+          wtag = tag;
+          const int nfree = len > PB ? PB - 1 : len;
+          for (int i = 0; i < PB; ++i)
+            if (i < nfree) atomicAdd(&S[sh_pb[i * W + me]].st, 0ull - (mytag << K_BITS));
+          if (len > PB) {
+            c = (int32_t)sh_pb[(PB - 1) * W + me];
+            rh = h;
+            rskip = false;
+            mode = P_RELEASE;
           } else {
-            const uint32_t gcur = sh_gen[w];
-            if (gcur == tgen) {
-              // x is on walker w's active path
-              confirm_tag = 0;
-              if (h < 0 || (uint32_t)me < w) continue;  // wait (retry next iteration)
-              // die: give the whole path back, stacks untouched
-              uint32_t v = (uint32_t)s;
-              int32_t guard = 0;
-              while (guard++ <= n) {
-                const uint32_t nv = S[v].nxt;
-                atomicAdd(&S[v].st, 0ull - (mytag << K_BITS));
-                if (v == (uint32_t)h) break;
-                v = nv;
-              }
-              h = -1;
-              mode = M_WAIT;
-              wait_tag = tag;
-              continue;
-            }
-            // w has finished generation tgen; confirm with a second read of x
-            // ordered after the generation read (x may have been popped from
-            // w's path between our CAS and that read)
-            if (confirm_tag != tag) {
-              confirm_tag = tag;
-              __threadfence_block();
-              continue;
-            }
-            in_tree = true;
+            mode = P_WAIT;
           }
-          if (in_tree) {
-            // the path s -> ... -> h reaches the tree through x
-            if (h >= 0) {
-              __threadfence_block();
-              ++gen;
-              sh_gen[me] = gen;
-            }
-            h = -1;
-            mode = M_IDLE;
-            confirm_tag = 0;
-            continue;
-          }
+          h = -1;
+          len = 0;
+          break;
         }
+        case P_EDGE: {
+          CNT(CNT_EDGE);
+          ++deps;
+          S[h].nxt = (uint32_t)t;
+          if (!nb) {
+            atomicAdd(p.R + (size_t)a * n + h, 1u);
+            if (p.C != nullptr && kx == 0u) atomicAdd(p.C + (size_t)a * n + h, 1u);
+            finished = true;
+            break;
+          }
+          x = t;
+          mode = P_CHECK;
+          break;
+        }
+        case P_POP: {
+          // cycle x -> ... -> h -> x: free every vertex but x at its next entry
+          CNT(CNT_POP);
+          if (!rskip) {
+            atomicAdd(&S[c].st, 1ull - (mytag << K_BITS));
+            ++pops;
+          }
+          rskip = false;
+          c = (int32_t)nc;
+          if (c == x) {
+            atomicAdd(&S[x].st, 1ull);
+            ++pops;
+            ++kx;
+            if (kx >= (uint32_t)K_MASK) {
+              atomicOr(p.err, ERR_OVERFLOW);
+              sh_abort = 1u;
+              mode = P_DONE;
+              break;
+            }
+            // the path now ends at x
+            int32_t pos = len;
+            for (int i = 0; i < PB; ++i)
+              if (i < len && sh_pb[i * W + me] == (uint32_t)x) pos = i;
+            if (pos < PB) len = pos + 1;
+            h = x;
+            mode = P_EDGE;
+          }
+          break;
+        }
+        case P_RETRACE: {
+          if (!rskip) atomicOr(bits + (c >> 5), 1u << (c & 31));
+          rskip = false;
+          if (c == rh) mode = P_IDLE;
+          else c = (int32_t)nc;
+          break;
+        }
+        case P_RELEASE: {
+          atomicAdd(&S[c].st, 0ull - (mytag << K_BITS));
+          if (c == rh) mode = P_WAIT;
+          else c = (int32_t)nc;
+          break;
+        }
+        case P_WAIT: {
+          CNT(CNT_WAIT);
+          const uint32_t ww = (uint32_t)(wtag & ((1u << W_BITS) - 1));
+          if ((old >> K_BITS) == wtag && sh_gen[ww] == (uint32_t)(wtag >> W_BITS)) break;
+          x = s;
+          mode = P_CHECK;
+          break;
+        }
+        default:
+          break;
       }
-      // ---- x is the new head, at stack entry k ----
-      confirm_tag = 0;
-      h = x;
-      const uint32_t t = select_vertex(p, ri, o, Brow);
-      S[h].nxt = t;
-      ++deps;
-      if (t == (uint32_t)n) {
-        // the loop-erased walk ends with the edge {h, u*} (Algorithm 2: R[h]++)
-        atomicAdd(Ra + h, 1u);
-        if (Ca != nullptr && k == 0u) atomicAdd(Ca + h, 1u);
-        __threadfence_block();
-        ++gen;
-        sh_gen[me] = gen;
+
+      if (finished) {
+        // the path s -> ... -> h joins the tree: bump the generation (walkers
+        // that meet the path from now on re-check the bit instead of dying),
+        // then set the bits of the remembered prefix and walk the rest
+        if (len > 0) {
+          __threadfence_block();
+          ++gen;
+          sh_gen[me] = gen;
+          for (int i = 0; i < PB; ++i)
+            if (i < len) {
+              const uint32_t v = sh_pb[i * W + me];
+              atomicOr(bits + (v >> 5), 1u << (v & 31));
+            }
+          if (len > PB) {
+            c = (int32_t)sh_pb[(PB - 1) * W + me];
+            rh = h;
+            rskip = true;
+            mode = P_RETRACE;
+          } else {
+            mode = P_IDLE;
+          }
+        } else {
+          mode = P_IDLE;
+        }
         h = -1;
-        mode = M_IDLE;
-        continue;
+        len = 0;
       }
-      x = (int32_t)t;
     }
 
-    atomicAdd(&sh_pops, pops);
-    atomicAdd(&sh_deps, deps);
+    atomicAdd(&sh_pops, (unsigned long long)pops);
+    atomicAdd(&sh_deps, (unsigned long long)deps);
+#if FC_WILSON_COUNTERS
+#pragma unroll
+    for (int q = 0; q < N_CNT; ++q) {
+      unsigned long long vq = cnt[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) vq += __shfl_xor_sync(FULL, vq, o);
+      if (lane == 0 && vq) atomicAdd(&p.stats[2 + q], vq);
+    }
+#endif
     __syncthreads();
     if (p.parents != nullptr) {
       int32_t* par = p.parents + (size_t)tree * n;
@@ -327,17 +502,73 @@ __global__ void k_stack_entries(WParams p, int a, uint32_t tg, int64_t count, co
   }
   const uint4 ri = p.rowinfo[(size_t)a * p.n + v];
   const uint4 o = philox4x32_10(ks[i], (uint32_t)v, tg, (uint32_t)a, p.key0, p.key1);
-  out[i] = (int32_t)select_vertex(p, ri, o, p.B ? p.B + (size_t)a * p.nnz : nullptr);
+  uint32_t e = 0;
+  out[i] = select_edge(p, a, ri, o, &e) ? p.colidx[e] : p.n;
 }
 
 static size_t smem_bytes(int W, int32_t n, bool smem) {
-  const size_t gen = ((size_t)W * 4 + 15) & ~(size_t)15;
-  return smem ? gen + (size_t)n * sizeof(VState) : gen;
+  const size_t gen = ((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15;
+  const size_t words = ((size_t)n + 31) / 32;
+  return smem ? gen + (size_t)n * sizeof(VState) + words * 4 : gen;
 }
 
-static int default_walkers(int32_t n) {
-  int w = (n / 64) & ~31;
-  return std::max(32, std::min(256, w));
+typedef void (*WilsonFn)(WParams);
+
+static WilsonFn wilson_fn(bool smem, int regs) {
+  if (smem) {
+    if (regs == 32) return k_wilson<true, 32>;
+    if (regs == 40) return k_wilson<true, 40>;
+    return k_wilson<true, 64>;
+  }
+  if (regs == 32) return k_wilson<false, 32>;
+  if (regs == 40) return k_wilson<false, 40>;
+  return k_wilson<false, 64>;
+}
+
+struct Shape {
+  int W = 0;
+  int regs = 64;
+  int per_sm = 0;
+};
+
+// Launch shape: the largest walker count whose CTAs hold every tree of the
+// launch in one wave (trees of one launch take about equally long), else the
+// shape with the most walkers resident.  Walkers per tree are capped at n/8.
+static fc_status choose_shape(const fc_graph* g, int64_t total, bool smem, int nsm, Shape* out) {
+  const int32_t n = g->n;
+  const int wcap = std::max(32, std::min(1024, (int)((n / 8) & ~31)));
+  const int regs_list[3] = {32, 40, 64};
+  double best = -1.0;
+  for (int ri = 0; ri < 3; ++ri) {
+    const int regs = g->regs > 0 ? g->regs : regs_list[ri];
+    if (g->regs > 0 && ri > 0) break;
+    const WilsonFn fn = wilson_fn(smem, regs);
+    for (int W = (g->walkers > 0 ? g->walkers : wcap); W >= 32; W -= 32) {
+      const size_t shb = smem_bytes(W, n, smem);
+      if (smem) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
+      int per_sm = 0;
+      FC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, W, shb));
+      if (per_sm > 0) {
+        const int64_t slots = (int64_t)per_sm * nsm;
+        const int64_t waves = (total + slots - 1) / slots;
+        // walkers busy per wave, averaged over the waves
+        const double score = (double)W * (double)std::min<int64_t>(total, slots) * (double)total /
+                             ((double)waves * (double)std::min<int64_t>(total, slots) * (double)waves + 1e-9);
+        if (score > best * 1.0001) {
+          best = score;
+          out->W = W;
+          out->regs = regs;
+          out->per_sm = per_sm;
+        }
+      }
+      if (g->walkers > 0) break;
+    }
+  }
+  if (out->W == 0) {
+    set_error("fc_sample_usts: launch shape does not fit on an SM");
+    return FC_EINVAL;
+  }
+  return FC_OK;
 }
 
 }  // namespace fcx
@@ -354,55 +585,56 @@ extern "C" fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int
   if (tau == 0) return FC_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const int32_t n = g->n;
-  const int W = g->walkers > 0 ? g->walkers : default_walkers(n);
   int dev_smem_optin = 0, nsm = 0;
   FC_CK(cudaDeviceGetAttribute(&dev_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
   FC_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device));
-  const bool fits = smem_bytes(W, n, true) + 64 <= (size_t)dev_smem_optin;
-  bool use_smem = g->smem_mode == 2 ? true : (g->smem_mode == 1 ? false : fits);
+  const int64_t total = (int64_t)g->n_alpha * tau;
+  const int wmin = g->walkers > 0 ? g->walkers : 32;
+  const bool fits = smem_bytes(wmin, n, true) + 64 <= (size_t)dev_smem_optin;
+  const bool use_smem = g->smem_mode == 2 ? true : (g->smem_mode == 1 ? false : fits);
   if (use_smem && !fits) {
     set_error("fc_sample_usts: tree state does not fit in shared memory");
     return FC_EINVAL;
   }
+  Shape sh;
+  {
+    const fc_status r = choose_shape(g, total, use_smem, nsm, &sh);
+    if (r != FC_OK) return r;
+  }
+  const int W = sh.W;
   const size_t shb = smem_bytes(W, n, use_smem);
-  int per_sm = 0;
-  if (use_smem) {
-    FC_CK(cudaFuncSetAttribute(k_wilson<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
-    FC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wilson<true>, W, shb));
-  } else {
-    FC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wilson<false>, W, shb));
-  }
-  if (per_sm < 1) {
-    set_error("fc_sample_usts: launch shape does not fit on an SM");
-    return FC_EINVAL;
-  }
-  const int64_t total = (int64_t)g->n_alpha * tau;
-  int64_t grid = std::min<int64_t>(total, (int64_t)per_sm * nsm);
+  int64_t grid = std::min<int64_t>(total, (int64_t)sh.per_sm * nsm);
   if (g->max_trees > 0) grid = std::min<int64_t>(grid, g->max_trees);
   void* gstate = nullptr;
+  uint32_t* gbits = nullptr;
   if (!use_smem) {
     // keep the per-tree state within a quarter of the device memory
     size_t freeb = 0, totalb = 0;
     FC_CK(cudaMemGetInfo(&freeb, &totalb));
-    const size_t per_tree = (size_t)n * sizeof(VState);
+    const size_t words = ((size_t)n + 31) / 32;
+    const size_t per_tree = (size_t)n * sizeof(VState) + ((words * 4 + 255) & ~(size_t)255);
     const size_t cap_trees = std::max<size_t>(1, (totalb / 4) / per_tree);
     grid = std::min<int64_t>(grid, (int64_t)cap_trees);
     void* ws = nullptr;
     const fc_status s = sampler_scratch(g->device, (size_t)grid * per_tree, st, &ws);
     if (s != FC_OK) return s;
-    g->ws = nullptr;
     gstate = ws;
+    gbits = (uint32_t*)((char*)ws + (size_t)grid * n * sizeof(VState));
   }
+  g->last_W = W;
+  g->last_regs = sh.regs;
+  g->last_grid = (int32_t)grid;
   WParams p;
   p.n = n;
   p.n_alpha = g->n_alpha;
   p.nnz = g->nnz;
   p.rowinfo = g->rowinfo;
   p.colidx = g->colidx;
-  p.B = g->weighted ? g->B : nullptr;
   p.order = g->order;
+  p.B = g->weighted ? g->B : nullptr;
   p.tau = tau;
   p.tree_offset = tree_offset;
+  p.descending = g->order_desc;
   p.key0 = (uint32_t)seed;
   p.key1 = (uint32_t)(seed >> 32);
   p.R = R;
@@ -410,17 +642,21 @@ extern "C" fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int
   p.parents = parents;
   p.steps = steps_out;
   p.gstate = (VState*)gstate;
+  p.gbits = gbits;
+  p.words = (int32_t)(((int64_t)n + 31) / 32);
   p.counter = g->d_counter;
   p.err = g->d_err;
   p.stats = g->d_stats;
-  p.max_iters = max_steps_per_tree ? max_steps_per_tree : (uint64_t)8 * (uint64_t)n + (1ull << 20);
+  {
+    const uint64_t mi = max_steps_per_tree ? max_steps_per_tree : (uint64_t)8 * (uint64_t)n + (1ull << 20);
+    p.max_iters = (uint32_t)std::min<uint64_t>(mi, 0xffffffffull);
+  }
   FC_CK(cudaMemsetAsync(g->d_counter, 0, sizeof(unsigned long long), st));
   FC_CK(cudaMemsetAsync(g->d_err, 0, sizeof(uint32_t), st));
-  FC_CK(cudaMemsetAsync(g->d_stats, 0, 2 * sizeof(unsigned long long), st));
-  if (use_smem)
-    k_wilson<true><<<(unsigned)grid, W, shb, st>>>(p);
-  else
-    k_wilson<false><<<(unsigned)grid, W, shb, st>>>(p);
+  FC_CK(cudaMemsetAsync(g->d_stats, 0, (2 + N_CNT) * sizeof(unsigned long long), st));
+  const WilsonFn fn = wilson_fn(use_smem, sh.regs);
+  if (use_smem) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
+  fn<<<(unsigned)grid, W, shb, st>>>(p);
   FC_LAUNCHED();
   uint32_t herr = 0;
   FC_CK(cudaMemcpyAsync(&herr, g->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -450,6 +686,14 @@ extern "C" fc_status fc_sampler_stats(fc_graph* g, uint64_t* pops, uint64_t* dep
   if (pops) *pops = h[0];
   if (departures) *departures = h[1];
   return FC_OK;
+}
+
+extern "C" fc_status fc_sampler_counters(fc_graph* g, uint64_t* out, int32_t count) {
+  if (g == nullptr || out == nullptr || count < 0) return FC_EINVAL;
+  unsigned long long h[N_CNT] = {};
+  FC_CK(cudaMemcpy(h, g->d_stats + 2, sizeof(h), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < count && i < N_CNT; ++i) out[i] = h[i];
+  return N_CNT <= count ? FC_OK : FC_EINVAL;
 }
 
 extern "C" fc_status fc_stack_entries(fc_graph* g, int32_t alpha_idx, uint64_t seed, uint32_t tree, int64_t count,

@@ -38,7 +38,10 @@ def lib():
         sig = {
             "fc_build_augmented": ([I32, I64, P, P, P, P, I32, U32, P, ctypes.POINTER(P)], ctypes.c_int),
             "fc_graph_info": ([P, P, P, P, P], ctypes.c_int),
-            "fc_set_sampler_shape": ([P, I32, I32, I32], ctypes.c_int),
+            "fc_set_sampler_shape": ([P, I32, I32, I32, I32], ctypes.c_int),
+            "fc_sampler_last_shape": ([P, P, P, P], ctypes.c_int),
+            "fc_set_start_order": ([P, I32], ctypes.c_int),
+            "fc_sampler_counters": ([P, P, I32], ctypes.c_int),
             "fc_sample_usts": ([P, U64, I64, I64, P, P, P, U64, P, P], ctypes.c_int),
             "fc_sampler_stats": ([P, P, P], ctypes.c_int),
             "fc_stack_entries": ([P, I32, U64, U32, I64, P, P, P, P], ctypes.c_int),
@@ -137,9 +140,26 @@ class Graph:
     def __exit__(self, *a):
         self.close()
 
-    def set_shape(self, walkers_per_tree: int = 0, max_trees_resident: int = 0, smem: int = 0):
-        _check(lib().fc_set_sampler_shape(self._h, walkers_per_tree, max_trees_resident, smem),
+    def set_shape(self, walkers_per_tree: int = 0, max_trees_resident: int = 0, smem: int = 0, regs: int = 0):
+        _check(lib().fc_set_sampler_shape(self._h, walkers_per_tree, max_trees_resident, smem, regs),
                "fc_set_sampler_shape")
+
+    def set_start_order(self, descending: bool):
+        _check(lib().fc_set_start_order(self._h, int(bool(descending))), "fc_set_start_order")
+
+    COUNTERS = ("iterations", "claims", "tree_hits", "confirms", "conflict_waits", "release_waits",
+                "releases", "pop_steps", "tops_k_gt_0", "idle_lane_iterations")
+
+    def sampler_counters(self):
+        out = (ctypes.c_uint64 * 10)()
+        _check(lib().fc_sampler_counters(self._h, out, 10), "fc_sampler_counters")
+        return dict(zip(self.COUNTERS, [int(v) for v in out]))
+
+    def last_shape(self):
+        w, r, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().fc_sampler_last_shape(self._h, ctypes.byref(w), ctypes.byref(r), ctypes.byref(c)),
+               "fc_sampler_last_shape")
+        return {"walkers_per_tree": w.value, "regs": r.value, "ctas": c.value}
 
     def sample(self, seed: int, tau: int, tree_offset: int = 0, R=None, C=None, with_C: bool = True,
                want_parents: bool = False, want_steps: bool = False, max_steps_per_tree: int = 0,

@@ -42,5 +42,5 @@ def test_null_graph_arguments_rejected_without_gpu():
     L = fc.lib()
     assert L.fc_graph_info(None, None, None, None, None) == fc.FC_EINVAL
     assert L.fc_sample_usts(None, 1, 1, 0, None, None, None, 0, None, None) == fc.FC_EINVAL
-    assert L.fc_set_sampler_shape(None, 32, 0, 0) == fc.FC_EINVAL
+    assert L.fc_set_sampler_shape(None, 32, 0, 0, 0) == fc.FC_EINVAL
     L.fc_destroy(None)
