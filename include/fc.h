@@ -219,6 +219,40 @@ fc_status fc_forest_farness_noalloc(fc_graph* g, int32_t alpha_idx, const uint32
 fc_status fc_p_root(fc_graph* g, int32_t alpha_idx, double* p_out, void* stream);
 
 /*
+ * Learned control variate (not in the paper).  A network g(x) = p + (1 - p)
+ * sigmoid(w2 . relu(W1 x + b1) + b2) predicts Omega_vv from the features
+ *   x = (log(1 + deg v), log(1 + alpha d_w(v)), log(1 + sum_{u in N(v)} deg u), log alpha),
+ * p = p_v (fc_p_root), 128 hidden units.  Parameters: FP32 master vector of
+ * fc_mlp_param_count() = 769 floats, W1[128][4] | b1[128] | w2[128] | b2; the
+ * kernels use them rounded to BF16 and accumulate in FP32.  Its output feeds
+ * g_pred of fc_forest_farness; any output keeps the estimator unbiased.
+ */
+int32_t fc_mlp_param_count(void);
+
+/* Features of every vertex for alpha index a: X float32 device [n][4].  Async. */
+fc_status fc_vertex_features(fc_graph* g, int32_t alpha_idx, float* X, void* stream);
+
+/* Prediction g_out float32 device [n] from features X [n][4].  Async. */
+fc_status fc_mlp_forward(fc_graph* g, int32_t alpha_idx, const float* X, const float* params, float* g_out,
+                         void* stream);
+
+/*
+ * Mean squared error loss(y) = mean_v (g_v - y_v)^2 and its gradient with
+ * respect to the (BF16-rounded) parameters.  y float32 device [n]; grad float32
+ * device [769]; loss float32 device [1] (may be NULL).  Deterministic
+ * (fixed-order reductions).  Allocates temporary device memory.  Async.
+ */
+fc_status fc_mlp_loss_grad(fc_graph* g, int32_t alpha_idx, const float* X, const float* y, const float* params,
+                           float* grad, float* loss, void* stream);
+
+/*
+ * One Adam step (Kingma & Ba, bias-corrected; step is 1-based) on count
+ * parameters, all device pointers.  Async.
+ */
+fc_status fc_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t count, int32_t step, float lr,
+                      float beta1, float beta2, float eps, void* stream);
+
+/*
  * Top-k ranking (Sec. 6.1): the k vertices with the smallest diag values
  * (= highest forest closeness by Eq. 3), ascending, ties by ascending vertex
  * id.  diag: FP64 device [n]; idx_out: int32 device [k]; 1 <= k <= n.

@@ -1,0 +1,265 @@
+// Learned control variate (not in the paper): a two-layer perceptron that
+// predicts g_v ~ Omega_vv from local features of v; the prediction only sets
+// the control-variate coefficient beta_v = (1 - g_v) / (1 - p_v), so the
+// estimator stays unbiased whatever the network outputs.
+//
+//   features  x = (log(1 + deg), log(1 + alpha d_w), log(1 + sum_{u in N(v)} deg(u)), log(alpha))
+//   network   h = relu(W1 x + b1) (128 units), z = w2 . h + b2,
+//             g = p + (1 - p) sigmoid(z)
+//   loss      mean over vertices of (g - y)^2
+//   optimiser Adam (Kingma & Ba) with bias correction
+//
+// Parameters: one FP32 master vector of MLP_NPARAM floats laid out as
+// W1[128][4], b1[128], w2[128], b2.  Every kernel reads them rounded to BF16
+// (round to nearest even) and accumulates in FP32.  The hidden layer has K = 4
+// and the output layer N = 1, so these are per-vertex dot products on the
+// CUDA cores, bound by reading the 16-byte feature rows.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "fc_internal.cuh"
+
+namespace fcx {
+
+constexpr int HID = 128;
+constexpr int NF = 4;
+constexpr int OFF_W1 = 0, OFF_B1 = HID * NF, OFF_W2 = OFF_B1 + HID, OFF_B2 = OFF_W2 + HID;
+constexpr int NPARAM = OFF_B2 + 1;  // 769
+constexpr int MLP_T = 128;          // threads per block (one hidden unit each in the gradient pass)
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ double p_of(const uint4& ri) {
+  const uint64_t T = (uint64_t)ri.z | ((uint64_t)ri.w << 32);
+  return (double)T * 0x1.0p-53;
+}
+
+// sum over neighbours of their degree, RG lanes per row
+constexpr int FG = 8;
+__global__ void k_features(int32_t n, double alpha, const int64_t* __restrict__ rowptr,
+                           const int32_t* __restrict__ colidx, const int32_t* __restrict__ deg,
+                           const double* __restrict__ dw, float4* __restrict__ X) {
+  const int gl = threadIdx.x % FG;
+  const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / FG;
+  double s2 = 0.0;
+  if (v < n)
+    for (int64_t e = rowptr[v] + gl; e < rowptr[v + 1]; e += FG) s2 += (double)deg[colidx[e]];
+#pragma unroll
+  for (int o = FG / 2; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  if (v < n && gl == 0) {
+    X[v] = make_float4((float)log1p((double)deg[v]), (float)log1p(alpha * dw[v]), (float)log1p(s2),
+                       (float)log(alpha));
+  }
+}
+
+__device__ __forceinline__ void load_params(const float* __restrict__ params, float* sw) {
+  for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) sw[i] = bf16r(params[i]);
+  __syncthreads();
+}
+
+// z = w2 . relu(W1 x + b1) + b2 with the (BF16-valued) weights in shared memory
+__device__ __forceinline__ float mlp_z(const float* sw, const float4& x) {
+  float z = sw[OFF_B2];
+#pragma unroll 8
+  for (int j = 0; j < HID; ++j) {
+    const float* w = sw + OFF_W1 + j * NF;
+    float pre = sw[OFF_B1 + j];
+    pre = fmaf(w[0], x.x, pre);
+    pre = fmaf(w[1], x.y, pre);
+    pre = fmaf(w[2], x.z, pre);
+    pre = fmaf(w[3], x.w, pre);
+    z = fmaf(sw[OFF_W2 + j], fmaxf(pre, 0.0f), z);
+  }
+  return z;
+}
+
+__global__ void __launch_bounds__(MLP_T) k_mlp_forward(int32_t n, const float4* __restrict__ X,
+                                                       const uint4* __restrict__ rinfo,
+                                                       const float* __restrict__ params, float* __restrict__ gout) {
+  __shared__ float sw[NPARAM];
+  load_params(params, sw);
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const float z = mlp_z(sw, X[v]);
+    const float s = 1.0f / (1.0f + expf(-z));
+    const float p = (float)p_of(rinfo[v]);
+    gout[v] = p + (1.0f - p) * s;
+  }
+}
+
+// Loss and gradient, per-block partials (fixed order, deterministic).
+// Pass over tiles of MLP_T vertices: thread t runs the forward pass of vertex
+// t of the tile and its dL/dz; then thread j accumulates the gradient of
+// hidden unit j over the tile's vertices in order.
+__global__ void __launch_bounds__(MLP_T) k_mlp_grad(int32_t n, const float4* __restrict__ X,
+                                                    const uint4* __restrict__ rinfo, const float* __restrict__ y,
+                                                    const float* __restrict__ params, float inv_n,
+                                                    float* __restrict__ gpart, double* __restrict__ lpart) {
+  __shared__ float sw[NPARAM];
+  __shared__ float4 sx[MLP_T];
+  __shared__ float sdz[MLP_T];
+  __shared__ double sl[MLP_T];
+  load_params(params, sw);
+  const int j = threadIdx.x;
+  float gW0 = 0.f, gW1 = 0.f, gW2 = 0.f, gW3 = 0.f, gb1 = 0.f, gw2 = 0.f, gb2 = 0.f;
+  double lsum = 0.0;
+  const float* wj = sw + OFF_W1 + j * NF;
+  for (int64_t base = (int64_t)blockIdx.x * MLP_T; base < n; base += (int64_t)gridDim.x * MLP_T) {
+    const int64_t v = base + j;
+    float dz = 0.0f;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (v < n) {
+      x = X[v];
+      const float z = mlp_z(sw, x);
+      const float s = 1.0f / (1.0f + expf(-z));
+      const float p = (float)p_of(rinfo[v]);
+      const float g = p + (1.0f - p) * s;
+      const float r = g - y[v];
+      lsum += (double)r * (double)r;
+      dz = 2.0f * r * inv_n * (1.0f - p) * s * (1.0f - s);
+    }
+    sx[j] = x;
+    sdz[j] = dz;
+    __syncthreads();
+    const int cnt = (n - base) < (int64_t)MLP_T ? (int)(n - base) : MLP_T;
+    for (int i = 0; i < cnt; ++i) {
+      const float4 xi = sx[i];
+      const float dzi = sdz[i];
+      float pre = sw[OFF_B1 + j];
+      pre = fmaf(wj[0], xi.x, pre);
+      pre = fmaf(wj[1], xi.y, pre);
+      pre = fmaf(wj[2], xi.z, pre);
+      pre = fmaf(wj[3], xi.w, pre);
+      if (pre > 0.0f) {
+        gw2 = fmaf(dzi, pre, gw2);
+        const float dpre = dzi * sw[OFF_W2 + j];
+        gW0 = fmaf(dpre, xi.x, gW0);
+        gW1 = fmaf(dpre, xi.y, gW1);
+        gW2 = fmaf(dpre, xi.z, gW2);
+        gW3 = fmaf(dpre, xi.w, gW3);
+        gb1 += dpre;
+      }
+      if (j == 0) gb2 += dzi;
+    }
+    __syncthreads();
+  }
+  float* out = gpart + (size_t)blockIdx.x * NPARAM;
+  out[OFF_W1 + j * NF + 0] = gW0;
+  out[OFF_W1 + j * NF + 1] = gW1;
+  out[OFF_W1 + j * NF + 2] = gW2;
+  out[OFF_W1 + j * NF + 3] = gW3;
+  out[OFF_B1 + j] = gb1;
+  out[OFF_W2 + j] = gw2;
+  if (j == 0) out[OFF_B2] = gb2;
+  sl[j] = lsum;
+  __syncthreads();
+  for (int s = MLP_T / 2; s > 0; s >>= 1) {
+    if (j < s) sl[j] += sl[j + s];
+    __syncthreads();
+  }
+  if (j == 0) lpart[blockIdx.x] = sl[0];
+}
+
+__global__ void k_mlp_grad_reduce(const float* __restrict__ gpart, const double* __restrict__ lpart, int nb,
+                                  double inv_n, float* __restrict__ grad, float* __restrict__ loss) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < NPARAM) {
+    float s = 0.0f;
+    for (int b = 0; b < nb; ++b) s += gpart[(size_t)b * NPARAM + i];
+    grad[i] = s;
+  }
+  if (i == 0 && loss != nullptr) {
+    double l = 0.0;
+    for (int b = 0; b < nb; ++b) l += lpart[b];
+    *loss = (float)(l * inv_n);
+  }
+}
+
+__global__ void k_adam(int32_t count, float* __restrict__ params, const float* __restrict__ grad,
+                       float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const float g = grad[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * g;
+  const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+  m[i] = mi;
+  v[i] = vi;
+  params[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+static int mlp_blocks(int32_t n) {
+  int64_t b = ((int64_t)n + MLP_T - 1) / MLP_T;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 8));
+}
+
+}  // namespace fcx
+
+using namespace fcx;
+
+extern "C" int32_t fc_mlp_param_count(void) { return NPARAM; }
+
+extern "C" fc_status fc_vertex_features(fc_graph* g, int32_t alpha_idx, float* X, void* stream) {
+  if (g == nullptr || X == nullptr || alpha_idx < 0 || alpha_idx >= g->n_alpha) {
+    set_error("fc_vertex_features: bad argument");
+    return FC_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t threads = (int64_t)g->n * FG;
+  k_features<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g->n, g->alphas[alpha_idx], g->rowptr,
+                                                                g->colidx, g->deg, g->dw, (float4*)X);
+  FC_LAUNCHED();
+  return FC_OK;
+}
+
+extern "C" fc_status fc_mlp_forward(fc_graph* g, int32_t alpha_idx, const float* X, const float* params,
+                                    float* g_out, void* stream) {
+  if (g == nullptr || X == nullptr || params == nullptr || g_out == nullptr || alpha_idx < 0 ||
+      alpha_idx >= g->n_alpha) {
+    set_error("fc_mlp_forward: bad argument");
+    return FC_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  k_mlp_forward<<<mlp_blocks(g->n), MLP_T, 0, st>>>(g->n, (const float4*)X, g->rowinfo + (size_t)alpha_idx * g->n,
+                                                    params, g_out);
+  FC_LAUNCHED();
+  return FC_OK;
+}
+
+extern "C" fc_status fc_mlp_loss_grad(fc_graph* g, int32_t alpha_idx, const float* X, const float* y,
+                                      const float* params, float* grad, float* loss, void* stream) {
+  if (g == nullptr || X == nullptr || y == nullptr || params == nullptr || grad == nullptr || alpha_idx < 0 ||
+      alpha_idx >= g->n_alpha) {
+    set_error("fc_mlp_loss_grad: bad argument");
+    return FC_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nb = mlp_blocks(g->n);
+  float* gpart = nullptr;
+  double* lpart = nullptr;
+  FC_CK(cudaMallocAsync((void**)&gpart, (size_t)nb * NPARAM * sizeof(float), st));
+  FC_CK(cudaMallocAsync((void**)&lpart, (size_t)nb * sizeof(double), st));
+  k_mlp_grad<<<nb, MLP_T, 0, st>>>(g->n, (const float4*)X, g->rowinfo + (size_t)alpha_idx * g->n, y, params,
+                                   1.0f / (float)g->n, gpart, lpart);
+  FC_LAUNCHED();
+  k_mlp_grad_reduce<<<(NPARAM + 255) / 256, 256, 0, st>>>(gpart, lpart, nb, 1.0 / (double)g->n, grad, loss);
+  FC_LAUNCHED();
+  FC_CK(cudaFreeAsync(gpart, st));
+  FC_CK(cudaFreeAsync(lpart, st));
+  return FC_OK;
+}
+
+extern "C" fc_status fc_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t count, int32_t step,
+                                 float lr, float beta1, float beta2, float eps, void* stream) {
+  if (params == nullptr || grad == nullptr || m == nullptr || v == nullptr || count < 1 || step < 1) {
+    set_error("fc_mlp_adam: bad argument");
+    return FC_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const float c1 = 1.0f - powf(beta1, (float)step);
+  const float c2 = 1.0f - powf(beta2, (float)step);
+  k_adam<<<(count + 255) / 256, 256, 0, st>>>(count, params, grad, m, v, lr, beta1, beta2, eps, c1, c2);
+  FC_LAUNCHED();
+  return FC_OK;
+}

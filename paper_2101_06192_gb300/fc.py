@@ -51,6 +51,12 @@ def lib():
             "fc_forest_farness_noalloc": ([P, I32, P, P, P, P, I64, P, P, P, P], ctypes.c_int),
             "fc_p_root": ([P, I32, P, P], ctypes.c_int),
             "fc_top_k": ([P, I32, I32, P, P], ctypes.c_int),
+            "fc_mlp_param_count": ([], I32),
+            "fc_vertex_features": ([P, I32, P, P], ctypes.c_int),
+            "fc_mlp_forward": ([P, I32, P, P, P, P], ctypes.c_int),
+            "fc_mlp_loss_grad": ([P, I32, P, P, P, P, P, P], ctypes.c_int),
+            "fc_mlp_adam": ([P, P, P, P, I32, I32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                             ctypes.c_float, P], ctypes.c_int),
             "fc_tau_for": ([D, D, D, I64], I64),
             "fc_destroy": ([P], None),
             "fc_status_str": ([ctypes.c_int], ctypes.c_char_p),
@@ -241,6 +247,25 @@ class Graph:
                "fc_forest_farness")
         return diag, far, clo
 
+    # ---- learned control variate ----
+    def features(self, alpha_idx: int = 0, stream=None):
+        X = torch.empty(self.n * 4, dtype=torch.float32, device=torch.device("cuda", torch.cuda.current_device()))
+        _check(lib().fc_vertex_features(self._h, alpha_idx, _ptr(X), _stream(stream)), "fc_vertex_features")
+        return X.view(self.n, 4)
+
+    def mlp_forward(self, X, params, alpha_idx: int = 0, stream=None):
+        out = torch.empty(self.n, dtype=torch.float32, device=X.device)
+        _check(lib().fc_mlp_forward(self._h, alpha_idx, _ptr(X.contiguous()), _ptr(params), _ptr(out),
+                                    _stream(stream)), "fc_mlp_forward")
+        return out
+
+    def mlp_loss_grad(self, X, y, params, alpha_idx: int = 0, stream=None):
+        grad = torch.empty_like(params)
+        loss = torch.empty(1, dtype=torch.float32, device=params.device)
+        _check(lib().fc_mlp_loss_grad(self._h, alpha_idx, _ptr(X.contiguous()), _ptr(y.contiguous()), _ptr(params),
+                                      _ptr(grad), _ptr(loss), _stream(stream)), "fc_mlp_loss_grad")
+        return loss, grad
+
     def p_root(self, alpha_idx: int = 0, stream=None):
         p = torch.empty(self.n, dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))
         _check(lib().fc_p_root(self._h, alpha_idx, _ptr(p), _stream(stream)), "fc_p_root")
@@ -252,6 +277,16 @@ def top_k(diag, k: int, stream=None):
     out = torch.empty(k, dtype=torch.int32, device=diag.device)
     _check(lib().fc_top_k(_ptr(diag), int(diag.numel()), int(k), _ptr(out), _stream(stream)), "fc_top_k")
     return out
+
+
+def mlp_param_count() -> int:
+    return int(lib().fc_mlp_param_count())
+
+
+def mlp_adam(params, grad, m, v, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+             eps: float = 1e-8, stream=None):
+    _check(lib().fc_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(), int(step), float(lr),
+                             float(beta1), float(beta2), float(eps), _stream(stream)), "fc_mlp_adam")
 
 
 def launch_count() -> int:

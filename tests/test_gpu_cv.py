@@ -1,0 +1,116 @@
+"""GPU learned control variate: features, gradients and optimiser against the
+FP64 oracle, and what the trained network gains over the plain estimator."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import cv as ocv
+from oracle import dense, mlp
+
+pytestmark = pytest.mark.gpu
+
+fc = pytest.importorskip("paper_2101_06192_gb300.fc")
+cvnet = pytest.importorskip("paper_2101_06192_gb300.cvnet")
+
+
+def _bf16_round(a):
+    """float32 -> nearest bfloat16 (ties to even), returned as float64."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _to_oracle(flat, hid=128):
+    f = _bf16_round(flat)
+    return {"W1": f[: hid * 4].reshape(hid, 4), "b1": f[hid * 4: hid * 5], "w2": f[hid * 5: hid * 6],
+            "b2": f[hid * 6:]}
+
+
+def _from_oracle(g):
+    return np.concatenate([g["W1"].ravel(), g["b1"], g["w2"], g["b2"]])
+
+
+@pytest.mark.parametrize("weighted,alpha", [(False, 1.0), (True, 0.4)])
+def test_features_match_oracle(weighted, alpha):
+    g = synth.barabasi_albert(3000, 3, 2, weighted=weighted)
+    G = fc.Graph.from_csr(g, [alpha])
+    X = G.features().cpu().numpy()
+    np.testing.assert_allclose(X, mlp.features(g, alpha), rtol=2e-6, atol=2e-6)
+    G.close()
+
+
+def test_gradient_matches_fp64_oracle():
+    g = synth.barabasi_albert(700, 3, 4)
+    G = fc.Graph.from_csr(g, [1.0])
+    Xo = mlp.features(g, 1.0)
+    X = torch.from_numpy(Xo.astype(np.float32)).cuda()
+    rng = np.random.default_rng(3)
+    p = ocv.p_root(g, 1.0)
+    y = np.clip(p + 0.3 * rng.random(g.n), 0, 1).astype(np.float32)
+    params = cvnet.init_params(11)
+    params += 0.05 * torch.randn_like(params)
+    loss, grad = G.mlp_loss_grad(X, torch.from_numpy(y).cuda(), params)
+    po = _to_oracle(params.cpu().numpy())
+    l_ref, g_ref = mlp.loss_and_grads(po, Xo.astype(np.float32).astype(np.float64), p, y.astype(np.float64))
+    gr = _from_oracle(g_ref)
+    gg = grad.cpu().numpy().astype(np.float64)
+    assert abs(float(loss.item()) - l_ref) <= 1e-4 * abs(l_ref)
+    np.testing.assert_allclose(gg, gr, rtol=2e-3, atol=2e-4 * np.abs(gr).max())
+    # forward
+    out = G.mlp_forward(X, params).cpu().numpy()
+    gref, _ = mlp.forward(po, Xo.astype(np.float32).astype(np.float64), p)
+    np.testing.assert_allclose(out, gref, rtol=1e-5, atol=1e-6)
+    G.close()
+
+
+def test_adam_step_matches_oracle():
+    rng = np.random.default_rng(5)
+    n = 769
+    p0 = rng.normal(size=n).astype(np.float32)
+    g1 = rng.normal(size=n).astype(np.float32)
+    g2 = rng.normal(size=n).astype(np.float32)
+    P = torch.from_numpy(p0.copy()).cuda()
+    m = torch.zeros_like(P)
+    v = torch.zeros_like(P)
+    st = {}
+    po = {"a": p0.astype(np.float64)}
+    for t, gg in ((1, g1), (2, g2)):
+        fc.mlp_adam(P, torch.from_numpy(gg).cuda(), m, v, t, 1e-2)
+        mlp.adam_step(po, {"a": gg.astype(np.float64)}, st, lr=1e-2, t=t)
+    np.testing.assert_allclose(P.cpu().numpy(), po["a"], rtol=1e-5, atol=1e-6)
+
+
+def test_trained_network_reduces_error_and_stays_unbiased():
+    """Train on small R-MAT graphs (plain-estimator targets), then on a held-out
+    graph the control-variate estimator has a markedly lower error against the
+    dense inverse than the plain estimator at the same number of trees."""
+    train = []
+    for seed in (101, 102, 103):
+        g = synth.rmat(10, 8, seed)
+        G = fc.Graph.from_csr(g, [1.0])
+        y = cvnet.plain_targets(G, 4096, seed=seed)
+        train.append((G, G.features(), y, 0))
+    params, hist = cvnet.train(train, steps=400, lr=3e-3, seed=1, log_every=100)
+    assert hist[-1][1] < hist[0][1]
+    gt = synth.rmat(11, 8, 999)
+    Gt = fc.Graph.from_csr(gt, [1.0])
+    om = np.diag(dense.forest_matrix(gt, 1.0))
+    gp = cvnet.predict(Gt, params)
+    tau = 128
+    err_plain, err_cv, mean_cv = [], [], []
+    for seed in range(8):
+        out = Gt.sample(5000 + seed, tau)
+        d_plain, _, _ = Gt.farness(out["R"], tau)
+        d_cv, _, _ = Gt.farness(out["R"], tau, C=out["C"], g_pred=gp)
+        err_plain.append(np.sqrt(np.mean((d_plain.cpu().numpy() - om) ** 2)))
+        err_cv.append(np.sqrt(np.mean((d_cv.cpu().numpy() - om) ** 2)))
+        mean_cv.append(d_cv.cpu().numpy())
+    gain = np.mean(err_plain) / np.mean(err_cv)
+    assert gain > 1.2, (np.mean(err_plain), np.mean(err_cv))
+    # unbiased: the average over the 8 runs is close to the truth
+    bias = np.mean(np.stack(mean_cv), axis=0) - om
+    assert abs(np.mean(bias)) < 3 * np.mean(err_cv) / np.sqrt(8 * gt.n) + 1e-3
+    for (G, _, _, _) in train:
+        G.close()
+    Gt.close()
