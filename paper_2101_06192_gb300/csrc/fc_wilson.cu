@@ -63,6 +63,7 @@ struct WParams {
   VState* gstate;           // [gridDim.x][n] (global-state variant)
   uint32_t* gbits;          // [gridDim.x][words] in-tree bitmaps (global-state variant)
   int32_t words;            // bitmap words per tree: ceil(n / 32)
+  int pre_cleared;          // the first tree of every CTA starts from host-cleared state
   unsigned long long* counter;
   uint32_t* err;
   unsigned long long* stats;  // [0] pops, [1] departures, [2..] iteration counters (N_CNT)
@@ -156,6 +157,9 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
   uint32_t* sh_pb = (uint32_t*)(smem_raw + (size_t)W * 4);  // [PB][W] path prefix of each walker
   const int32_t n = p.n;
   const int32_t words = p.words;
+  // Tree-major state: each CTA's trees use their own contiguous column.  (A
+  // vertex-major layout, which lets trees share lines at common start
+  // vertices, measured slower: atomics from many SMs then meet on one line.)
   VState* S;
   uint32_t* bits;
   if (SMEM) {
@@ -166,6 +170,9 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
     S = p.gstate + (size_t)blockIdx.x * n;
     bits = p.gbits + (size_t)blockIdx.x * words;
   }
+#define SV(v) S[(v)]
+#define BW(q) bits[(q)]
+  bool first_tree = true;
   const int64_t total = (int64_t)p.n_alpha * p.tau;
 
   for (;;) {
@@ -175,8 +182,11 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
     if ((int64_t)tree >= total || *(volatile uint32_t*)p.err != 0u) break;
     const int a = (int)(tree / (unsigned long long)p.tau);
     const uint32_t tg = (uint32_t)(p.tree_offset + (int64_t)(tree % (unsigned long long)p.tau));
-    for (int32_t v = me; v < n; v += W) reinterpret_cast<uint4*>(S)[v] = make_uint4(0u, 0u, 0u, 0u);
-    for (int32_t q = me; q < words; q += W) bits[q] = 0u;
+    if (!(first_tree && p.pre_cleared)) {
+      for (int32_t v = me; v < n; v += W) reinterpret_cast<uint4&>(SV(v)) = make_uint4(0u, 0u, 0u, 0u);
+      for (int32_t q = me; q < words; q += W) BW(q) = 0u;
+    }
+    first_tree = false;
     sh_gen[me] = 1u;
     if (me == 0) {
       sh_next = 0;
@@ -247,16 +257,24 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
       const unsigned long long mytag = ((unsigned long long)gen << W_BITS) | (unsigned)me;
 
       // ---- issue ----
-      uint32_t bw = 0;
-      if (mode == P_CHECK) bw = ld_volatile32(bits + (x >> 5));
-      if (mode == P_CHECK) xr = __ldg(rinfo + x);
+      // STEP (= CHECK then CLAIM of x within one iteration): the in-tree bit
+      // and row info of x come from L2; only if the bit is clear does the
+      // walker touch the 16-byte state (CAS), with the stack entry for k = 0
+      // computed and its CSR target loaded speculatively alongside.
+      bool hit = false;
+      if (mode == P_CHECK) {
+        const uint32_t bw = ld_volatile32(&BW(x >> 5));
+        xr = __ldg(rinfo + x);
+        hit = (bw >> (x & 31)) & 1u;
+        if (!hit) mode = P_CLAIM;
+      }
       unsigned long long old = 0ull;
-      if (mode == P_CLAIM) old = atomicCAS(&S[x].st, 0ull, mytag << K_BITS);
-      else if (mode == P_CLAIM2) old = atomicCAS(&S[x].st, cexp, (mytag << K_BITS) | (cexp & K_MASK));
-      else if (mode == P_WAIT) old = ld_volatile(&S[x].st);
+      if (mode == P_CLAIM) old = atomicCAS(&SV(x).st, 0ull, mytag << K_BITS);
+      else if (mode == P_CLAIM2) old = atomicCAS(&SV(x).st, cexp, (mytag << K_BITS) | (cexp & K_MASK));
+      else if (mode == P_WAIT) old = ld_volatile(&SV(x).st);
       const bool walk = (mode == P_POP) || (mode == P_RETRACE) || (mode == P_RELEASE);
       uint32_t nc = 0;
-      if (walk) nc = S[c].nxt;
+      if (walk) nc = SV(c).nxt;
       // the stack entry: k = 0 speculatively while claiming, kx when computing a top
       const bool topc = (mode == P_CLAIM) || (mode == P_EDGE);
       uint32_t e = 0;
@@ -272,13 +290,9 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
       // ---- consume ----
       bool finished = false;  // the path reached the tree or u*
       switch (mode) {
-        case P_CHECK: {
-          if ((bw >> (x & 31)) & 1u) {
-            CNT(CNT_TREE_HIT);
-            finished = true;
-          } else {
-            mode = P_CLAIM;
-          }
+        case P_CHECK: {  // x is in the tree
+          CNT(CNT_TREE_HIT);
+          finished = true;
           break;
         }
         case P_CLAIM:
@@ -301,7 +315,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
             }
             CNT(CNT_CLAIM_OK);
             ++deps;
-            S[h].nxt = (uint32_t)t;
+            SV(h).nxt = (uint32_t)t;
             if (!nb) {
               atomicAdd(p.R + (size_t)a * n + h, 1u);
               if (p.C != nullptr) atomicAdd(p.C + (size_t)a * n + h, 1u);
@@ -355,7 +369,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
           wtag = tag;
           const int nfree = len > PB ? PB - 1 : len;
           for (int i = 0; i < PB; ++i)
-            if (i < nfree) atomicAdd(&S[sh_pb[i * W + me]].st, 0ull - (mytag << K_BITS));
+            if (i < nfree) atomicAdd(&SV(sh_pb[i * W + me]).st, 0ull - (mytag << K_BITS));
           if (len > PB) {
             c = (int32_t)sh_pb[(PB - 1) * W + me];
             rh = h;
@@ -371,7 +385,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
         case P_EDGE: {
           CNT(CNT_EDGE);
           ++deps;
-          S[h].nxt = (uint32_t)t;
+          SV(h).nxt = (uint32_t)t;
           if (!nb) {
             atomicAdd(p.R + (size_t)a * n + h, 1u);
             if (p.C != nullptr && kx == 0u) atomicAdd(p.C + (size_t)a * n + h, 1u);
@@ -386,13 +400,13 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
           // cycle x -> ... -> h -> x: free every vertex but x at its next entry
           CNT(CNT_POP);
           if (!rskip) {
-            atomicAdd(&S[c].st, 1ull - (mytag << K_BITS));
+            atomicAdd(&SV(c).st, 1ull - (mytag << K_BITS));
             ++pops;
           }
           rskip = false;
           c = (int32_t)nc;
           if (c == x) {
-            atomicAdd(&S[x].st, 1ull);
+            atomicAdd(&SV(x).st, 1ull);
             ++pops;
             ++kx;
             if (kx >= (uint32_t)K_MASK) {
@@ -412,14 +426,14 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
           break;
         }
         case P_RETRACE: {
-          if (!rskip) atomicOr(bits + (c >> 5), 1u << (c & 31));
+          if (!rskip) atomicOr(&BW(c >> 5), 1u << (c & 31));
           rskip = false;
           if (c == rh) mode = P_IDLE;
           else c = (int32_t)nc;
           break;
         }
         case P_RELEASE: {
-          atomicAdd(&S[c].st, 0ull - (mytag << K_BITS));
+          atomicAdd(&SV(c).st, 0ull - (mytag << K_BITS));
           if (c == rh) mode = P_WAIT;
           else c = (int32_t)nc;
           break;
@@ -447,7 +461,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
           for (int i = 0; i < PB; ++i)
             if (i < len) {
               const uint32_t v = sh_pb[i * W + me];
-              atomicOr(bits + (v >> 5), 1u << (v & 31));
+              atomicOr(&BW(v >> 5), 1u << (v & 31));
             }
           if (len > PB) {
             c = (int32_t)sh_pb[(PB - 1) * W + me];
@@ -479,7 +493,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
     __syncthreads();
     if (p.parents != nullptr) {
       int32_t* par = p.parents + (size_t)tree * n;
-      for (int32_t v = me; v < n; v += W) par[v] = (int32_t)S[v].nxt;
+      for (int32_t v = me; v < n; v += W) par[v] = (int32_t)SV(v).nxt;
     }
     if (me == 0) {
       if (p.steps != nullptr) p.steps[tree] = (uint64_t)n + sh_pops;
@@ -489,6 +503,9 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
     __syncthreads();
   }
 }
+
+#undef SV
+#undef BW
 
 __global__ void k_stack_entries(WParams p, int a, uint32_t tg, int64_t count, const int32_t* __restrict__ verts,
                                 const uint32_t* __restrict__ ks, int32_t* __restrict__ out) {
@@ -653,6 +670,13 @@ extern "C" fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int
   {
     const uint64_t mi = max_steps_per_tree ? max_steps_per_tree : (uint64_t)8 * (uint64_t)n + (1ull << 20);
     p.max_iters = (uint32_t)std::min<uint64_t>(mi, 0xffffffffull);
+  }
+  p.pre_cleared = 0;
+  if (!use_smem) {
+    // clear the state and bitmaps of the first wave in one pass
+    const size_t words = ((size_t)n + 31) / 32;
+    FC_CK(cudaMemsetAsync(gstate, 0, (size_t)grid * n * sizeof(VState) + (size_t)grid * words * 4, st));
+    p.pre_cleared = 1;
   }
   FC_CK(cudaMemsetAsync(g->d_counter, 0, sizeof(unsigned long long), st));
   FC_CK(cudaMemsetAsync(g->d_err, 0, sizeof(uint32_t), st));
