@@ -78,6 +78,36 @@ fc_status fc_build_augmented(int32_t n, int64_t nnz, const int64_t* rowptr, cons
                              const float* w, const double* alphas, int32_t n_alpha, uint32_t flags,
                              void* stream, fc_graph** out);
 
+/*
+ * A batch of graphs sampled together (one persistent launch): the graphs are
+ * given as one block-diagonal CSR over n = vertex_offsets[num_graphs] vertices
+ * (graph i owns vertices [vertex_offsets[i], vertex_offsets[i+1]); no edge may
+ * leave its graph -- FC_EINVAL otherwise), each with its own alpha
+ * (graph_alphas[i], host).  vertex_offsets is a host array of num_graphs + 1
+ * entries starting at 0, every graph non-empty.  Because G* of the union is
+ * the union of the graphs' G* glued at u*, a spanning tree of it is one tree
+ * per graph, and all the per-vertex entry points below apply unchanged with
+ * vertex ids of the union, alpha index 0:
+ *   fc_sample_usts   samples tau trees of every graph: work items (graph,
+ *                    tree) run largest graph first; steps_out is [graph][tree];
+ *                    parents is [tree][n]; the random stacks use union vertex
+ *                    ids, so results equal those of the union graph.
+ *   fc_forest_farness  Eq. 3 and Def. 2 within each graph (its n and trace).
+ *   fc_batch_latency   per-graph completion time of the last launch.
+ * Other arguments as fc_build_augmented.  Synchronises `stream`.
+ */
+fc_status fc_build_batch(int32_t num_graphs, const int64_t* vertex_offsets, int64_t nnz, const int64_t* rowptr,
+                         const int32_t* colidx, const float* w, const double* graph_alphas, uint32_t flags,
+                         void* stream, fc_graph** out);
+
+/*
+ * Per-graph latency of the last fc_sample_usts on a batch graph: for graph i,
+ * the time from the first CTA start of the launch to the completion of the
+ * graph's last tree, in ms (%globaltimer).  per_graph_ms: host double[G].
+ * Synchronous.
+ */
+fc_status fc_batch_latency(fc_graph* g, double* per_graph_ms);
+
 /* Graph metadata (host pointers; any may be NULL). */
 fc_status fc_graph_info(const fc_graph* g, int32_t* n, int64_t* nnz, int32_t* n_alpha,
                         int32_t* weighted);
@@ -197,7 +227,8 @@ fc_status fc_forest_farness(fc_graph* g, int32_t alpha_idx, const uint32_t* R, c
  * the process exits).  It calls no cudaMalloc/cudaFree or other allocating
  * routine.  The paper has no counterpart: this is an engineering variant.
  *   - n must be <= 4194304 (2^22); larger graphs get FC_EINVAL.
- *   - The graph's device must be the current device.
+ *   - The graph's device must be the current device; batches of graphs
+ *     (fc_build_batch) are rejected with FC_EINVAL.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) and caches it; make that first call before any
  *     stream capture begins.

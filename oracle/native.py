@@ -38,6 +38,9 @@ def lib():
         L.orc_wilson.argtypes = [ctypes.c_int32, P, P, P, ctypes.c_double, ctypes.c_uint32,
                                  ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P]
         L.orc_wilson.restype = ctypes.c_int
+        L.orc_wilson_v.argtypes = [ctypes.c_int32, P, P, P, ctypes.c_double, P, ctypes.c_uint32,
+                                   ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P]
+        L.orc_wilson_v.restype = ctypes.c_int
         L.orc_philox_batch.argtypes = [ctypes.c_int64, P, ctypes.c_uint64, P]
         L.orc_philox_batch.restype = None
         L.orc_row_prefix.argtypes = [ctypes.c_int32, P, P, P]
@@ -87,10 +90,11 @@ def stack_entries(g, alpha: float, seed: int, tree: int, verts, ks, alpha_idx: i
     return out
 
 
-def wilson(g, alpha: float, seed: int, tau: int, tree_offset: int = 0, alpha_idx: int = 0,
+def wilson(g, alpha, seed: int, tau: int, tree_offset: int = 0, alpha_idx: int = 0,
            order=None, want_parents: bool = False, want_C: bool = True, want_steps: bool = True):
-    """Sequential Wilson sampler on G* (Algorithm 2).  Returns dict with R, C,
-    parents ([tau, n], n = u*) and steps ([tau])."""
+    """Sequential Wilson sampler on G* (Algorithm 2).  ``alpha`` is a float or a
+    per-vertex array (a batch of graphs as one block-diagonal union).  Returns
+    dict with R, C, parents ([tau, n], n = u*) and steps ([tau])."""
     n = g.n
     R = np.zeros(n, dtype=np.uint32)
     C = np.zeros(n, dtype=np.uint32) if want_C else None
@@ -98,9 +102,14 @@ def wilson(g, alpha: float, seed: int, tau: int, tree_offset: int = 0, alpha_idx
     steps = np.zeros(tau, dtype=np.uint64) if want_steps else None
     w = None if g.w is None else np.ascontiguousarray(g.w, dtype=np.float32)
     order_arr = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
-    rc = lib().orc_wilson(n, _ptr(g.rowptr), _ptr(g.colidx), _ptr(w), float(alpha), int(alpha_idx),
-                          int(seed) & (2**64 - 1), int(tree_offset), int(tau), _ptr(order_arr),
-                          _ptr(R), _ptr(C), _ptr(parents), _ptr(steps))
+    av = None
+    if np.ndim(alpha) > 0:
+        av = np.ascontiguousarray(alpha, dtype=np.float64)
+        assert av.size == n
+        alpha = 0.0
+    rc = lib().orc_wilson_v(n, _ptr(g.rowptr), _ptr(g.colidx), _ptr(w), float(alpha), _ptr(av), int(alpha_idx),
+                            int(seed) & (2**64 - 1), int(tree_offset), int(tau), _ptr(order_arr),
+                            _ptr(R), _ptr(C), _ptr(parents), _ptr(steps))
     if rc != 0:
         raise MemoryError("oracle sampler allocation failed")
     return {"R": R, "C": C, "parents": parents, "steps": steps}

@@ -70,6 +70,7 @@ typedef struct {
     const int32_t* colidx;
     const double* S;      /* per-nnz FP64 prefix of the row's weights, or NULL */
     double alpha;
+    const double* alpha_v; /* per-vertex alpha (a batch of graphs as one union), or NULL */
     uint32_t alpha_idx;
     uint32_t key[2];
 } orc_graph;
@@ -86,24 +87,25 @@ static int32_t stack_entry(const orc_graph* g, int32_t v, uint32_t k, uint32_t t
     orc_philox4x32_10(ctr, g->key, o);
     const int64_t b = g->rowptr[v];
     const int64_t d = g->rowptr[v + 1] - b;
+    const double alpha = g->alpha_v ? g->alpha_v[v] : g->alpha;
     int64_t slot;
     const uint64_t u53 = ((uint64_t)o[0] << 21) | (uint64_t)(o[1] >> 11);
     const double U = (double)u53 * 0x1.0p-53;
     if (g->S == NULL) {
-        const double t = 1.0 + g->alpha * (double)d;
+        const double t = 1.0 + alpha * (double)d;
         double x = U * t;
         if (x >= t) x = below(t);
         if (x < 1.0) slot = 0;
         else slot = 1 + (int64_t)(((uint64_t)o[2] * (uint64_t)d) >> 32);
     } else {
-        const double t_last = d > 0 ? 1.0 + g->alpha * g->S[b + d - 1] : 1.0;
+        const double t_last = d > 0 ? 1.0 + alpha * g->S[b + d - 1] : 1.0;
         double x = U * t_last;
         if (x >= t_last) x = below(t_last);
         slot = 0;
         if (!(x < 1.0)) {
             slot = d; /* fallback; the loop below always finds a smaller j */
             for (int64_t j = 1; j <= d; ++j) {
-                const double tj = 1.0 + g->alpha * g->S[b + j - 1];
+                const double tj = 1.0 + alpha * g->S[b + j - 1];
                 if (x < tj) { slot = j; break; }
             }
         }
@@ -146,12 +148,29 @@ void orc_row_prefix(int32_t n, const int64_t* rowptr, const float* w, double* S)
  *   order      start-vertex order, NULL = ascending degree
  * Returns 0 on success, -1 on allocation failure.
  */
+int orc_wilson_v(int32_t n, const int64_t* rowptr, const int32_t* colidx, const float* w,
+                 double alpha, const double* alpha_v, uint32_t alpha_idx, uint64_t seed,
+                 int64_t tree_offset, int64_t tau, const int32_t* order_in, uint32_t* R, uint32_t* C,
+                 int32_t* parents, uint64_t* steps);
+
 int orc_wilson(int32_t n, const int64_t* rowptr, const int32_t* colidx, const float* w,
                double alpha, uint32_t alpha_idx, uint64_t seed, int64_t tree_offset,
                int64_t tau, const int32_t* order_in, uint32_t* R, uint32_t* C,
                int32_t* parents, uint64_t* steps) {
+    return orc_wilson_v(n, rowptr, colidx, w, alpha, NULL, alpha_idx, seed, tree_offset, tau,
+                        order_in, R, C, parents, steps);
+}
+
+/* As orc_wilson with an optional per-vertex alpha (alpha_v != NULL overrides
+ * alpha): a batch of graphs given as one block-diagonal union, each vertex
+ * carrying its own graph's alpha. */
+int orc_wilson_v(int32_t n, const int64_t* rowptr, const int32_t* colidx, const float* w,
+                 double alpha, const double* alpha_v, uint32_t alpha_idx, uint64_t seed,
+                 int64_t tree_offset, int64_t tau, const int32_t* order_in, uint32_t* R, uint32_t* C,
+                 int32_t* parents, uint64_t* steps) {
     orc_graph g;
     g.n = n; g.rowptr = rowptr; g.colidx = colidx; g.alpha = alpha; g.alpha_idx = alpha_idx;
+    g.alpha_v = alpha_v;
     g.key[0] = (uint32_t)seed; g.key[1] = (uint32_t)(seed >> 32);
     g.S = NULL;
     double* S = NULL;
@@ -240,6 +259,7 @@ int orc_stack_entries(int32_t n, const int64_t* rowptr, const int32_t* colidx, c
                       int64_t count, const int32_t* verts, const uint32_t* ks, int32_t* out) {
     orc_graph g;
     g.n = n; g.rowptr = rowptr; g.colidx = colidx; g.alpha = alpha; g.alpha_idx = alpha_idx;
+    g.alpha_v = NULL;
     g.key[0] = (uint32_t)seed; g.key[1] = (uint32_t)(seed >> 32);
     g.S = NULL;
     double* S = NULL;

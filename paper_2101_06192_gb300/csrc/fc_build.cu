@@ -2,6 +2,7 @@
 // FP64 weight prefixes, ascending-degree start order (Algorithm 2) and the
 // integer thresholds of the random-stack selector.  Also the shared error
 // plumbing and the small graph-management entry points of the C ABI.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <atomic>
@@ -68,7 +69,7 @@ fc_status cuda_fail(cudaError_t e, const char* what) {
 // ---------------------------------------------------------------------------
 __global__ void k_validate(int32_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
                            const int32_t* __restrict__ colidx, const float* __restrict__ w,
-                           uint32_t* err) {
+                           const int32_t* __restrict__ gid, uint32_t* err) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -85,6 +86,7 @@ __global__ void k_validate(int32_t n, int64_t nnz, const int64_t* __restrict__ r
     for (int64_t i = b + lane; i < e; i += 32) {
       const int32_t c = colidx[i];
       bool ok = c >= 0 && c < n && c != v;
+      if (ok && gid != nullptr && gid[c] != gid[v]) ok = false;  // batch: edges stay in their graph
       if (ok && i > b && colidx[i - 1] >= c) ok = false;  // sorted, no duplicates
       float wv = 1.0f;
       if (ok && w != nullptr) {
@@ -266,11 +268,12 @@ __global__ void k_iota_keys(int32_t n, const int32_t* __restrict__ deg, uint32_t
 //   B_e = count_below(t_j, t_v) for the entry e of slot j (weighted rows),
 // with t_v = fl(1 + fl(alpha s_v)), s_v = d_v (unweighted) or d_w(v) (weighted).
 // ---------------------------------------------------------------------------
-__global__ void k_thr_vertex(int32_t n, double alpha, bool weighted, const int64_t* __restrict__ rowptr,
-                             const int32_t* __restrict__ deg, const double* __restrict__ dw,
-                             uint4* __restrict__ rowinfo) {
+__global__ void k_thr_vertex(int32_t n, double alpha_s, const double* __restrict__ alpha_v, bool weighted,
+                             const int64_t* __restrict__ rowptr, const int32_t* __restrict__ deg,
+                             const double* __restrict__ dw, uint4* __restrict__ rowinfo) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
+    const double alpha = alpha_v ? alpha_v[v] : alpha_s;
     const int32_t d = deg[v];
     const double t = deg_star(alpha, weighted ? dw[v] : (double)d);
     const uint64_t T = count_below(1.0, t);
@@ -278,17 +281,41 @@ __global__ void k_thr_vertex(int32_t n, double alpha, bool weighted, const int64
   }
 }
 
-__global__ void k_thr_nnz(int32_t n, double alpha, const int64_t* __restrict__ rowptr,
-                          const double* __restrict__ S, const double* __restrict__ dw,
-                          uint64_t* __restrict__ B) {
+__global__ void k_thr_nnz(int32_t n, double alpha_s, const double* __restrict__ alpha_v,
+                          const int64_t* __restrict__ rowptr, const double* __restrict__ S,
+                          const double* __restrict__ dw, uint64_t* __restrict__ B) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t v = warp; v < n; v += nwarps) {
+    const double alpha = alpha_v ? alpha_v[v] : alpha_s;
     const double t = deg_star(alpha, dw[v]);
     for (int64_t e = rowptr[v] + lane; e < rowptr[v + 1]; e += 32)
       B[e] = count_below(deg_star(alpha, S[e]), t);
   }
+}
+
+// graph of each vertex (binary search over the vertex offsets) and its alpha
+__global__ void k_batch_vertex(int32_t n, int32_t G, const int64_t* __restrict__ voff,
+                               const double* __restrict__ galpha, int32_t* __restrict__ gid,
+                               double* __restrict__ alpha_v, uint32_t* __restrict__ keys) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t lo = 0, hi = G - 1;
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (voff[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    gid[v] = lo;
+    alpha_v[v] = galpha[lo];
+  }
+  (void)keys;
+}
+
+// keys[i] = graph of order[i] (second, stable sort pass of the batch start order)
+__global__ void k_gid_keys(int32_t n, const int32_t* __restrict__ order, const int32_t* __restrict__ gid,
+                           uint32_t* __restrict__ keys) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    keys[i] = (uint32_t)gid[order[i]];
 }
 
 static int grid_for(int64_t items, int threads) {
@@ -300,7 +327,8 @@ static int grid_for(int64_t items, int threads) {
 
 static void free_graph_arrays(fc_graph* g, cudaStream_t st) {
   void* ptrs[] = {g->rowptr, g->colidx, g->w, g->deg, g->dw, g->S, g->order, g->rowinfo, g->B,
-                  g->alphas_d, g->d_err, g->d_counter, g->d_stats};
+                  g->alphas_d, g->d_err, g->d_counter, g->d_stats, g->voff, g->gid, g->alpha_v,
+                  g->gorder, g->item_ns, g->t0_ns};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, st);
   if (g->ws) cudaFree(g->ws);
@@ -352,9 +380,9 @@ extern "C" fc_status fc_release_scratch(void) {
     }                                                    \
   } while (0)
 
-extern "C" fc_status fc_build_augmented(int32_t n, int64_t nnz, const int64_t* rowptr,
-                                        const int32_t* colidx, const float* w, const double* alphas,
-                                        int32_t n_alpha, uint32_t flags, void* stream, fc_graph** out) {
+static fc_status build_impl(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
+                            const float* w, const double* alphas, int32_t n_alpha, uint32_t flags, void* stream,
+                            fc_graph** out, int32_t G, const int64_t* voff_h, const double* galpha_h) {
   if (out == nullptr) return FC_EINVAL;
   *out = nullptr;
   if (n < 1 || n >= (1 << 30) || nnz < 0 || nnz >= (int64_t(1) << 32) || n_alpha < 1 || n_alpha > 64 ||
@@ -378,6 +406,34 @@ extern "C" fc_status fc_build_augmented(int32_t n, int64_t nnz, const int64_t* r
   g->alphas.assign(alphas, alphas + n_alpha);
   BUILD_CK(cudaGetDevice(&g->device));
   retain_pool(g->device);
+  if (G > 0) {
+    g->num_graphs = G;
+    g->voff_h.assign(voff_h, voff_h + G + 1);
+    g->galpha.assign(galpha_h, galpha_h + G);
+    std::vector<int32_t> ord(G);
+    for (int i = 0; i < G; ++i) {
+      ord[i] = i;
+      g->max_ng = std::max<int32_t>(g->max_ng, (int32_t)(voff_h[i + 1] - voff_h[i]));
+    }
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+      return (voff_h[a + 1] - voff_h[a]) > (voff_h[b + 1] - voff_h[b]);
+    });
+    BUILD_CK(cudaMallocAsync((void**)&g->voff, (G + 1) * sizeof(int64_t), st));
+    BUILD_CK(cudaMallocAsync((void**)&g->gorder, G * sizeof(int32_t), st));
+    BUILD_CK(cudaMallocAsync((void**)&g->gid, (size_t)n * sizeof(int32_t), st));
+    BUILD_CK(cudaMallocAsync((void**)&g->alpha_v, (size_t)n * sizeof(double), st));
+    BUILD_CK(cudaMallocAsync((void**)&g->t0_ns, sizeof(unsigned long long), st));
+    double* galpha_d = nullptr;
+    BUILD_CK(cudaMallocAsync((void**)&galpha_d, G * sizeof(double), st));
+    BUILD_CK(cudaMemcpyAsync(g->voff, voff_h, (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    BUILD_CK(cudaMemcpyAsync(g->gorder, ord.data(), G * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    BUILD_CK(cudaMemcpyAsync(galpha_d, galpha_h, G * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_batch_vertex<<<grid_for(n, 256), 256, 0, st>>>(n, G, g->voff, galpha_d, g->gid, g->alpha_v, nullptr);
+    BUILD_CK((fcx::note_launch(), cudaGetLastError()));
+    BUILD_CK(cudaFreeAsync(galpha_d, st));
+    // ord must outlive the async copy
+    BUILD_CK(cudaStreamSynchronize(st));
+  }
   const size_t nz = (size_t)(nnz > 0 ? nnz : 1);
   BUILD_CK(cudaMallocAsync((void**)&g->rowptr, (n + 1) * sizeof(int64_t), st));
   BUILD_CK(cudaMallocAsync((void**)&g->colidx, nz * sizeof(int32_t), st));
@@ -402,7 +458,8 @@ extern "C" fc_status fc_build_augmented(int32_t n, int64_t nnz, const int64_t* r
   BUILD_CK(cudaMemcpyAsync(g->alphas_d, alphas, n_alpha * sizeof(double), cudaMemcpyHostToDevice, st));
   BUILD_CK(cudaMemsetAsync(g->d_err, 0, 4 * sizeof(uint32_t), st));
 
-  k_validate<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(n, nnz, g->rowptr, g->colidx, g->w, g->d_err);
+  k_validate<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(n, nnz, g->rowptr, g->colidx, g->w, g->gid,
+                                                              g->d_err);
   BUILD_CK((fcx::note_launch(), cudaGetLastError()));
   uint32_t hs[4] = {0, 0, 0, 0};
   BUILD_CK(cudaMemcpyAsync(hs, g->d_err, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -456,6 +513,25 @@ extern "C" fc_status fc_build_augmented(int32_t n, int64_t nnz, const int64_t* r
       std::swap(kin, kout);
       std::swap(vin, vout);
     }
+    if (g->num_graphs > 0) {
+      // second stable pass: by graph, so each graph's start vertices are contiguous
+      k_gid_keys<<<grid_for(n, 256), 256, 0, st>>>(n, vin, g->gid, kin);
+      BUILD_CK((fcx::note_launch(), cudaGetLastError()));
+      for (int pass = 0; pass < 4 && ((uint32_t)(g->num_graphs - 1) >> (8 * pass)); ++pass) {
+        k_rs_hist<<<nblk, 32, 0, st>>>(n, kin, 8 * pass, hist, nblk);
+        BUILD_CK((fcx::note_launch(), cudaGetLastError()));
+        fc_status r = exclusive_scan(hist, offs, (int64_t)256 * nblk, st);
+        if (r != FC_OK) {
+          free_graph_arrays(g, st);
+          delete g;
+          return r;
+        }
+        k_rs_scatter<<<nblk, 32, 0, st>>>(n, kin, vin, kout, vout, 8 * pass, offs, nblk);
+        BUILD_CK((fcx::note_launch(), cudaGetLastError()));
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+      }
+    }
     if (vin != g->order)
       BUILD_CK(cudaMemcpyAsync(g->order, vin, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     BUILD_CK(cudaFreeAsync(k0, st));
@@ -466,18 +542,49 @@ extern "C" fc_status fc_build_augmented(int32_t n, int64_t nnz, const int64_t* r
   }
 
   for (int a = 0; a < n_alpha; ++a) {
-    k_thr_vertex<<<grid_for(n, 256), 256, 0, st>>>(n, g->alphas[a], g->weighted, g->rowptr, g->deg,
-                                                   g->dw, g->rowinfo + (size_t)a * n);
+    k_thr_vertex<<<grid_for(n, 256), 256, 0, st>>>(n, g->alphas[a], g->alpha_v, g->weighted, g->rowptr,
+                                                   g->deg, g->dw, g->rowinfo + (size_t)a * n);
     BUILD_CK((fcx::note_launch(), cudaGetLastError()));
     if (g->weighted && nnz > 0) {
-      k_thr_nnz<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(n, g->alphas[a], g->rowptr, g->S, g->dw,
-                                                                g->B + (size_t)a * nnz);
+      k_thr_nnz<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(n, g->alphas[a], g->alpha_v, g->rowptr, g->S,
+                                                                g->dw, g->B + (size_t)a * nnz);
       BUILD_CK((fcx::note_launch(), cudaGetLastError()));
     }
   }
   BUILD_CK(cudaStreamSynchronize(st));
   *out = g;
   return FC_OK;
+}
+
+extern "C" fc_status fc_build_augmented(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
+                                        const float* w, const double* alphas, int32_t n_alpha, uint32_t flags,
+                                        void* stream, fc_graph** out) {
+  return build_impl(n, nnz, rowptr, colidx, w, alphas, n_alpha, flags, stream, out, 0, nullptr, nullptr);
+}
+
+extern "C" fc_status fc_build_batch(int32_t num_graphs, const int64_t* vertex_offsets, int64_t nnz,
+                                    const int64_t* rowptr, const int32_t* colidx, const float* w,
+                                    const double* graph_alphas, uint32_t flags, void* stream, fc_graph** out) {
+  if (out == nullptr) return FC_EINVAL;
+  *out = nullptr;
+  if (num_graphs < 1 || vertex_offsets == nullptr || graph_alphas == nullptr || vertex_offsets[0] != 0) {
+    set_error("fc_build_batch: bad argument");
+    return FC_EINVAL;
+  }
+  for (int32_t i = 0; i < num_graphs; ++i) {
+    if (vertex_offsets[i + 1] <= vertex_offsets[i] || !(std::isfinite(graph_alphas[i]) && graph_alphas[i] > 0.0)) {
+      set_error("fc_build_batch: graphs must be non-empty and alphas finite and > 0");
+      return FC_EINVAL;
+    }
+  }
+  const int64_t n = vertex_offsets[num_graphs];
+  if (n >= (1 << 30)) {
+    set_error("fc_build_batch: too many vertices");
+    return FC_EINVAL;
+  }
+  const double one = 1.0;
+  return build_impl((int32_t)n, nnz, rowptr, colidx, w, &one, 1, flags, stream, out, num_graphs, vertex_offsets,
+                    graph_alphas);
 }
 
 extern "C" fc_status fc_graph_info(const fc_graph* g, int32_t* n, int64_t* nnz, int32_t* n_alpha,

@@ -75,6 +75,35 @@ __global__ void k_farness(int32_t n, const double* __restrict__ diag, const doub
   if (closeness) closeness[v] = (double)n / f;         // Def. 2
 }
 
+// Batch of graphs: per-graph trace (one block per graph, fixed order) and
+// farness with that graph's n and trace.
+__global__ void k_seg_trace(const int64_t* __restrict__ voff, const double* __restrict__ diag,
+                            double* __restrict__ tr) {
+  __shared__ double red[RED_THREADS];
+  const int gi = blockIdx.x;
+  double s = 0.0;
+  for (int64_t v = voff[gi] + threadIdx.x; v < voff[gi + 1]; v += RED_THREADS) s += diag[v];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = RED_THREADS / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tr[gi] = red[0];
+}
+
+__global__ void k_farness_seg(int32_t n, const int32_t* __restrict__ gid, const int64_t* __restrict__ voff,
+                              const double* __restrict__ diag, const double* __restrict__ tr,
+                              double* __restrict__ farness, double* __restrict__ closeness) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const int32_t gi = gid[v];
+  const double ng = (double)(voff[gi + 1] - voff[gi]);
+  const double f = ng * diag[v] + tr[gi] - 2.0;  // Eq. 3 within the graph
+  if (farness) farness[v] = f;
+  if (closeness) closeness[v] = ng / f;          // Def. 2
+}
+
 __global__ void k_p_root(int32_t n, const uint4* __restrict__ rinfo, double* __restrict__ p) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v < n) p[v] = p_from_rowinfo(rinfo[v]);
@@ -174,6 +203,20 @@ extern "C" fc_status fc_forest_farness(fc_graph* g, int32_t alpha_idx, const uin
   k_combine<<<(unsigned)nb, RED_THREADS, 0, st>>>(n, R, C, g_pred, rinfo, x_pivot, 1.0 / (double)tau, diag_out,
                                                   partial);
   FC_LAUNCHED();
+  if (g->num_graphs > 0) {
+    double* tr = nullptr;
+    FC_CK(cudaMallocAsync((void**)&tr, (size_t)g->num_graphs * sizeof(double), st));
+    k_seg_trace<<<g->num_graphs, RED_THREADS, 0, st>>>(g->voff, diag_out, tr);
+    FC_LAUNCHED();
+    if (farness_out || closeness_out) {
+      k_farness_seg<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, g->gid, g->voff, diag_out, tr, farness_out,
+                                                                 closeness_out);
+      FC_LAUNCHED();
+    }
+    FC_CK(cudaFreeAsync(tr, st));
+    FC_CK(cudaFreeAsync(partial, st));
+    return FC_OK;
+  }
   k_sum_partials<<<1, 1024, 0, st>>>(partial, nb, partial + nb);
   FC_LAUNCHED();
   if (farness_out || closeness_out) {
@@ -274,6 +317,10 @@ extern "C" fc_status fc_forest_farness_noalloc(fc_graph* g, int32_t alpha_idx, c
   if (g == nullptr || R == nullptr || diag_out == nullptr || tau < 1 || alpha_idx < 0 ||
       alpha_idx >= g->n_alpha || ((C == nullptr) != (g_pred == nullptr))) {
     set_error("fc_forest_farness_noalloc: bad argument");
+    return FC_EINVAL;
+  }
+  if (g->num_graphs > 0) {
+    set_error("fc_forest_farness_noalloc: batches of graphs need per-graph traces; use fc_forest_farness");
     return FC_EINVAL;
   }
   if (g->n > NOALLOC_MAX_N) {

@@ -159,6 +159,19 @@ struct fc_graph {
   uint64_t* B = nullptr;       // [n_alpha][nnz] slot thresholds (weighted only)
   double* alphas_d = nullptr;  // [n_alpha]
   int32_t max_deg = 0;
+  // batch of graphs (block-diagonal union with one alpha per graph)
+  int32_t num_graphs = 0;      // 0 = a single graph
+  int64_t* voff = nullptr;     // [G+1] vertex offsets
+  int32_t* gid = nullptr;      // [n] graph of each vertex
+  double* alpha_v = nullptr;   // [n] alpha of each vertex's graph
+  int32_t* gorder = nullptr;   // [G] graphs by decreasing size (work order)
+  int32_t max_ng = 0;          // largest graph
+  std::vector<int64_t> voff_h;
+  std::vector<double> galpha;
+  unsigned long long* item_ns = nullptr;  // [G * tau_last] completion times of the last launch
+  size_t item_cap = 0;
+  int64_t last_tau = 0;
+  unsigned long long* t0_ns = nullptr;    // earliest CTA start of the last launch
   // sampler shape
   int32_t walkers = 0;
   int32_t max_trees = 0;

@@ -38,9 +38,10 @@ __device__ __forceinline__ double p_of(const uint4& ri) {
 
 // sum over neighbours of their degree, RG lanes per row
 constexpr int FG = 8;
-__global__ void k_features(int32_t n, double alpha, const int64_t* __restrict__ rowptr,
-                           const int32_t* __restrict__ colidx, const int32_t* __restrict__ deg,
-                           const double* __restrict__ dw, float4* __restrict__ X) {
+__global__ void k_features(int32_t n, double alpha_s, const double* __restrict__ alpha_v,
+                           const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                           const int32_t* __restrict__ deg, const double* __restrict__ dw,
+                           float4* __restrict__ X) {
   const int gl = threadIdx.x % FG;
   const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / FG;
   double s2 = 0.0;
@@ -49,6 +50,7 @@ __global__ void k_features(int32_t n, double alpha, const int64_t* __restrict__ 
 #pragma unroll
   for (int o = FG / 2; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
   if (v < n && gl == 0) {
+    const double alpha = alpha_v ? alpha_v[v] : alpha_s;
     X[v] = make_float4((float)log1p((double)deg[v]), (float)log1p(alpha * dw[v]), (float)log1p(s2),
                        (float)log(alpha));
   }
@@ -207,8 +209,9 @@ extern "C" fc_status fc_vertex_features(fc_graph* g, int32_t alpha_idx, float* X
   }
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t threads = (int64_t)g->n * FG;
-  k_features<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g->n, g->alphas[alpha_idx], g->rowptr,
-                                                                g->colidx, g->deg, g->dw, (float4*)X);
+  k_features<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g->n, g->alphas[alpha_idx], g->alpha_v,
+                                                                g->rowptr, g->colidx, g->deg, g->dw,
+                                                                (float4*)X);
   FC_LAUNCHED();
   return FC_OK;
 }

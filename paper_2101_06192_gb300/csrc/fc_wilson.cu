@@ -62,14 +62,27 @@ struct WParams {
   uint64_t* steps;          // [n_alpha*tau] or null
   VState* gstate;           // [gridDim.x][n] (global-state variant)
   uint32_t* gbits;          // [gridDim.x][words] in-tree bitmaps (global-state variant)
-  int32_t words;            // bitmap words per tree: ceil(n / 32)
+  int32_t words;            // bitmap words per tree: ceil(nmax / 32)
+  int32_t nmax;             // vertices of the largest tree of the launch (state records per CTA)
   int pre_cleared;          // the first tree of every CTA starts from host-cleared state
   unsigned long long* counter;
   uint32_t* err;
   unsigned long long* stats;  // [0] pops, [1] departures, [2..] iteration counters (N_CNT)
   uint32_t max_iters;
   int descending;           // take start vertices from the high-degree end
+  // batch of graphs: work item i samples tree (i % tau) of graph gorder[i / tau]
+  int32_t num_graphs;       // 0 = single graph
+  const int64_t* voff;      // [G+1]
+  const int32_t* gorder;    // [G] graphs by decreasing size
+  unsigned long long* item_ns;  // [G*tau] %globaltimer at completion, indexed graph-major (or null)
+  unsigned long long* t0_ns;    // earliest CTA start (or null)
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // Iteration counters (diagnostic), summed over walkers and trees.
 enum { CNT_ITER = 0, CNT_CLAIM_OK, CNT_TREE_HIT, CNT_CONFIRM, CNT_SPIN, CNT_WAIT, CNT_RELEASE, CNT_POP,
@@ -155,36 +168,48 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
   const unsigned lt_mask = (1u << lane) - 1u;
   volatile uint32_t* sh_gen = (volatile uint32_t*)smem_raw;
   uint32_t* sh_pb = (uint32_t*)(smem_raw + (size_t)W * 4);  // [PB][W] path prefix of each walker
-  const int32_t n = p.n;
+  const int32_t n = p.n;  // u* = n (global numbering)
   const int32_t words = p.words;
+  if (p.t0_ns != nullptr && threadIdx.x == 0) atomicMin(p.t0_ns, global_ns());
   // Tree-major state: each CTA's trees use their own contiguous column.  (A
   // vertex-major layout, which lets trees share lines at common start
   // vertices, measured slower: atomics from many SMs then meet on one line.)
   VState* S;
   uint32_t* bits;
   if (SMEM) {
-    unsigned char* base = smem_raw + (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15);
-    S = (VState*)base;
-    bits = (uint32_t*)(base + (size_t)n * sizeof(VState));
+    unsigned char* sbase = smem_raw + (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15);
+    S = (VState*)sbase;
+    bits = (uint32_t*)(sbase + (size_t)p.nmax * sizeof(VState));
   } else {
-    S = p.gstate + (size_t)blockIdx.x * n;
+    S = p.gstate + (size_t)blockIdx.x * p.nmax;
     bits = p.gbits + (size_t)blockIdx.x * words;
   }
-#define SV(v) S[(v)]
-#define BW(q) bits[(q)]
+#define SV(v) S[(v) - base]
+#define BWV(v) bits[((v) - base) >> 5]
+#define BITV(v) (1u << (((v) - base) & 31))
   bool first_tree = true;
-  const int64_t total = (int64_t)p.n_alpha * p.tau;
+  const int64_t total = (int64_t)(p.num_graphs > 0 ? p.num_graphs : p.n_alpha) * p.tau;
 
   for (;;) {
     if (me == 0) sh_tree = atomicAdd(p.counter, 1ull);
     __syncthreads();
     const unsigned long long tree = sh_tree;
     if ((int64_t)tree >= total || *(volatile uint32_t*)p.err != 0u) break;
-    const int a = (int)(tree / (unsigned long long)p.tau);
-    const uint32_t tg = (uint32_t)(p.tree_offset + (int64_t)(tree % (unsigned long long)p.tau));
+    // item -> (alpha index or graph, tree); the tree's vertices are [base, base + nl)
+    const unsigned long long tq = tree / (unsigned long long)p.tau;
+    const int64_t tloc = (int64_t)(tree % (unsigned long long)p.tau);
+    int a = (int)tq;
+    int32_t base = 0, nl = n, gi = 0;
+    if (p.num_graphs > 0) {
+      gi = p.gorder[tq];
+      a = 0;
+      base = (int32_t)p.voff[gi];
+      nl = (int32_t)(p.voff[gi + 1] - p.voff[gi]);
+    }
+    const uint32_t tg = (uint32_t)(p.tree_offset + tloc);
     if (!(first_tree && p.pre_cleared)) {
-      for (int32_t v = me; v < n; v += W) reinterpret_cast<uint4&>(SV(v)) = make_uint4(0u, 0u, 0u, 0u);
-      for (int32_t q = me; q < words; q += W) BW(q) = 0u;
+      for (int32_t v = me; v < nl; v += W) reinterpret_cast<uint4&>(S[v]) = make_uint4(0u, 0u, 0u, 0u);
+      for (int32_t q = me; q < ((nl + 31) >> 5); q += W) bits[q] = 0u;
     }
     first_tree = false;
     sh_gen[me] = 1u;
@@ -222,12 +247,12 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
       const unsigned want = __ballot_sync(FULL, need && !fin);
       if (want) {
         const int leader = __ffs(want) - 1;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(&sh_next, (uint32_t)__popc(want));
-        base = __shfl_sync(FULL, base, leader);
+        uint32_t ibase = 0;
+        if (lane == leader) ibase = atomicAdd(&sh_next, (uint32_t)__popc(want));
+        ibase = __shfl_sync(FULL, ibase, leader);
         if (need && !fin) {
-          sni = base + __popc(want & lt_mask);
-          sn = sni < (uint32_t)n ? __ldg(p.order + (p.descending ? (uint32_t)n - 1u - sni : sni)) : -1;
+          sni = ibase + __popc(want & lt_mask);
+          sn = sni < (uint32_t)nl ? __ldg(p.order + base + (p.descending ? (uint32_t)nl - 1u - sni : sni)) : -1;
           need = false;
         }
       }
@@ -247,6 +272,12 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
           mode = P_DONE;
           continue;
         }
+        if (sn < base || sn >= base + nl) {  // start order must stay inside the tree's vertex range
+          atomicOr(p.err, ERR_INVAL);
+          sh_abort = 1u;
+          mode = P_DONE;
+          continue;
+        }
         s = sn;
         x = s;
         h = -1;
@@ -263,9 +294,9 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
       // computed and its CSR target loaded speculatively alongside.
       bool hit = false;
       if (mode == P_CHECK) {
-        const uint32_t bw = ld_volatile32(&BW(x >> 5));
+        const uint32_t bw = ld_volatile32(&BWV(x));
         xr = __ldg(rinfo + x);
-        hit = (bw >> (x & 31)) & 1u;
+        hit = (bw & BITV(x)) != 0u;
         if (!hit) mode = P_CLAIM;
       }
       unsigned long long old = 0ull;
@@ -426,7 +457,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
           break;
         }
         case P_RETRACE: {
-          if (!rskip) atomicOr(&BW(c >> 5), 1u << (c & 31));
+          if (!rskip) atomicOr(&BWV(c), BITV(c));
           rskip = false;
           if (c == rh) mode = P_IDLE;
           else c = (int32_t)nc;
@@ -461,7 +492,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
           for (int i = 0; i < PB; ++i)
             if (i < len) {
               const uint32_t v = sh_pb[i * W + me];
-              atomicOr(&BW(v >> 5), 1u << (v & 31));
+              atomicOr(&BWV(v), BITV(v));
             }
           if (len > PB) {
             c = (int32_t)sh_pb[(PB - 1) * W + me];
@@ -491,12 +522,14 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
     }
 #endif
     __syncthreads();
+    const size_t item = (size_t)(p.num_graphs > 0 ? gi : a) * (size_t)p.tau + (size_t)tloc;
     if (p.parents != nullptr) {
-      int32_t* par = p.parents + (size_t)tree * n;
-      for (int32_t v = me; v < n; v += W) par[v] = (int32_t)SV(v).nxt;
+      int32_t* par = p.parents + (p.num_graphs > 0 ? (size_t)tloc : (size_t)tree) * n + base;
+      for (int32_t v = me; v < nl; v += W) par[v] = (int32_t)S[v].nxt;
     }
     if (me == 0) {
-      if (p.steps != nullptr) p.steps[tree] = (uint64_t)n + sh_pops;
+      if (p.steps != nullptr) p.steps[item] = (uint64_t)nl + sh_pops;
+      if (p.item_ns != nullptr) p.item_ns[item] = global_ns();
       atomicAdd(&p.stats[0], sh_pops);
       atomicAdd(&p.stats[1], sh_deps);
     }
@@ -505,7 +538,8 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
 }
 
 #undef SV
-#undef BW
+#undef BWV
+#undef BITV
 
 __global__ void k_stack_entries(WParams p, int a, uint32_t tg, int64_t count, const int32_t* __restrict__ verts,
                                 const uint32_t* __restrict__ ks, int32_t* __restrict__ out) {
@@ -551,8 +585,7 @@ struct Shape {
 // Launch shape: the largest walker count whose CTAs hold every tree of the
 // launch in one wave (trees of one launch take about equally long), else the
 // shape with the most walkers resident.  Walkers per tree are capped at n/8.
-static fc_status choose_shape(const fc_graph* g, int64_t total, bool smem, int nsm, Shape* out) {
-  const int32_t n = g->n;
+static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool smem, int nsm, Shape* out) {
   const int wcap = std::max(32, std::min(1024, (int)((n / 8) & ~31)));
   // measured on GB300 (BA n = 2^20, tau = 1024): the 40-register variant is
   // fastest; graphs with long walks prefer more walkers per tree, which the
@@ -608,9 +641,11 @@ extern "C" fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int
   int dev_smem_optin = 0, nsm = 0;
   FC_CK(cudaDeviceGetAttribute(&dev_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
   FC_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device));
-  const int64_t total = (int64_t)g->n_alpha * tau;
+  const bool batch = g->num_graphs > 0;
+  const int64_t total = (int64_t)(batch ? g->num_graphs : g->n_alpha) * tau;
+  const int32_t nmax = batch ? g->max_ng : n;  // largest tree of the launch
   const int wmin = g->walkers > 0 ? g->walkers : 32;
-  const bool fits = smem_bytes(wmin, n, true) + 64 <= (size_t)dev_smem_optin;
+  const bool fits = smem_bytes(wmin, nmax, true) + 64 <= (size_t)dev_smem_optin;
   const bool use_smem = g->smem_mode == 2 ? true : (g->smem_mode == 1 ? false : fits);
   if (use_smem && !fits) {
     set_error("fc_sample_usts: tree state does not fit in shared memory");
@@ -618,11 +653,11 @@ extern "C" fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int
   }
   Shape sh;
   {
-    const fc_status r = choose_shape(g, total, use_smem, nsm, &sh);
+    const fc_status r = choose_shape(g, nmax, total, use_smem, nsm, &sh);
     if (r != FC_OK) return r;
   }
   const int W = sh.W;
-  const size_t shb = smem_bytes(W, n, use_smem);
+  const size_t shb = smem_bytes(W, nmax, use_smem);
   int64_t grid = std::min<int64_t>(total, (int64_t)sh.per_sm * nsm);
   if (g->max_trees > 0) grid = std::min<int64_t>(grid, g->max_trees);
   void* gstate = nullptr;
@@ -631,15 +666,15 @@ extern "C" fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int
     // keep the per-tree state within a quarter of the device memory
     size_t freeb = 0, totalb = 0;
     FC_CK(cudaMemGetInfo(&freeb, &totalb));
-    const size_t words = ((size_t)n + 31) / 32;
-    const size_t per_tree = (size_t)n * sizeof(VState) + ((words * 4 + 255) & ~(size_t)255);
+    const size_t words = ((size_t)nmax + 31) / 32;
+    const size_t per_tree = (size_t)nmax * sizeof(VState) + ((words * 4 + 255) & ~(size_t)255);
     const size_t cap_trees = std::max<size_t>(1, (totalb / 4) / per_tree);
     grid = std::min<int64_t>(grid, (int64_t)cap_trees);
     void* ws = nullptr;
     const fc_status s = sampler_scratch(g->device, (size_t)grid * per_tree, st, &ws);
     if (s != FC_OK) return s;
     gstate = ws;
-    gbits = (uint32_t*)((char*)ws + (size_t)grid * n * sizeof(VState));
+    gbits = (uint32_t*)((char*)ws + (size_t)grid * nmax * sizeof(VState));
   }
   g->last_W = W;
   g->last_regs = sh.regs;
@@ -663,7 +698,25 @@ extern "C" fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int
   p.steps = steps_out;
   p.gstate = (VState*)gstate;
   p.gbits = gbits;
-  p.words = (int32_t)(((int64_t)n + 31) / 32);
+  p.words = (int32_t)(((int64_t)nmax + 31) / 32);
+  p.nmax = nmax;
+  p.num_graphs = g->num_graphs;
+  p.voff = g->voff;
+  p.gorder = g->gorder;
+  p.item_ns = nullptr;
+  p.t0_ns = nullptr;
+  if (batch) {
+    const size_t items = (size_t)g->num_graphs * (size_t)tau;
+    if (g->item_cap < items) {
+      if (g->item_ns) FC_CK(cudaFreeAsync(g->item_ns, st));
+      FC_CK(cudaMallocAsync((void**)&g->item_ns, items * sizeof(unsigned long long), st));
+      g->item_cap = items;
+    }
+    g->last_tau = tau;
+    p.item_ns = g->item_ns;
+    p.t0_ns = g->t0_ns;
+    FC_CK(cudaMemsetAsync(g->t0_ns, 0xff, sizeof(unsigned long long), st));
+  }
   p.counter = g->d_counter;
   p.err = g->d_err;
   p.stats = g->d_stats;
@@ -674,8 +727,8 @@ extern "C" fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int
   p.pre_cleared = 0;
   if (!use_smem) {
     // clear the state and bitmaps of the first wave in one pass
-    const size_t words = ((size_t)n + 31) / 32;
-    FC_CK(cudaMemsetAsync(gstate, 0, (size_t)grid * n * sizeof(VState) + (size_t)grid * words * 4, st));
+    const size_t words = ((size_t)nmax + 31) / 32;
+    FC_CK(cudaMemsetAsync(gstate, 0, (size_t)grid * nmax * sizeof(VState) + (size_t)grid * words * 4, st));
     p.pre_cleared = 1;
   }
   FC_CK(cudaMemsetAsync(g->d_counter, 0, sizeof(unsigned long long), st));
@@ -744,5 +797,23 @@ extern "C" fc_status fc_stack_entries(fc_graph* g, int32_t alpha_idx, uint64_t s
   p.err = g->d_err;
   k_stack_entries<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(p, alpha_idx, tree, count, verts, ks, out);
   FC_LAUNCHED();
+  return FC_OK;
+}
+
+extern "C" fc_status fc_batch_latency(fc_graph* g, double* per_graph_ms) {
+  if (g == nullptr || per_graph_ms == nullptr || g->num_graphs < 1 || g->item_ns == nullptr || g->last_tau < 1) {
+    set_error("fc_batch_latency: no batch launch recorded");
+    return FC_EINVAL;
+  }
+  const size_t items = (size_t)g->num_graphs * (size_t)g->last_tau;
+  std::vector<unsigned long long> h(items);
+  unsigned long long t0 = 0;
+  FC_CK(cudaMemcpy(h.data(), g->item_ns, items * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  FC_CK(cudaMemcpy(&t0, g->t0_ns, sizeof(t0), cudaMemcpyDeviceToHost));
+  for (int32_t gi = 0; gi < g->num_graphs; ++gi) {
+    unsigned long long mx = 0;
+    for (int64_t t = 0; t < g->last_tau; ++t) mx = std::max(mx, h[(size_t)gi * g->last_tau + t]);
+    per_graph_ms[gi] = mx > t0 ? (double)(mx - t0) * 1e-6 : 0.0;
+  }
   return FC_OK;
 }

@@ -38,6 +38,8 @@ def lib():
         sig = {
             "fc_build_augmented": ([I32, I64, P, P, P, P, I32, U32, P, ctypes.POINTER(P)], ctypes.c_int),
             "fc_graph_info": ([P, P, P, P, P], ctypes.c_int),
+            "fc_build_batch": ([I32, P, I64, P, P, P, P, U32, P, ctypes.POINTER(P)], ctypes.c_int),
+            "fc_batch_latency": ([P, P], ctypes.c_int),
             "fc_set_sampler_shape": ([P, I32, I32, I32, I32], ctypes.c_int),
             "fc_sampler_last_shape": ([P, P, P, P], ctypes.c_int),
             "fc_set_start_order": ([P, I32], ctypes.c_int),
@@ -129,6 +131,33 @@ class Graph:
         self.weighted = w is not None
 
     @classmethod
+    def batch(cls, union_csr, vertex_offsets, graph_alphas, stream=None):
+        """fc_build_batch: graphs as one block-diagonal CSR (host arrays), one alpha each."""
+        self = cls.__new__(cls)
+        voff = np.ascontiguousarray(vertex_offsets, dtype=np.int64)
+        ga = np.ascontiguousarray(graph_alphas, dtype=np.float64)
+        rp = np.ascontiguousarray(union_csr.rowptr, dtype=np.int64)
+        ci = np.ascontiguousarray(union_csr.colidx, dtype=np.int32)
+        ww = None if union_csr.w is None else np.ascontiguousarray(union_csr.w, dtype=np.float32)
+        h = ctypes.c_void_p()
+        _check(lib().fc_build_batch(int(ga.size), _ptr(voff), int(ci.shape[0]), _ptr(rp), _ptr(ci), _ptr(ww), _ptr(ga),
+                                    FC_HOST_PTRS, _stream(stream), ctypes.byref(h)), "fc_build_batch")
+        self._h = h
+        self.n = int(rp.shape[0]) - 1
+        self.nnz = int(ci.shape[0])
+        self.alphas = np.ones(1)
+        self.n_alpha = 1
+        self.weighted = ww is not None
+        self.num_graphs = int(ga.size)
+        self.vertex_offsets = voff.copy()
+        return self
+
+    def batch_latency_ms(self):
+        out = np.zeros(self.num_graphs, dtype=np.float64)
+        _check(lib().fc_batch_latency(self._h, _ptr(out)), "fc_batch_latency")
+        return out
+
+    @classmethod
     def from_csr(cls, g, alphas=(1.0,), stream=None):
         """From any object with rowptr/colidx/w numpy arrays (host copy path)."""
         return cls(g.rowptr, g.colidx, g.w, alphas, stream)
@@ -181,7 +210,8 @@ class Graph:
         if C is not None:
             _dev_tensor(C, torch.int32, na * n, "C")
         parents = torch.empty(na * tau * n, dtype=torch.int32, device=dev) if want_parents else None
-        steps = torch.zeros(na * tau, dtype=torch.int64, device=dev) if want_steps else None
+        nrow = getattr(self, "num_graphs", 0) or na
+        steps = torch.zeros(nrow * tau, dtype=torch.int64, device=dev) if want_steps else None
         _check(lib().fc_sample_usts(self._h, int(seed) & (2**64 - 1), int(tau), int(tree_offset), _ptr(R),
                                     _ptr(C), _ptr(parents), int(max_steps_per_tree), _ptr(steps),
                                     _stream(stream)), "fc_sample_usts")
@@ -189,7 +219,7 @@ class Graph:
         if want_parents:
             out["parents"] = parents.view(na, tau, n)
         if want_steps:
-            out["steps"] = steps.view(na, tau)
+            out["steps"] = steps.view(getattr(self, "num_graphs", 0) or na, tau)
         return out
 
     def stack_entries(self, seed: int, tree: int, verts, ks, alpha_idx: int = 0, stream=None):

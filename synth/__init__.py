@@ -22,4 +22,5 @@ from .graphs import (  # noqa: F401
     empty,
     random_small,
     uneven_batch,
+    union,
 )

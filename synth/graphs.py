@@ -305,3 +305,24 @@ def uneven_batch(count: int, seed: int, n_min: int = 100, n_max: int = 50_000,
             side = max(2, int(round(math.sqrt(nn))))
             graphs.append(perturbed_grid(side, side, gseed, weighted=False))
     return graphs, alphas
+
+
+def union(graphs):
+    """Block-diagonal union of graphs (vertex ids shifted); returns
+    (Graph, vertex offsets int64[len(graphs)+1])."""
+    offs = np.zeros(len(graphs) + 1, dtype=np.int64)
+    for i, g in enumerate(graphs):
+        offs[i + 1] = offs[i] + g.n
+    weighted = any(g.w is not None for g in graphs)
+    rowptr = np.zeros(int(offs[-1]) + 1, dtype=np.int64)
+    cols, ws = [], []
+    e0 = 0
+    for i, g in enumerate(graphs):
+        rowptr[offs[i] + 1: offs[i + 1] + 1] = g.rowptr[1:] + e0
+        cols.append(g.colidx.astype(np.int64) + offs[i])
+        if weighted:
+            ws.append(np.ones(g.nnz, np.float32) if g.w is None else g.w)
+        e0 += g.nnz
+    colidx = np.concatenate(cols).astype(np.int32) if cols else np.zeros(0, np.int32)
+    w = np.concatenate(ws).astype(np.float32) if weighted else None
+    return Graph(n=int(offs[-1]), rowptr=rowptr, colidx=colidx, w=w, name=f"union{len(graphs)}"), offs
