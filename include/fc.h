@@ -173,6 +173,23 @@ fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_o
                          uint64_t* steps_out, void* stream);
 
 /*
+ * fc_sample_usts without the synchronising error read-back, for enqueueing on
+ * a stream that is being captured into a CUDA graph (the persistent sampling
+ * launch, its memsets and the combinations after it become graph nodes).
+ * Device-side errors stay in the graph's error word until fc_sampler_check.
+ * The sampler's scratch buffer must already be large enough: make one
+ * uncaptured fc_sample_usts call with the same graph and tau first (else
+ * FC_EINVAL during capture).
+ */
+fc_status fc_sample_usts_async(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R,
+                               uint32_t* C, int32_t* parents, uint64_t max_steps_per_tree, uint64_t* steps_out,
+                               void* stream);
+
+/* Read and clear the device error word of g (synchronises `stream`); the
+ * status an fc_sample_usts call would have returned. */
+fc_status fc_sampler_check(fc_graph* g, void* stream);
+
+/*
  * Solve (I + alpha_a L) x_j = b_j for n_rhs right-hand sides by Jacobi-
  * preconditioned CG with FP32 inner iterations and FP64 residual / iterative
  * refinement (the paper's ground truth uses CG at tolerance 1e-9, Sec. 6.1;
@@ -282,6 +299,29 @@ fc_status fc_mlp_loss_grad(fc_graph* g, int32_t alpha_idx, const float* X, const
  */
 fc_status fc_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t count, int32_t step, float lr,
                       float beta1, float beta2, float eps, void* stream);
+
+/*
+ * Tree-path aggregation.  For T sampled trees given as parent arrays
+ * (int32 device [T][n], u* = n, as written by fc_sample_usts), computes for
+ * every vertex its forest root -- the vertex on its path whose parent is u* --
+ * and its depth below that root (0 for roots), by BFS levels from u*: children
+ * lists by counting sort, one level at a time, output positions from
+ * block-wide warp scans.  roots, depth: int32 device [T][n] (depth may be
+ * NULL).  FC_EINVAL if some parent array is not a spanning tree rooted at u*.
+ * By the matrix-forest theorem (Sec. 2), P(root(v) = u) = Omega[u, v].
+ * Allocates temporary device memory.  Synchronises `stream`.
+ */
+fc_status fc_tree_roots(const int32_t* parents, int32_t n, int64_t T, int32_t* roots, int32_t* depth,
+                        void* stream);
+
+/*
+ * Root-frequency counts for k query vertices: counts[q][v] += #{t : roots[t][v]
+ * == queries[q]} (uint32 device [k][n], accumulated).  counts/T estimates the
+ * column Omega[queries[q], :] without bias; the diagonal entry equals the
+ * u*-edge count R.  Allocates temporary device memory.  Synchronises `stream`.
+ */
+fc_status fc_root_counts(const int32_t* roots, int32_t n, int64_t T, const int32_t* queries, int32_t k,
+                         uint32_t* counts, void* stream);
 
 /*
  * Top-k ranking (Sec. 6.1): the k vertices with the smallest diag values

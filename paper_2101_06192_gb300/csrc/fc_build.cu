@@ -26,10 +26,14 @@ struct Scratch {
 static std::mutex g_scratch_mu;
 static Scratch g_scratch[64];
 
-fc_status sampler_scratch(int device, size_t bytes, cudaStream_t st, void** out) {
+fc_status sampler_scratch(int device, size_t bytes, cudaStream_t st, void** out, bool capturing) {
   if (device < 0 || device >= 64) return FC_EINVAL;
   std::lock_guard<std::mutex> lk(g_scratch_mu);
   Scratch& sc = g_scratch[device];
+  if (sc.bytes < bytes && capturing) {
+    set_error("fc_sample_usts_async: sampler scratch must be sized by an uncaptured call before stream capture");
+    return FC_EINVAL;
+  }
   if (sc.bytes < bytes) {
     if (sc.ptr) {
       FC_CK(cudaDeviceSynchronize());
@@ -405,6 +409,10 @@ static fc_status build_impl(int32_t n, int64_t nnz, const int64_t* rowptr, const
   g->weighted = (w != nullptr);
   g->alphas.assign(alphas, alphas + n_alpha);
   BUILD_CK(cudaGetDevice(&g->device));
+  {
+    size_t freeb = 0;
+    BUILD_CK(cudaMemGetInfo(&freeb, &g->device_bytes));
+  }
   retain_pool(g->device);
   if (G > 0) {
     g->num_graphs = G;

@@ -35,7 +35,7 @@ void note_launch();
 
 // Process-wide device scratch for the sampler's per-tree state: grown on
 // demand, reused across graphs and calls, released by fc_release_scratch.
-fc_status sampler_scratch(int device, size_t bytes, cudaStream_t st, void** out);
+fc_status sampler_scratch(int device, size_t bytes, cudaStream_t st, void** out, bool capturing = false);
 
 // Keep freed stream-ordered allocations in the device's default pool.
 void retain_pool(int device);
@@ -146,6 +146,7 @@ struct fc_graph {
   int32_t n_alpha = 0;
   bool weighted = false;
   int device = 0;
+  size_t device_bytes = 0;  // total device memory, read at build
   std::vector<double> alphas;
   // device arrays owned by the graph
   int64_t* rowptr = nullptr;   // [n+1]

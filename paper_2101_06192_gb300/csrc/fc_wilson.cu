@@ -628,9 +628,48 @@ static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool 
 
 using namespace fcx;
 
+static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R, uint32_t* C,
+                             int32_t* parents, uint64_t max_steps_per_tree, uint64_t* steps_out, void* stream,
+                             bool sync);
+
 extern "C" fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R,
                                     uint32_t* C, int32_t* parents, uint64_t max_steps_per_tree,
                                     uint64_t* steps_out, void* stream) {
+  return sample_impl(g, seed, tau, tree_offset, R, C, parents, max_steps_per_tree, steps_out, stream, true);
+}
+
+extern "C" fc_status fc_sample_usts_async(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R,
+                                          uint32_t* C, int32_t* parents, uint64_t max_steps_per_tree,
+                                          uint64_t* steps_out, void* stream) {
+  return sample_impl(g, seed, tau, tree_offset, R, C, parents, max_steps_per_tree, steps_out, stream, false);
+}
+
+extern "C" fc_status fc_sampler_check(fc_graph* g, void* stream) {
+  if (g == nullptr) return FC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t herr = 0;
+  FC_CK(cudaMemcpyAsync(&herr, g->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  FC_CK(cudaStreamSynchronize(st));
+  FC_CK(cudaMemsetAsync(g->d_err, 0, sizeof(uint32_t), st));
+  FC_CK(cudaStreamSynchronize(st));
+  if (herr & ERR_OVERFLOW) {
+    set_error("fc_sampler_check: a visit counter exceeded 2^24 - 1");
+    return FC_EOVERFLOW;
+  }
+  if (herr & ERR_TIMEOUT) {
+    set_error("fc_sampler_check: watchdog iteration budget exhausted");
+    return FC_ETIMEOUT;
+  }
+  if (herr != 0) {
+    set_error("fc_sampler_check: internal consistency check failed");
+    return FC_ECUDA;
+  }
+  return FC_OK;
+}
+
+static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R, uint32_t* C,
+                             int32_t* parents, uint64_t max_steps_per_tree, uint64_t* steps_out, void* stream,
+                             bool sync) {
   if (g == nullptr || R == nullptr || tau < 0 || tree_offset < 0 || tree_offset + tau > (int64_t(1) << 32)) {
     set_error("fc_sample_usts: bad argument");
     return FC_EINVAL;
@@ -638,6 +677,13 @@ extern "C" fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int
   if (tau == 0) return FC_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const int32_t n = g->n;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  FC_CK(cudaStreamIsCapturing(st, &cap));
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
+  if (capturing && sync) {
+    set_error("fc_sample_usts: reads its status back; use fc_sample_usts_async on a capturing stream");
+    return FC_EINVAL;
+  }
   int dev_smem_optin = 0, nsm = 0;
   FC_CK(cudaDeviceGetAttribute(&dev_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
   FC_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device));
@@ -664,14 +710,12 @@ extern "C" fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int
   uint32_t* gbits = nullptr;
   if (!use_smem) {
     // keep the per-tree state within a quarter of the device memory
-    size_t freeb = 0, totalb = 0;
-    FC_CK(cudaMemGetInfo(&freeb, &totalb));
     const size_t words = ((size_t)nmax + 31) / 32;
     const size_t per_tree = (size_t)nmax * sizeof(VState) + ((words * 4 + 255) & ~(size_t)255);
-    const size_t cap_trees = std::max<size_t>(1, (totalb / 4) / per_tree);
+    const size_t cap_trees = std::max<size_t>(1, (g->device_bytes / 4) / per_tree);
     grid = std::min<int64_t>(grid, (int64_t)cap_trees);
     void* ws = nullptr;
-    const fc_status s = sampler_scratch(g->device, (size_t)grid * per_tree, st, &ws);
+    const fc_status s = sampler_scratch(g->device, (size_t)grid * per_tree, st, &ws, capturing);
     if (s != FC_OK) return s;
     gstate = ws;
     gbits = (uint32_t*)((char*)ws + (size_t)grid * nmax * sizeof(VState));
@@ -707,6 +751,10 @@ extern "C" fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int
   p.t0_ns = nullptr;
   if (batch) {
     const size_t items = (size_t)g->num_graphs * (size_t)tau;
+    if (g->item_cap < items && capturing) {
+      set_error("fc_sample_usts_async: batch timestamps must be sized by an uncaptured call before stream capture");
+      return FC_EINVAL;
+    }
     if (g->item_cap < items) {
       if (g->item_ns) FC_CK(cudaFreeAsync(g->item_ns, st));
       FC_CK(cudaMallocAsync((void**)&g->item_ns, items * sizeof(unsigned long long), st));
@@ -732,12 +780,13 @@ extern "C" fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int
     p.pre_cleared = 1;
   }
   FC_CK(cudaMemsetAsync(g->d_counter, 0, sizeof(unsigned long long), st));
-  FC_CK(cudaMemsetAsync(g->d_err, 0, sizeof(uint32_t), st));
+  if (sync) FC_CK(cudaMemsetAsync(g->d_err, 0, sizeof(uint32_t), st));
   FC_CK(cudaMemsetAsync(g->d_stats, 0, (2 + N_CNT) * sizeof(unsigned long long), st));
   const WilsonFn fn = wilson_fn(use_smem, sh.regs);
   if (use_smem) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
   fn<<<(unsigned)grid, W, shb, st>>>(p);
   FC_LAUNCHED();
+  if (!sync) return FC_OK;
   uint32_t herr = 0;
   FC_CK(cudaMemcpyAsync(&herr, g->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   FC_CK(cudaStreamSynchronize(st));

@@ -46,6 +46,8 @@ def lib():
             "fc_sampler_counters": ([P, P, I32], ctypes.c_int),
             "fc_sample_usts": ([P, U64, I64, I64, P, P, P, U64, P, P], ctypes.c_int),
             "fc_sampler_stats": ([P, P, P], ctypes.c_int),
+            "fc_sample_usts_async": ([P, U64, I64, I64, P, P, P, U64, P, P], ctypes.c_int),
+            "fc_sampler_check": ([P, P], ctypes.c_int),
             "fc_stack_entries": ([P, I32, U64, U32, I64, P, P, P, P], ctypes.c_int),
             "fc_solve": ([P, I32, P, P, I32, D, I32, P, P], ctypes.c_int),
             "fc_pivot_solve": ([P, I32, P, D, I32, P, P], ctypes.c_int),
@@ -53,6 +55,8 @@ def lib():
             "fc_forest_farness_noalloc": ([P, I32, P, P, P, P, I64, P, P, P, P], ctypes.c_int),
             "fc_p_root": ([P, I32, P, P], ctypes.c_int),
             "fc_top_k": ([P, I32, I32, P, P], ctypes.c_int),
+            "fc_tree_roots": ([P, I32, I64, P, P, P], ctypes.c_int),
+            "fc_root_counts": ([P, I32, I64, P, I32, P, P], ctypes.c_int),
             "fc_mlp_param_count": ([], I32),
             "fc_vertex_features": ([P, I32, P, P], ctypes.c_int),
             "fc_mlp_forward": ([P, I32, P, P, P, P], ctypes.c_int),
@@ -196,6 +200,14 @@ class Graph:
                "fc_sampler_last_shape")
         return {"walkers_per_tree": w.value, "regs": r.value, "ctas": c.value}
 
+    def sample_async(self, seed: int, tau: int, R, C=None, tree_offset: int = 0, stream=None):
+        """fc_sample_usts_async (capturable; errors via check())."""
+        _check(lib().fc_sample_usts_async(self._h, int(seed) & (2**64 - 1), int(tau), int(tree_offset), _ptr(R),
+                                          _ptr(C), None, 0, None, _stream(stream)), "fc_sample_usts_async")
+
+    def check(self, stream=None):
+        _check(lib().fc_sampler_check(self._h, _stream(stream)), "fc_sampler_check")
+
     def sample(self, seed: int, tau: int, tree_offset: int = 0, R=None, C=None, with_C: bool = True,
                want_parents: bool = False, want_steps: bool = False, max_steps_per_tree: int = 0,
                stream=None):
@@ -322,6 +334,28 @@ def mlp_adam(params, grad, m, v, step: int, lr: float, beta1: float = 0.9, beta2
 def launch_count() -> int:
     """Kernel launches made by libfc.so in this process so far."""
     return int(lib().fc_launch_count())
+
+
+def tree_roots(parents, want_depth: bool = True, stream=None):
+    """fc_tree_roots on parents [T, n] (int32 CUDA): (roots, depth)."""
+    T, n = parents.shape[-2], parents.shape[-1]
+    par = parents.reshape(T, n).contiguous()
+    roots = torch.empty_like(par)
+    depth = torch.empty_like(par) if want_depth else None
+    _check(lib().fc_tree_roots(_ptr(par), int(n), int(T), _ptr(roots), _ptr(depth), _stream(stream)),
+           "fc_tree_roots")
+    return roots, depth
+
+
+def root_counts(roots, queries, counts=None, stream=None):
+    """fc_root_counts: counts[q][v] of trees in which v's forest root is queries[q]."""
+    T, n = roots.shape
+    q = queries.to(torch.int32).contiguous()
+    if counts is None:
+        counts = torch.zeros(q.numel() * n, dtype=torch.int32, device=roots.device)
+    _check(lib().fc_root_counts(_ptr(roots.contiguous()), int(n), int(T), _ptr(q), int(q.numel()), _ptr(counts),
+                                _stream(stream)), "fc_root_counts")
+    return counts.view(q.numel(), n)
 
 
 def tau_for(eps: float, delta: float, kappa: float, m: int) -> int:

@@ -1,0 +1,56 @@
+"""Tree sharding across ranks (gloo, world size 2, CPU): trees are indexed
+globally, so ranks sampling disjoint tree ranges (tree_offset = rank * share)
+and summing R and C with one allreduce reproduce a single run exactly.  This is
+the exchange the multi-GPU path would do; the samples come from the CPU oracle
+sampler (the only sampler available without a GPU)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import synth
+from oracle import native
+
+TAU = 40
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    g = synth.barabasi_albert(400, 3, 8)
+    share = TAU // world
+    o = native.wilson(g, 1.0, seed=21, tau=share, tree_offset=rank * share)
+    R = torch.from_numpy(o["R"].astype(np.int64))
+    C = torch.from_numpy(o["C"].astype(np.int64))
+    dist.all_reduce(R, op=dist.ReduceOp.SUM)
+    dist.all_reduce(C, op=dist.ReduceOp.SUM)
+    t = torch.tensor([float(rank + 1)])
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)  # max-over-ranks timing reduction used by the bench
+    if rank == 0:
+        np.savez(out_path, R=R.numpy(), C=C.numpy(), tmax=t.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_tree_sharding_matches_single_run(tmp_path):
+    out = str(tmp_path / "r.npz")
+    mp.start_processes(_worker, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+    got = np.load(out)
+    g = synth.barabasi_albert(400, 3, 8)
+    ref = native.wilson(g, 1.0, seed=21, tau=TAU)
+    np.testing.assert_array_equal(got["R"], ref["R"].astype(np.int64))
+    np.testing.assert_array_equal(got["C"], ref["C"].astype(np.int64))
+    assert got["tmax"][0] == 2.0
