@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--graphs", type=int, default=4096)
     ap.add_argument("--rmat-scale", type=int, default=22)
     ap.add_argument("--seeds", type=int, default=5)
+    ap.add_argument("--shape", default="",
+                    help="sampler shape 'walkers,regs[,order]' instead of the tuner's choice (profiling runs)")
     return ap.parse_args()
 
 
@@ -466,14 +468,15 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     tree_offset = rank * tau
-    shape_w, shape_r = 0, 0
+    shape = {}
+    from paper_2101_06192_gb300 import tune
 
     def step(seed, host_inputs=False, samp_ev=None, stats=None):
         if host_inputs:
             G = fc.Graph(rowptr_h.numpy(), colidx_h.numpy(), None, [ALPHA])
         else:
             G = fc.Graph(rowptr_d, colidx_d, None, [ALPHA])
-        G.set_shape(shape_w, 0, 0, shape_r)
+        tune.apply(G, shape)
         R.zero_()
         C.zero_()
         if samp_ev is not None:
@@ -497,11 +500,14 @@ def main():
             dist.barrier()
 
     # launch shape: empirical tuner (cached per graph class), untimed
-    from paper_2101_06192_gb300 import tune
-    shape_probe = fc.Graph(rowptr_d, colidx_d, None, [ALPHA])
-    shape = tune.autotune(shape_probe, tau)
-    shape_w, shape_r = shape.get("walkers", 0), shape.get("regs", 0)
-    shape_probe.close()
+    if args.shape:
+        parts = args.shape.split(",")
+        shape = {"walkers": int(parts[0]), "regs": int(parts[1]),
+                 "order": parts[2] if len(parts) > 2 else "degree", "fixed": True}
+    else:
+        shape_probe = fc.Graph(rowptr_d, colidx_d, None, [ALPHA])
+        shape = tune.autotune(shape_probe, tau)
+        shape_probe.close()
     for i in range(args.warmup):
         step(1000 + i)
     torch.cuda.synchronize()

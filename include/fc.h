@@ -117,26 +117,44 @@ fc_status fc_graph_info(const fc_graph* g, int32_t* n, int64_t* nnz, int32_t* n_
  * one tree (a multiple of 32 in [32, 1024], 0 = automatic); max_trees_resident:
  * cap on trees in flight (0 = fill the GPU); smem: 0 = automatic, 1 = force
  * global-memory tree state, 2 = force shared-memory tree state (FC_EINVAL if
- * it does not fit); regs: register cap of the kernel variant (32, 40 or 64;
- * 0 = automatic).  Affects speed only, never results.
+ * it does not fit); regs: register cap of the kernel variant (32, 40, 48 or
+ * 64; 0 = automatic; the CSR-walk kernel maps 48 to 40, the edge-record kernel
+ * maps 32 to 40).  Affects speed only, never results.
  */
 fc_status fc_set_sampler_shape(fc_graph* g, int32_t walkers_per_tree, int32_t max_trees_resident,
                                int32_t smem, int32_t regs);
 
 /*
  * Order in which the sampler's walkers take start vertices: 0 = ascending
- * degree (Algorithm 2's order, the default), 1 = descending degree.  The trees
- * do not depend on it (cycle popping); only the amount of waiting between
- * concurrent walkers does.
+ * degree (Algorithm 2's order, the default), 1 = descending degree, 2 =
+ * ascending vertex id, 3 = descending vertex id.  The trees do not depend on
+ * it (cycle popping); only the amount of waiting between concurrent walkers
+ * and the locality of the first steps do (vertex-id order loads start windows
+ * coalesced but makes walkers collide on graphs whose ids follow geometry).
  */
-fc_status fc_set_start_order(fc_graph* g, int32_t descending);
+fc_status fc_set_start_order(fc_graph* g, int32_t order);
+
+/*
+ * Sampler kernel: 0 = automatic (the default: the edge-record kernel for an
+ * unweighted single graph whose tree state lives in global memory, else the
+ * CSR-walk kernel), 1 = CSR-walk kernel, 2 = edge-record kernel (FC_EINVAL if
+ * g has no edge records: weighted graphs and batches).  Both draw the same
+ * random stacks, so the trees are identical; only speed differs.
+ * fc_sampler_last_kernel returns the kernel of the last launch on g (1 or 2;
+ * 0 before any launch).
+ */
+fc_status fc_set_sampler_kernel(fc_graph* g, int32_t kernel);
+int32_t fc_sampler_last_kernel(const fc_graph* g);
 
 /*
  * Diagnostic per-iteration counters of the last fc_sample_usts on g, summed
  * over walkers and trees: [0] walker iterations, [1] claims at stack entry 0,
  * [2] tree hits, [3] tree-hit confirmations, [4] conflict waits, [5] waits
  * after a release, [6] releases, [7] pop steps, [8] tops computed at entry
- * k > 0, [9] idle-lane iterations.  out: host uint64[count], count >= 10.
+ * k > 0, [9] idle-lane iterations.  For the edge-record kernel [1] counts
+ * every successful claim (any k) and [3] counts re-reads of a vertex whose
+ * owner has already moved on (its path joined the tree or was released).
+ * out: host uint64[count], count >= 10.
  * The counters are compiled in only when the library is built with
  * FC_WILSON_COUNTERS=1 (they cost registers); otherwise they read 0.
  * Synchronous.

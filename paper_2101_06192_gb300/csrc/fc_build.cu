@@ -329,8 +329,20 @@ static int grid_for(int64_t items, int threads) {
   return (int)b;
 }
 
+// Edge records of the edge-record sampler: for CSR entry e with target t,
+// {t, row offset of t, degree of t, min(T_t >> 21, 2^32 - 1)}.
+__global__ void k_edge_records(int64_t nnz, const int32_t* __restrict__ colidx, const uint4* __restrict__ rowinfo,
+                               uint4* __restrict__ edges) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t t = colidx[e];
+    const uint4 ri = rowinfo[t];
+    const uint64_t T = (uint64_t)ri.z | ((uint64_t)ri.w << 32);
+    edges[e] = make_uint4((uint32_t)t, ri.x, ri.y, T >= (1ull << 53) ? 0xffffffffu : (uint32_t)(T >> 21));
+  }
+}
+
 static void free_graph_arrays(fc_graph* g, cudaStream_t st) {
-  void* ptrs[] = {g->rowptr, g->colidx, g->w, g->deg, g->dw, g->S, g->order, g->rowinfo, g->B,
+  void* ptrs[] = {g->rowptr, g->colidx, g->w, g->deg, g->dw, g->S, g->order, g->rowinfo, g->B, g->edges,
                   g->alphas_d, g->d_err, g->d_counter, g->d_stats, g->voff, g->gid, g->alpha_v,
                   g->gorder, g->item_ns, g->t0_ns};
   for (void* p : ptrs)
@@ -559,6 +571,14 @@ static fc_status build_impl(int32_t n, int64_t nnz, const int64_t* rowptr, const
       BUILD_CK((fcx::note_launch(), cudaGetLastError()));
     }
   }
+  if (!g->weighted && g->num_graphs == 0 && nnz > 0) {
+    BUILD_CK(cudaMallocAsync((void**)&g->edges, (size_t)nnz * n_alpha * sizeof(uint4), st));
+    for (int a = 0; a < n_alpha; ++a) {
+      k_edge_records<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, g->colidx, g->rowinfo + (size_t)a * n,
+                                                        g->edges + (size_t)a * nnz);
+      BUILD_CK((fcx::note_launch(), cudaGetLastError()));
+    }
+  }
   BUILD_CK(cudaStreamSynchronize(st));
   *out = g;
   return FC_OK;
@@ -608,7 +628,8 @@ extern "C" fc_status fc_graph_info(const fc_graph* g, int32_t* n, int64_t* nnz, 
 extern "C" fc_status fc_set_sampler_shape(fc_graph* g, int32_t walkers_per_tree, int32_t max_trees_resident,
                                           int32_t smem, int32_t regs) {
   if (g == nullptr || walkers_per_tree < 0 || walkers_per_tree > 1024 || (walkers_per_tree % 32) != 0 ||
-      max_trees_resident < 0 || smem < 0 || smem > 2 || !(regs == 0 || regs == 32 || regs == 40 || regs == 64))
+      max_trees_resident < 0 || smem < 0 || smem > 2 ||
+      !(regs == 0 || regs == 32 || regs == 40 || regs == 48 || regs == 64))
     return FC_EINVAL;
   g->walkers = walkers_per_tree;
   g->max_trees = max_trees_resident;
@@ -617,11 +638,24 @@ extern "C" fc_status fc_set_sampler_shape(fc_graph* g, int32_t walkers_per_tree,
   return FC_OK;
 }
 
-extern "C" fc_status fc_set_start_order(fc_graph* g, int32_t descending) {
-  if (g == nullptr || descending < 0 || descending > 1) return FC_EINVAL;
-  g->order_desc = descending;
+extern "C" fc_status fc_set_start_order(fc_graph* g, int32_t order) {
+  if (g == nullptr || order < 0 || order > 3) return FC_EINVAL;
+  g->order_desc = order & 1;
+  g->order_id = order >> 1;
   return FC_OK;
 }
+
+extern "C" fc_status fc_set_sampler_kernel(fc_graph* g, int32_t kernel) {
+  if (g == nullptr || kernel < 0 || kernel > 2) return FC_EINVAL;
+  if (kernel == 2 && g->edges == nullptr) {
+    set_error("fc_set_sampler_kernel: edge records exist only for unweighted single graphs");
+    return FC_EINVAL;
+  }
+  g->kernel_pref = kernel;
+  return FC_OK;
+}
+
+extern "C" int32_t fc_sampler_last_kernel(const fc_graph* g) { return g ? g->last_kernel : -1; }
 
 extern "C" fc_status fc_sampler_last_shape(const fc_graph* g, int32_t* walkers_per_tree, int32_t* regs,
                                            int32_t* ctas) {

@@ -158,6 +158,7 @@ struct fc_graph {
   int32_t* order = nullptr;    // [n] ascending degree, ties by id
   uint4* rowinfo = nullptr;    // [n_alpha][n] {row offset, degree, T lo, T hi}
   uint64_t* B = nullptr;       // [n_alpha][nnz] slot thresholds (weighted only)
+  uint4* edges = nullptr;      // [n_alpha][nnz] edge records (unweighted single graphs)
   double* alphas_d = nullptr;  // [n_alpha]
   int32_t max_deg = 0;
   // batch of graphs (block-diagonal union with one alpha per graph)
@@ -178,7 +179,10 @@ struct fc_graph {
   int32_t max_trees = 0;
   int32_t smem_mode = 0;
   int32_t regs = 0;            // register cap of the sampler variant (0 = automatic)
-  int32_t order_desc = 0;      // sampler takes start vertices from the high-degree end
+  int32_t order_desc = 0;      // sampler takes start vertices from the high end of the order
+  int32_t order_id = 0;        // start order: 0 = degree (the default), 1 = vertex id (fc_set_start_order)
+  int32_t kernel_pref = 0;     // 0 = automatic, 1 = CSR-walk kernel, 2 = edge-record kernel
+  int32_t last_kernel = 0;     // kernel of the last launch (1 or 2)
   int32_t last_W = 0, last_regs = 0, last_grid = 0;  // shape of the last launch
   // scratch owned by the graph
   void* ws = nullptr;          // sampler per-tree state

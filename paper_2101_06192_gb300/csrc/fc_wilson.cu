@@ -30,122 +30,13 @@
 // only point from lower to higher walker ids and cannot form a cycle.
 #include <algorithm>
 
-#include "fc_internal.cuh"
+#include "fc_wilson_common.cuh"
 
 namespace fcx {
-
-struct __align__(16) VState {
-  unsigned long long st;
-  uint32_t nxt;
-  uint32_t pad;
-};
-
-constexpr int K_BITS = 24;
-constexpr unsigned long long K_MASK = (1ull << K_BITS) - 1;
-constexpr int W_BITS = 10;
-constexpr unsigned FULL = 0xffffffffu;
-
-struct WParams {
-  int32_t n;
-  int32_t n_alpha;
-  int64_t nnz;
-  const uint4* rowinfo;     // [n_alpha][n] {row offset, degree, T lo, T hi}
-  const int32_t* colidx;    // [nnz]
-  const int32_t* order;     // [n] start order (ascending degree)
-  const uint64_t* B;        // [n_alpha][nnz] slot thresholds, or null (unweighted)
-  int64_t tau;
-  int64_t tree_offset;
-  uint32_t key0, key1;
-  uint32_t* R;              // [n_alpha][n]
-  uint32_t* C;              // [n_alpha][n] or null
-  int32_t* parents;         // [n_alpha*tau][n] or null
-  uint64_t* steps;          // [n_alpha*tau] or null
-  VState* gstate;           // [gridDim.x][n] (global-state variant)
-  uint32_t* gbits;          // [gridDim.x][words] in-tree bitmaps (global-state variant)
-  int32_t words;            // bitmap words per tree: ceil(nmax / 32)
-  int32_t nmax;             // vertices of the largest tree of the launch (state records per CTA)
-  int pre_cleared;          // the first tree of every CTA starts from host-cleared state
-  unsigned long long* counter;
-  uint32_t* err;
-  unsigned long long* stats;  // [0] pops, [1] departures, [2..] iteration counters (N_CNT)
-  uint32_t max_iters;
-  int descending;           // take start vertices from the high-degree end
-  // batch of graphs: work item i samples tree (i % tau) of graph gorder[i / tau]
-  int32_t num_graphs;       // 0 = single graph
-  const int64_t* voff;      // [G+1]
-  const int32_t* gorder;    // [G] graphs by decreasing size
-  unsigned long long* item_ns;  // [G*tau] %globaltimer at completion, indexed graph-major (or null)
-  unsigned long long* t0_ns;    // earliest CTA start (or null)
-};
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Iteration counters (diagnostic), summed over walkers and trees.
-enum { CNT_ITER = 0, CNT_CLAIM_OK, CNT_TREE_HIT, CNT_CONFIRM, CNT_SPIN, CNT_WAIT, CNT_RELEASE, CNT_POP,
-       CNT_EDGE, CNT_IDLE_LANE, N_CNT };
-
-// Slot decision for one stack entry with Philox words o at a vertex with row
-// info ri = {row offset, degree, T lo, T hi}: returns true and sets *edge to
-// the CSR entry of the selected neighbour, or false when the entry selects u*
-// (u53 < T).  The neighbour is floor(o2 d / 2^32) (unweighted) or the first
-// entry of the row with u53 < B (weighted; the last B of a row is 2^53).
-__device__ __forceinline__ bool select_edge(const WParams& p, int a, const uint4& ri, const uint4& o,
-                                            uint32_t* edge) {
-  const uint32_t d = ri.y;
-  const uint64_t u = stack_u53(o);
-  const uint64_t T = (uint64_t)ri.z | ((uint64_t)ri.w << 32);
-  if (u < T) return false;
-  if (p.B == nullptr) {
-    *edge = ri.x + __umulhi(o.z, d);
-    return true;
-  }
-  const uint64_t* b = p.B + (size_t)a * p.nnz + ri.x;
-  uint32_t lo = 0, hi = d - 1;
-  if (d <= 8) {
-    // short rows: all thresholds in flight at once
-    uint64_t bv[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) bv[j] = (j < (int)d - 1) ? __ldg(b + j) : ~0ull;
-#pragma unroll
-    for (int j = 7; j >= 0; --j)
-      if (u < bv[j]) lo = (uint32_t)j;
-    lo = min(lo, d - 1);
-  } else {
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (u < __ldg(b + mid)) hi = mid; else lo = mid + 1;
-    }
-  }
-  *edge = ri.x + lo;
-  return true;
-}
 
 enum { P_IDLE = 0, P_CHECK, P_CLAIM, P_CLAIM2, P_EDGE, P_NEXT, P_POP, P_RETRACE, P_RELEASE, P_WAIT,
        P_DONE };
 constexpr uint32_t NO_START = 0xffffffffu;
-constexpr int PB = 8;  // path vertices remembered per walker (shared memory)
-
-__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* a) {
-  return *(const volatile unsigned long long*)a;
-}
-__device__ __forceinline__ uint32_t ld_volatile32(const uint32_t* a) {
-  return *(const volatile uint32_t*)a;
-}
-
-// Per-iteration diagnostic counters (fc_sampler_counters) are compiled in only
-// with -DFC_WILSON_COUNTERS=1; they cost registers in the walk loop.
-#ifndef FC_WILSON_COUNTERS
-#define FC_WILSON_COUNTERS 0
-#endif
-#if FC_WILSON_COUNTERS
-#define CNT(q) (++cnt[q])
-#else
-#define CNT(q) ((void)0)
-#endif
 
 // One loop iteration = at most one dependent round trip to memory per walker:
 // the memory operations of the iteration are issued (predicated by the
@@ -187,6 +78,14 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
 #define SV(v) S[(v) - base]
 #define BWV(v) bits[((v) - base) >> 5]
 #define BITV(v) (1u << (((v) - base) & 31))
+#define LD_BITS(v) ld_volatile32(&BWV(v))
+#define OR_BITS(v) ((void)atomicOr(&BWV(v), BITV(v)))
+#define CAS_ST(v, cmp, val) atomicCAS(&SV(v).st, (cmp), (val))
+#define ADD_ST(v, d) ((void)atomicAdd(&SV(v).st, (d)))
+#define LD_NXT(v) SV(v).nxt
+#define ST_NXT(v, t) ((void)(SV(v).nxt = (t)))
+#define LD_RINFO(v) __ldg(rinfo + (v))
+#define LD_COL(e) __ldg(p.colidx + (e))
   bool first_tree = true;
   const int64_t total = (int64_t)(p.num_graphs > 0 ? p.num_graphs : p.n_alpha) * p.tau;
 
@@ -252,7 +151,8 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
         ibase = __shfl_sync(FULL, ibase, leader);
         if (need && !fin) {
           sni = ibase + __popc(want & lt_mask);
-          sn = sni < (uint32_t)nl ? __ldg(p.order + base + (p.descending ? (uint32_t)nl - 1u - sni : sni)) : -1;
+          const uint32_t ix = p.descending ? (uint32_t)nl - 1u - sni : sni;
+          sn = sni < (uint32_t)nl ? (p.id_order ? base + (int32_t)ix : __ldg(p.order + base + ix)) : -1;
           need = false;
         }
       }
@@ -294,18 +194,18 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
       // computed and its CSR target loaded speculatively alongside.
       bool hit = false;
       if (mode == P_CHECK) {
-        const uint32_t bw = ld_volatile32(&BWV(x));
-        xr = __ldg(rinfo + x);
+        const uint32_t bw = LD_BITS(x);
+        xr = LD_RINFO(x);
         hit = (bw & BITV(x)) != 0u;
         if (!hit) mode = P_CLAIM;
       }
       unsigned long long old = 0ull;
-      if (mode == P_CLAIM) old = atomicCAS(&SV(x).st, 0ull, mytag << K_BITS);
-      else if (mode == P_CLAIM2) old = atomicCAS(&SV(x).st, cexp, (mytag << K_BITS) | (cexp & K_MASK));
+      if (mode == P_CLAIM) old = CAS_ST(x, 0ull, mytag << K_BITS);
+      else if (mode == P_CLAIM2) old = CAS_ST(x, cexp, (mytag << K_BITS) | (cexp & K_MASK));
       else if (mode == P_WAIT) old = ld_volatile(&SV(x).st);
       const bool walk = (mode == P_POP) || (mode == P_RETRACE) || (mode == P_RELEASE);
       uint32_t nc = 0;
-      if (walk) nc = SV(c).nxt;
+      if (walk) nc = LD_NXT(c);
       // the stack entry: k = 0 speculatively while claiming, kx when computing a top
       const bool topc = (mode == P_CLAIM) || (mode == P_EDGE);
       uint32_t e = 0;
@@ -315,8 +215,8 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
         nb = select_edge(p, a, xr, o, &e);
       }
       int32_t t = n;
-      if (topc && nb) t = __ldg(p.colidx + e);
-      else if (mode == P_NEXT) t = __ldg(p.colidx + enext);
+      if (topc && nb) t = LD_COL(e);
+      else if (mode == P_NEXT) t = LD_COL(enext);
 
       // ---- consume ----
       bool finished = false;  // the path reached the tree or u*
@@ -346,7 +246,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
             }
             CNT(CNT_CLAIM_OK);
             ++deps;
-            SV(h).nxt = (uint32_t)t;
+            ST_NXT(h, (uint32_t)t);
             if (!nb) {
               atomicAdd(p.R + (size_t)a * n + h, 1u);
               if (p.C != nullptr) atomicAdd(p.C + (size_t)a * n + h, 1u);
@@ -400,7 +300,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
           wtag = tag;
           const int nfree = len > PB ? PB - 1 : len;
           for (int i = 0; i < PB; ++i)
-            if (i < nfree) atomicAdd(&SV(sh_pb[i * W + me]).st, 0ull - (mytag << K_BITS));
+            if (i < nfree) ADD_ST(sh_pb[i * W + me], 0ull - (mytag << K_BITS));
           if (len > PB) {
             c = (int32_t)sh_pb[(PB - 1) * W + me];
             rh = h;
@@ -416,7 +316,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
         case P_EDGE: {
           CNT(CNT_EDGE);
           ++deps;
-          SV(h).nxt = (uint32_t)t;
+          ST_NXT(h, (uint32_t)t);
           if (!nb) {
             atomicAdd(p.R + (size_t)a * n + h, 1u);
             if (p.C != nullptr && kx == 0u) atomicAdd(p.C + (size_t)a * n + h, 1u);
@@ -431,13 +331,13 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
           // cycle x -> ... -> h -> x: free every vertex but x at its next entry
           CNT(CNT_POP);
           if (!rskip) {
-            atomicAdd(&SV(c).st, 1ull - (mytag << K_BITS));
+            ADD_ST(c, 1ull - (mytag << K_BITS));
             ++pops;
           }
           rskip = false;
           c = (int32_t)nc;
           if (c == x) {
-            atomicAdd(&SV(x).st, 1ull);
+            ADD_ST(x, 1ull);
             ++pops;
             ++kx;
             if (kx >= (uint32_t)K_MASK) {
@@ -457,14 +357,14 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
           break;
         }
         case P_RETRACE: {
-          if (!rskip) atomicOr(&BWV(c), BITV(c));
+          if (!rskip) OR_BITS(c);
           rskip = false;
           if (c == rh) mode = P_IDLE;
           else c = (int32_t)nc;
           break;
         }
         case P_RELEASE: {
-          atomicAdd(&SV(c).st, 0ull - (mytag << K_BITS));
+          ADD_ST(c, 0ull - (mytag << K_BITS));
           if (c == rh) mode = P_WAIT;
           else c = (int32_t)nc;
           break;
@@ -492,7 +392,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
           for (int i = 0; i < PB; ++i)
             if (i < len) {
               const uint32_t v = sh_pb[i * W + me];
-              atomicOr(&BWV(v), BITV(v));
+              OR_BITS(v);
             }
           if (len > PB) {
             c = (int32_t)sh_pb[(PB - 1) * W + me];
@@ -540,6 +440,14 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
 #undef SV
 #undef BWV
 #undef BITV
+#undef LD_BITS
+#undef OR_BITS
+#undef CAS_ST
+#undef ADD_ST
+#undef LD_NXT
+#undef ST_NXT
+#undef LD_RINFO
+#undef LD_COL
 
 __global__ void k_stack_entries(WParams p, int a, uint32_t tg, int64_t count, const int32_t* __restrict__ verts,
                                 const uint32_t* __restrict__ ks, int32_t* __restrict__ out) {
@@ -563,8 +471,6 @@ static size_t smem_bytes(int W, int32_t n, bool smem) {
   return smem ? gen + (size_t)n * sizeof(VState) + words * 4 : gen;
 }
 
-typedef void (*WilsonFn)(WParams);
-
 static WilsonFn wilson_fn(bool smem, int regs) {
   if (smem) {
     if (regs == 32) return k_wilson<true, 32>;
@@ -585,7 +491,8 @@ struct Shape {
 // Launch shape: the largest walker count whose CTAs hold every tree of the
 // launch in one wave (trees of one launch take about equally long), else the
 // shape with the most walkers resident.  Walkers per tree are capped at n/8.
-static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool smem, int nsm, Shape* out) {
+static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool smem, bool edge, int nsm,
+                              Shape* out) {
   const int wcap = std::max(32, std::min(1024, (int)((n / 8) & ~31)));
   // measured on GB300 (BA n = 2^20, tau = 1024): the 40-register variant is
   // fastest; graphs with long walks prefer more walkers per tree, which the
@@ -593,11 +500,14 @@ static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool 
   const int regs_list[2] = {40, 64};
   double best = -1.0;
   for (int ri = 0; ri < 2; ++ri) {
-    const int regs = g->regs > 0 ? g->regs : regs_list[ri];
+    int regs = g->regs > 0 ? g->regs : regs_list[ri];
     if (g->regs > 0 && ri > 0) break;
-    const WilsonFn fn = wilson_fn(smem, regs);
+    if (!edge && regs == 48) regs = 40;
+    if (edge && regs == 32) regs = 40;
+    const WilsonFn fn = edge ? wilson_edge_fn(regs) : wilson_fn(smem, regs);
     for (int W = (g->walkers > 0 ? g->walkers : wcap); W >= 32; W -= 32) {
-      const size_t shb = smem_bytes(W, n, smem);
+      const size_t shb = edge ? wilson_edge_smem(W) : smem_bytes(W, n, smem);
+      if (edge) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
       if (smem) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
       int per_sm = 0;
       FC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, W, shb));
@@ -692,25 +602,32 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   const int32_t nmax = batch ? g->max_ng : n;  // largest tree of the launch
   const int wmin = g->walkers > 0 ? g->walkers : 32;
   const bool fits = smem_bytes(wmin, nmax, true) + 64 <= (size_t)dev_smem_optin;
-  const bool use_smem = g->smem_mode == 2 ? true : (g->smem_mode == 1 ? false : fits);
+  // automatic placement keeps the state in global memory when the edge-record
+  // kernel is requested (it has no shared-memory variant)
+  const bool use_smem = g->smem_mode == 2 ? true : (g->smem_mode == 1 ? false : (fits && g->kernel_pref != 2));
   if (use_smem && !fits) {
     set_error("fc_sample_usts: tree state does not fit in shared memory");
     return FC_EINVAL;
   }
+  const bool edge = !use_smem && !batch && g->edges != nullptr && g->kernel_pref != 1;
+  if (g->kernel_pref == 2 && !edge) {
+    set_error("fc_sample_usts: the edge-record kernel needs an unweighted single graph with global state");
+    return FC_EINVAL;
+  }
   Shape sh;
   {
-    const fc_status r = choose_shape(g, nmax, total, use_smem, nsm, &sh);
+    const fc_status r = choose_shape(g, nmax, total, use_smem, edge, nsm, &sh);
     if (r != FC_OK) return r;
   }
   const int W = sh.W;
-  const size_t shb = smem_bytes(W, nmax, use_smem);
+  const size_t shb = edge ? wilson_edge_smem(W) : smem_bytes(W, nmax, use_smem);
   int64_t grid = std::min<int64_t>(total, (int64_t)sh.per_sm * nsm);
   if (g->max_trees > 0) grid = std::min<int64_t>(grid, g->max_trees);
   void* gstate = nullptr;
   uint32_t* gbits = nullptr;
   if (!use_smem) {
     // keep the per-tree state within a quarter of the device memory
-    const size_t words = ((size_t)nmax + 31) / 32;
+    const size_t words = edge ? 0 : ((size_t)nmax + 31) / 32;  // the edge-record kernel keeps no bitmap
     const size_t per_tree = (size_t)nmax * sizeof(VState) + ((words * 4 + 255) & ~(size_t)255);
     const size_t cap_trees = std::max<size_t>(1, (g->device_bytes / 4) / per_tree);
     grid = std::min<int64_t>(grid, (int64_t)cap_trees);
@@ -723,6 +640,7 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   g->last_W = W;
   g->last_regs = sh.regs;
   g->last_grid = (int32_t)grid;
+  g->last_kernel = edge ? 2 : 1;
   WParams p;
   p.n = n;
   p.n_alpha = g->n_alpha;
@@ -734,6 +652,8 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   p.tau = tau;
   p.tree_offset = tree_offset;
   p.descending = g->order_desc;
+  p.id_order = g->order_id;
+  p.edges = g->edges;
   p.key0 = (uint32_t)seed;
   p.key1 = (uint32_t)(seed >> 32);
   p.R = R;
@@ -775,15 +695,15 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   p.pre_cleared = 0;
   if (!use_smem) {
     // clear the state and bitmaps of the first wave in one pass
-    const size_t words = ((size_t)nmax + 31) / 32;
+    const size_t words = edge ? 0 : ((size_t)nmax + 31) / 32;
     FC_CK(cudaMemsetAsync(gstate, 0, (size_t)grid * nmax * sizeof(VState) + (size_t)grid * words * 4, st));
     p.pre_cleared = 1;
   }
   FC_CK(cudaMemsetAsync(g->d_counter, 0, sizeof(unsigned long long), st));
   if (sync) FC_CK(cudaMemsetAsync(g->d_err, 0, sizeof(uint32_t), st));
   FC_CK(cudaMemsetAsync(g->d_stats, 0, (2 + N_CNT) * sizeof(unsigned long long), st));
-  const WilsonFn fn = wilson_fn(use_smem, sh.regs);
-  if (use_smem) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
+  const WilsonFn fn = edge ? wilson_edge_fn(sh.regs) : wilson_fn(use_smem, sh.regs);
+  if (use_smem || edge) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
   fn<<<(unsigned)grid, W, shb, st>>>(p);
   FC_LAUNCHED();
   if (!sync) return FC_OK;

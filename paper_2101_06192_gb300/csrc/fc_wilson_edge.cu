@@ -1,0 +1,468 @@
+// Edge-record variant of the Wilson sampler (Algorithm 2 on G*, rooted at u*)
+// for unweighted single graphs with the per-tree state in global memory.
+//
+// It uses the same random stacks, the same cycle-popping argument (so the
+// trees are bit-identical to the sequential sampler's) and the same wait-die
+// protocol as the CSR-walk kernel; what differs is the memory schedule of a
+// walk step, which decides the speed of this latency-bound loop.
+//
+//  * Each CSR entry is widened to a 16-byte record describing its target:
+//    {vertex, row offset, degree, high 32 bits of its u*-threshold T}.  A
+//    walker that steps onto x therefore already holds x's row: it computes
+//    x's stack entry for k = 0 speculatively and loads the selected record in
+//    the same round trip as the CAS that claims x.
+//  * Tree membership is a flag bit in x's state word, set when a path joins
+//    the tree, so that same CAS also answers "is x in the tree?".  One
+//    dependent round trip per step instead of two, and no per-tree bitmap.
+//  * The slot decision stays exact: with T_hi = min(T >> 21, 2^32 - 1) and
+//    u_hi = u53 >> 21, u_hi < T_hi implies u53 < T and u_hi > T_hi implies
+//    u53 >= T; only u_hi == T_hi (probability about 2^-32 per step) reads the
+//    full T from the row info.
+//  * Start vertices are handed out per warp from windows of 32 consecutive
+//    positions of the start order; the warp loads the 32 state words and row
+//    infos together (coalesced in vertex-id order) and keeps only vertices
+//    not yet in the tree.
+//
+// State word: bits 0..23 k (stack entries popped), bits 24..62 tag
+// ((gen << 10) | walker, 0 = free), bit 63 in-tree flag.
+#include "fc_wilson_common.cuh"
+
+namespace fcx {
+
+namespace {
+
+constexpr unsigned long long IN_TREE = 1ull << 63;
+constexpr unsigned long long TAG_MASK = (1ull << (63 - K_BITS)) - 1ull;
+
+enum { E_IDLE = 0, E_START, E_CLAIM, E_CLAIM2, E_TOP, E_POP, E_RETRACE, E_RELEASE, E_WAIT, E_DONE };
+
+__device__ __forceinline__ uint32_t thr_hi(const uint4& ri) {
+  const uint64_t T = (uint64_t)ri.z | ((uint64_t)ri.w << 32);
+  return T >= (1ull << 53) ? 0xffffffffu : (uint32_t)(T >> 21);
+}
+
+// Position of set bit number r (0-based) of m; requires r < popc(m).  The
+// result is in [0, 31] for every input.
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t r) {
+  uint32_t pos = 0;
+#pragma unroll
+  for (int sh = 16; sh > 0; sh >>= 1)
+    if ((uint32_t)__popc(m & ((1u << (pos + sh)) - 1u)) <= r) pos += sh;
+  return pos;
+}
+
+// Asynchronous 16-byte global -> shared copies (through L2), used to fetch the
+// next start window in the same round trip as the walk step.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+}  // namespace
+
+template <int MAXREG>
+__global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned long long sh_tree, sh_pops, sh_deps;
+  __shared__ uint32_t sh_next;
+  __shared__ volatile uint32_t sh_abort;
+  const int me = threadIdx.x;
+  const int W = blockDim.x;
+  const int lane = me & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  volatile uint32_t* sh_gen = (volatile uint32_t*)smem_raw;               // [W]
+  uint32_t* sh_pb = (uint32_t*)(smem_raw + (size_t)W * 4);                // [PB][W] path prefix
+  // start window of this warp: row info and state record of each slot (copied
+  // asynchronously) and its vertex
+  uint4* sh_wri = (uint4*)(smem_raw + (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15));
+  uint4* sh_wst = sh_wri + W;
+  uint32_t* sh_wv = (uint32_t*)(sh_wst + W);
+  sh_wri += me & ~31;
+  sh_wst += me & ~31;
+  sh_wv += me & ~31;
+  const int32_t n = p.n;  // u* = n
+  VState* S = p.gstate + (size_t)blockIdx.x * p.nmax;
+  const int64_t total = (int64_t)p.n_alpha * p.tau;
+  bool first_tree = true;
+
+  // Plain memory operations: L2 eviction hints measured slower for this kernel
+  // (its 16-byte edge records do not fit in L2 at the sizes where it matters).
+#define ADD_ST(v, d) atomicAdd(&S[v].st, (d))
+#define OR_ST(v, f) atomicOr(&S[v].st, (f))
+#define LD_NXT(v) S[v].nxt
+#define ST_NXT(v, t) (S[v].nxt = (t))
+
+  for (;;) {
+    if (me == 0) sh_tree = atomicAdd(p.counter, 1ull);
+    __syncthreads();
+    const unsigned long long tree = sh_tree;
+    if ((int64_t)tree >= total || *(volatile uint32_t*)p.err != 0u) break;
+    const int a = (int)(tree / (unsigned long long)p.tau);
+    const int64_t tloc = (int64_t)(tree % (unsigned long long)p.tau);
+    const uint32_t tg = (uint32_t)(p.tree_offset + tloc);
+    if (!(first_tree && p.pre_cleared))
+      for (int32_t v = me; v < n; v += W) reinterpret_cast<uint4&>(S[v]) = make_uint4(0u, 0u, 0u, 0u);
+    first_tree = false;
+    sh_gen[me] = 1u;
+    if (me == 0) {
+      sh_next = 0;
+      sh_abort = 0;
+      sh_pops = 0;
+      sh_deps = 0;
+    }
+    __syncthreads();
+    const uint4* __restrict__ rinfo = p.rowinfo + (size_t)a * n;
+    const uint4* __restrict__ edges = p.edges + (size_t)a * p.nnz;
+
+    int mode = E_IDLE;
+    int32_t x = 0, h = -1, c = 0, rh = 0, s = 0, len = 0;
+    uint32_t xo = 0, xd = 0, xth = 0;  // row offset, degree and T_hi of x
+    bool rskip = false;
+    uint32_t gen = 1, kx = 0, iters = 0, pops = 0, deps = 0;
+    unsigned long long wtag = 0, cexp = 0;
+    uint32_t wmask = 0;   // warp-uniform: window slots not handed out yet
+    bool wdone = false;   // warp-uniform: the start order is exhausted
+#if FC_WILSON_COUNTERS
+    uint32_t cnt[N_CNT];
+#pragma unroll
+    for (int q = 0; q < N_CNT; ++q) cnt[q] = 0;
+#endif
+
+    while (true) {
+      __syncwarp();
+      const bool fin = (mode == E_DONE) || (sh_abort != 0u);
+      if (__all_sync(FULL, fin)) break;
+
+      // ---- start vertices: hand out the window; a dry window is refilled by
+      // copies issued with this iteration's memory operations ----
+      const bool need = !fin && mode == E_IDLE;
+      const unsigned want = __ballot_sync(FULL, need);
+      bool refill = false;  // warp-uniform
+      if (want) {
+        const uint32_t nw = (uint32_t)__popc(want), na = (uint32_t)__popc(wmask);
+        if (need) {
+          const uint32_t r = (uint32_t)__popc(want & lt_mask);
+          if (r < na) {
+            const uint32_t slot = nth_set_bit(wmask, r);
+            const uint4 wr = sh_wri[slot];
+            s = x = (int32_t)sh_wv[slot];
+            xo = wr.x;
+            xd = wr.y;
+            xth = thr_hi(wr);
+            h = -1;
+            len = 0;
+            mode = E_CLAIM;
+          } else if (wdone) {
+            mode = E_DONE;
+          }
+        }
+        wmask = nw >= na ? 0u : (wmask & ~((2u << nth_set_bit(wmask, nw - 1u)) - 1u));
+        refill = nw > na && !wdone;
+      }
+      bool act = !fin && mode != E_IDLE && mode != E_DONE;
+      if (act) {
+        CNT(CNT_ITER);
+        if (++iters > p.max_iters) {
+          atomicOr(p.err, ERR_TIMEOUT);
+          sh_abort = 1u;
+          mode = E_DONE;
+          act = false;
+        }
+      } else {
+        CNT(CNT_IDLE_LANE);
+      }
+      uint32_t wb = 0;
+      bool wok = false;
+      if (refill) {
+        __syncwarp();  // the slots handed out above are read before they are overwritten
+        if (lane == 0) wb = atomicAdd(&sh_next, 32u);
+        wb = __shfl_sync(FULL, wb, 0);
+        const uint32_t i = wb + (uint32_t)lane;
+        wok = i < (uint32_t)n;
+        if (wok) {
+          const uint32_t ix = p.descending ? (uint32_t)n - 1u - i : i;
+          const int32_t v = p.id_order ? (int32_t)ix : __ldg(p.order + ix);
+          sh_wv[lane] = (uint32_t)v;
+          cp_async16(&sh_wri[lane], rinfo + v);
+          cp_async16(&sh_wst[lane], &S[v]);
+        }
+        cp_async_commit();
+      }
+
+      if (act) {
+        const unsigned long long mytag = ((unsigned long long)gen << W_BITS) | (unsigned)me;
+
+        // ---- issue: claim x and, speculatively, load the record its top selects ----
+        unsigned long long old = 0ull;
+        if (mode == E_CLAIM) old = atomicCAS(&S[x].st, 0ull, mytag << K_BITS);
+        else if (mode == E_CLAIM2) old = atomicCAS(&S[x].st, cexp, (mytag << K_BITS) | (cexp & K_MASK));
+        else if (mode == E_WAIT) old = ld_volatile(&S[x].st);
+        uint4 ri = make_uint4(0u, 0u, 0u, 0u);
+        if (mode == E_START) ri = __ldg(rinfo + x);
+        const bool walk = (mode == E_POP) || (mode == E_RETRACE) || (mode == E_RELEASE);
+        uint32_t nc = 0;
+        if (walk) nc = LD_NXT(c);
+        const bool topc = (mode == E_CLAIM) || (mode == E_CLAIM2) || (mode == E_TOP);
+        bool nb = false;
+        uint4 er = make_uint4((uint32_t)n, 0u, 0u, 0u);
+        if (topc) {
+          const uint32_t ks = mode == E_TOP ? kx : (mode == E_CLAIM2 ? (uint32_t)(cexp & K_MASK) : 0u);
+          const uint4 o = philox4x32_10(ks, (uint32_t)x, tg, (uint32_t)a, p.key0, p.key1);
+          const uint64_t u = stack_u53(o);
+          const uint32_t uh = (uint32_t)(u >> 21);
+          if (uh != xth) {
+            nb = uh > xth;
+          } else {
+            const uint4 rx = __ldg(rinfo + x);
+            nb = u >= ((uint64_t)rx.z | ((uint64_t)rx.w << 32));
+          }
+          if (nb) er = __ldg(edges + xo + __umulhi(o.z, xd));
+        }
+
+        // ---- consume ----
+        bool finished = false;  // the path reached the tree or u*
+        switch (mode) {
+          case E_START: {  // row info of a restart vertex
+            xo = ri.x;
+            xd = ri.y;
+            xth = thr_hi(ri);
+            mode = E_CLAIM;
+            break;
+          }
+          case E_CLAIM:
+          case E_CLAIM2: {
+            if (mode == E_CLAIM ? (old == 0ull) : (old == cexp)) {
+              // x joins this walker's path with its top at entry kx
+              CNT(CNT_CLAIM_OK);
+              kx = mode == E_CLAIM ? 0u : (uint32_t)(cexp & K_MASK);
+              if (kx >= (uint32_t)K_MASK - 1u) {
+                // a pop while x is owned adds at most one more: keep k below 2^24
+                atomicOr(p.err, ERR_OVERFLOW);
+                sh_abort = 1u;
+                mode = E_DONE;
+                break;
+              }
+              h = x;
+              if (len < PB) sh_pb[len * W + me] = (uint32_t)x;
+              ++len;
+              ++deps;
+              ST_NXT(x, er.x);  // er.x = n when the entry selects u*
+              if (!nb) {
+                atomicAdd(p.R + (size_t)a * n + x, 1u);
+                if (p.C != nullptr && kx == 0u) atomicAdd(p.C + (size_t)a * n + x, 1u);
+                finished = true;
+                break;
+              }
+              x = (int32_t)er.x;
+              xo = er.y;
+              xd = er.z;
+              xth = er.w;
+              mode = E_CLAIM;
+              break;
+            }
+            if (mode == E_CLAIM2) {
+              mode = E_CLAIM;  // the state changed under us: look again
+              break;
+            }
+            if (old & IN_TREE) {
+              CNT(CNT_TREE_HIT);
+              finished = true;
+              break;
+            }
+            const unsigned long long tag = (old >> K_BITS) & TAG_MASK;
+            if (tag == 0ull) {
+              cexp = old;  // free with k > 0
+              mode = E_CLAIM2;
+              break;
+            }
+            const uint32_t w = (uint32_t)(tag & ((1u << W_BITS) - 1));
+            const uint32_t tgen = (uint32_t)(tag >> W_BITS);
+            if (w >= (uint32_t)W) {
+              atomicOr(p.err, ERR_INVAL);
+              sh_abort = 1u;
+              mode = E_DONE;
+              break;
+            }
+            if (w == (uint32_t)me && tgen == gen) {
+              // x closes a cycle on this walker's path: pop it
+              kx = (uint32_t)(old & K_MASK);
+              c = x;
+              rskip = true;
+              mode = E_POP;
+              break;
+            }
+            // w finished that path (its flag is on its way) or gave x up after
+            // our read: look again
+            if (sh_gen[w] != tgen) {
+              CNT(CNT_CONFIRM);
+              break;
+            }
+            if (h < 0 || (uint32_t)me < w) {
+              CNT(CNT_SPIN);
+              break;  // wait-die: wait
+            }
+            CNT(CNT_RELEASE);
+            // die: give the path back without popping anything; vertices whose
+            // nxt the release walk still needs are freed only after it is read
+            wtag = tag;
+            const int nfree = len > PB ? PB - 1 : len;
+            for (int i = 0; i < PB; ++i)
+              if (i < nfree) ADD_ST(sh_pb[i * W + me], 0ull - (mytag << K_BITS));
+            if (len > PB) {
+              c = (int32_t)sh_pb[(PB - 1) * W + me];
+              rh = h;
+              rskip = false;
+              mode = E_RELEASE;
+            } else {
+              mode = E_WAIT;
+            }
+            h = -1;
+            len = 0;
+            break;
+          }
+          case E_TOP: {  // top of the path head x at entry kx > 0 (after a pop)
+            CNT(CNT_EDGE);
+            ++deps;
+            ST_NXT(x, er.x);
+            if (!nb) {
+              atomicAdd(p.R + (size_t)a * n + x, 1u);
+              finished = true;  // kx > 0 here: the control variate counts entry 0 only
+              break;
+            }
+            x = (int32_t)er.x;
+            xo = er.y;
+            xd = er.z;
+            xth = er.w;
+            mode = E_CLAIM;
+            break;
+          }
+          case E_POP: {
+            // cycle x -> ... -> h -> x: free every vertex but x at its next entry
+            CNT(CNT_POP);
+            if (!rskip) {
+              ADD_ST(c, 1ull - (mytag << K_BITS));
+              ++pops;
+            }
+            rskip = false;
+            c = (int32_t)nc;
+            if (c == x) {
+              ADD_ST(x, 1ull);
+              ++pops;
+              ++kx;
+              if (kx >= (uint32_t)K_MASK) {
+                atomicOr(p.err, ERR_OVERFLOW);
+                sh_abort = 1u;
+                mode = E_DONE;
+                break;
+              }
+              // the path now ends at x
+              int32_t pos = len;
+              for (int i = 0; i < PB; ++i)
+                if (i < len && sh_pb[i * W + me] == (uint32_t)x) pos = i;
+              if (pos < PB) len = pos + 1;
+              h = x;
+              mode = E_TOP;
+            }
+            break;
+          }
+          case E_RETRACE: {
+            if (!rskip) OR_ST(c, IN_TREE);
+            rskip = false;
+            if (c == rh) mode = E_IDLE;
+            else c = (int32_t)nc;
+            break;
+          }
+          case E_RELEASE: {
+            ADD_ST(c, 0ull - (mytag << K_BITS));
+            if (c == rh) mode = E_WAIT;
+            else c = (int32_t)nc;
+            break;
+          }
+          case E_WAIT: {
+            CNT(CNT_WAIT);
+            const uint32_t ww = (uint32_t)(wtag & ((1u << W_BITS) - 1));
+            if ((old >> K_BITS) == wtag && sh_gen[ww] == (uint32_t)(wtag >> W_BITS)) break;
+            x = s;
+            mode = E_START;
+            break;
+          }
+          default:
+            break;
+        }
+
+        if (finished) {
+          // the path s -> ... -> h joins the tree: bump the generation, then flag
+          // the remembered prefix and walk the rest
+          if (len > 0) {
+            ++gen;
+            sh_gen[me] = gen;
+            for (int i = 0; i < PB; ++i)
+              if (i < len) OR_ST(sh_pb[i * W + me], IN_TREE);
+            if (len > PB) {
+              c = (int32_t)sh_pb[(PB - 1) * W + me];
+              rh = h;
+              rskip = true;
+              mode = E_RETRACE;
+            } else {
+              mode = E_IDLE;
+            }
+          } else {
+            mode = E_IDLE;
+          }
+          h = -1;
+          len = 0;
+        }
+      }
+
+      if (refill) {
+        // the new window: slots whose vertex is not in the tree yet
+        cp_async_wait_all();
+        __syncwarp();
+        const bool cand = wok && (sh_wst[lane].y & (uint32_t)(IN_TREE >> 32)) == 0u;
+        wmask = __ballot_sync(FULL, cand);
+        if (wb + 32u >= (uint32_t)n) wdone = true;
+      }
+    }
+
+    atomicAdd(&sh_pops, (unsigned long long)pops);
+    atomicAdd(&sh_deps, (unsigned long long)deps);
+#if FC_WILSON_COUNTERS
+#pragma unroll
+    for (int q = 0; q < N_CNT; ++q) {
+      unsigned long long vq = cnt[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) vq += __shfl_xor_sync(FULL, vq, o);
+      if (lane == 0 && vq) atomicAdd(&p.stats[2 + q], vq);
+    }
+#endif
+    __syncthreads();
+    if (p.parents != nullptr) {
+      int32_t* par = p.parents + (size_t)tree * n;
+      for (int32_t v = me; v < n; v += W) par[v] = (int32_t)S[v].nxt;
+    }
+    if (me == 0) {
+      if (p.steps != nullptr) p.steps[tree] = (uint64_t)n + sh_pops;
+      atomicAdd(&p.stats[0], sh_pops);
+      atomicAdd(&p.stats[1], sh_deps);
+    }
+    __syncthreads();
+  }
+#undef ADD_ST
+#undef OR_ST
+#undef LD_NXT
+#undef ST_NXT
+}
+
+WilsonFn wilson_edge_fn(int regs) {
+  if (regs == 40) return k_wilson_edge<40>;
+  if (regs == 48) return k_wilson_edge<48>;
+  return k_wilson_edge<64>;
+}
+
+size_t wilson_edge_smem(int W) {
+  return (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15) + (size_t)W * (16 + 16 + 4);
+}
+
+}  // namespace fcx

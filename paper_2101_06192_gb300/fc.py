@@ -43,6 +43,8 @@ def lib():
             "fc_set_sampler_shape": ([P, I32, I32, I32, I32], ctypes.c_int),
             "fc_sampler_last_shape": ([P, P, P, P], ctypes.c_int),
             "fc_set_start_order": ([P, I32], ctypes.c_int),
+            "fc_set_sampler_kernel": ([P, I32], ctypes.c_int),
+            "fc_sampler_last_kernel": ([P], I32),
             "fc_sampler_counters": ([P, P, I32], ctypes.c_int),
             "fc_sample_usts": ([P, U64, I64, I64, P, P, P, U64, P, P], ctypes.c_int),
             "fc_sampler_stats": ([P, P, P], ctypes.c_int),
@@ -183,8 +185,28 @@ class Graph:
         _check(lib().fc_set_sampler_shape(self._h, walkers_per_tree, max_trees_resident, smem, regs),
                "fc_set_sampler_shape")
 
-    def set_start_order(self, descending: bool):
-        _check(lib().fc_set_start_order(self._h, int(bool(descending))), "fc_set_start_order")
+    START_ORDERS = {"degree": 0, "degree_desc": 1, "id": 2, "id_desc": 3}
+
+    def set_start_order(self, order):
+        """fc_set_start_order: "degree" (default), "degree_desc", "id", "id_desc"
+        (or the integer code; True/False select descending/ascending degree)."""
+        if isinstance(order, bool):
+            code = int(order)
+        elif isinstance(order, str):
+            code = self.START_ORDERS[order]
+        else:
+            code = int(order)
+        _check(lib().fc_set_start_order(self._h, code), "fc_set_start_order")
+
+    kernel_pref = 0
+
+    def set_kernel(self, kernel: int = 0):
+        """fc_set_sampler_kernel: 0 automatic, 1 CSR-walk, 2 edge-record."""
+        _check(lib().fc_set_sampler_kernel(self._h, int(kernel)), "fc_set_sampler_kernel")
+        self.kernel_pref = int(kernel)
+
+    def last_kernel(self) -> int:
+        return int(lib().fc_sampler_last_kernel(self._h))
 
     COUNTERS = ("iterations", "claims", "tree_hits", "confirms", "conflict_waits", "release_waits",
                 "releases", "pop_steps", "tops_k_gt_0", "idle_lane_iterations")

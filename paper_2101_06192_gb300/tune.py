@@ -2,10 +2,13 @@
 
 Walkers per tree and the kernel's register variant trade walker count against
 conflicts between walkers of one tree; the best point depends on the graph
-(short BA walks vs. long grid walks at large alpha).  The tuner times a few
-candidate shapes on one wave of trees of the caller's graph, keeps the fastest
-and caches the choice per (size bucket, mean-degree bucket, weighted, trees)
-in a JSON file next to the built library.  Shapes never change results.
+(short BA walks vs. long grid walks at large alpha), and so does the start
+order (vertex-id order loads start windows coalesced but makes walkers collide
+where ids follow geometry).  The tuner times the start orders, then a few
+candidate shapes, on one wave of trees of the caller's graph, keeps the
+fastest and caches the choice per (size bucket, mean-degree bucket, weighted,
+trees, kernel) in a JSON file next to the built library.  Neither changes
+results.
 """
 from __future__ import annotations
 
@@ -18,7 +21,8 @@ import torch
 
 from . import build as _build
 
-CANDIDATES = [(0, 40), (0, 64), (128, 64), (256, 64), (512, 64), (256, 40)]
+CANDIDATES = [(0, 40), (0, 64), (128, 48), (256, 64), (512, 64), (1024, 48), (1024, 64)]
+ORDERS = ("degree", "id")
 _CACHE = os.path.join(_build.BUILD, "sampler_shapes.json")
 
 
@@ -26,7 +30,7 @@ def _key(G, tau: int) -> str:
     nb = int(math.log2(max(G.n, 1)))
     db = int(math.log2(max(1.0, G.nnz / max(G.n, 1))))
     tb = int(math.log2(max(1, tau * G.n_alpha)))
-    return f"n{nb}_d{db}_w{int(G.weighted)}_a{G.n_alpha}_t{tb}"
+    return f"n{nb}_d{db}_w{int(G.weighted)}_a{G.n_alpha}_t{tb}_k{G.kernel_pref}"
 
 
 def _load():
@@ -37,35 +41,56 @@ def _load():
         return {}
 
 
+def _time(G, seed: int, probe: int):
+    G.sample(seed, min(probe, 8), with_C=False)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G.sample(seed, probe, with_C=False)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0
+
+
+def apply(G, entry: dict):
+    """Apply a tuner entry (start order and shape) to a graph."""
+    G.set_start_order(entry.get("order", "degree"))
+    G.set_shape(entry.get("walkers", 0), 0, 0, entry.get("regs", 0))
+
+
 def autotune(G, tau: int, probe_trees: int | None = None, seed: int = 12345) -> dict:
-    """Pick and apply the fastest (walkers, regs) for G at tau trees per alpha."""
+    """Pick and apply the fastest start order, then the fastest (walkers,
+    regs), for G at tau trees per alpha."""
     key = _key(G, tau)
     cache = _load()
     if key in cache:
-        w, r = cache[key]["walkers"], cache[key]["regs"]
-        G.set_shape(w, 0, 0, r)
+        apply(G, cache[key])
         return dict(cache[key], cached=True)
     probe = probe_trees or max(1, min(tau, 1024 // max(1, G.n_alpha)))
+    G.set_shape(0, 0, 0, 0)
+    order, best_t = "degree", None
+    for o in ORDERS:
+        try:
+            G.set_start_order(o)
+            dt = _time(G, seed, probe)
+        except Exception:
+            continue
+        if best_t is None or dt < best_t:
+            order, best_t = o, dt
+    G.set_start_order(order)
     best = None
     for w, r in CANDIDATES:
         try:
             G.set_shape(w, 0, 0, r)
-            G.sample(seed, min(probe, 8), with_C=False)  # warm-up
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            G.sample(seed, probe, with_C=False)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
+            dt = _time(G, seed, probe)
         except Exception:
             continue
         if best is None or dt < best[0]:
             best = (dt, w, r, G.last_shape())
     if best is None:
         G.set_shape(0, 0, 0, 0)
-        return {"walkers": 0, "regs": 0}
+        return {"walkers": 0, "regs": 0, "order": order}
     dt, w, r, shp = best
-    G.set_shape(w, 0, 0, r)
-    entry = {"walkers": w, "regs": r, "probe_trees": probe, "probe_ms": dt * 1e3, "shape": shp}
+    entry = {"walkers": w, "regs": r, "order": order, "probe_trees": probe, "probe_ms": dt * 1e3, "shape": shp}
+    apply(G, entry)
     cache[key] = entry
     try:
         os.makedirs(os.path.dirname(_CACHE), exist_ok=True)

@@ -1,0 +1,142 @@
+"""The edge-record sampler kernel (unweighted single graphs, one dependent
+round trip per walk step) against the oracle: bit-exact trees, counts and step
+counters for every start order and launch shape, including the edge cases of
+the graph (isolated vertices, stars, paths) and of the walk (long paths that
+overflow the remembered prefix, many colliding walkers)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import native
+
+pytestmark = pytest.mark.gpu
+
+fc = pytest.importorskip("paper_2101_06192_gb300.fc")
+
+
+def _np32(t):
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+def _check(G, g, alphas, seed, tau, tree_offset=0):
+    out = G.sample(seed, tau, tree_offset=tree_offset, want_parents=True, want_steps=True)
+    torch.cuda.synchronize()
+    assert G.last_kernel() == 2
+    n = g.n
+    R = _np32(out["R"]).reshape(len(alphas), n)
+    C = _np32(out["C"]).reshape(len(alphas), n)
+    par = out["parents"].cpu().numpy()
+    steps = out["steps"].cpu().numpy()
+    for a, al in enumerate(alphas):
+        ref = native.wilson(g, al, seed=seed, tau=tau, tree_offset=tree_offset, alpha_idx=a, want_parents=True)
+        np.testing.assert_array_equal(par[a], ref["parents"], err_msg=f"parents alpha {a}")
+        np.testing.assert_array_equal(R[a], ref["R"], err_msg=f"R alpha {a}")
+        np.testing.assert_array_equal(C[a], ref["C"], err_msg=f"C alpha {a}")
+        np.testing.assert_array_equal(steps[a].astype(np.uint64), ref["steps"], err_msg=f"steps alpha {a}")
+    return out
+
+
+@pytest.mark.parametrize("order", ["id", "id_desc", "degree", "degree_desc"])
+@pytest.mark.parametrize("walkers,regs", [(0, 0), (32, 40), (256, 48), (1024, 64)])
+def test_er_trees_bit_exact(order, walkers, regs):
+    g = synth.erdos_renyi(1000, 8, 1)
+    G = fc.Graph.from_csr(g, [1.0])
+    G.set_kernel(2)
+    G.set_shape(walkers, 0, 1, regs)
+    G.set_start_order(order)
+    _check(G, g, [1.0], seed=2021, tau=200)
+    G.close()
+
+
+@pytest.mark.parametrize("kind", ["ba", "grid_small_alpha", "torus", "rmat"])
+def test_graph_families_bit_exact(kind):
+    if kind == "ba":
+        g, alphas, tau = synth.barabasi_albert(3000, 3, 5), [1.0], 64
+    elif kind == "grid_small_alpha":
+        # long walks (alpha small): paths longer than the remembered prefix
+        g, alphas, tau = synth.perturbed_grid(60, 50, 4, weighted=False), [0.02, 3.0], 24
+    elif kind == "torus":
+        g, alphas, tau = synth.torus(40, 30), [0.05], 24
+    else:
+        g, alphas, tau = synth.rmat(12, 8, 3), [0.5, 8.0], 32
+    G = fc.Graph.from_csr(g, alphas)
+    G.set_kernel(2)
+    for walkers in (0, 512):
+        G.set_shape(walkers, 0, 1)
+        _check(G, g, alphas, seed=99, tau=tau)
+    G.close()
+
+
+@pytest.mark.parametrize("name", ["single", "empty", "star", "path", "K8", "isolated_mix"])
+def test_edge_cases_bit_exact(name):
+    if name == "single":
+        g = synth.empty(1)
+    elif name == "empty":
+        g = synth.empty(37)
+    elif name == "star":
+        g = synth.star(300)
+    elif name == "path":
+        g = synth.path(500)
+    elif name == "K8":
+        g = synth.complete(8)
+    else:
+        base = synth.barabasi_albert(400, 2, 9)
+        u, v, _ = base.edges()
+        g = synth.from_edges(1000, u, v)
+    alphas = [0.5, 2.0]
+    G = fc.Graph.from_csr(g, alphas)
+    if g.nnz == 0:
+        # no edge records without edges: the automatic choice is the CSR-walk kernel
+        with pytest.raises(fc.FcError):
+            G.set_kernel(2)
+        G.close()
+        return
+    G.set_kernel(2)
+    for walkers in (32, 64):
+        G.set_shape(walkers, 0, 1)
+        out = _check(G, g, alphas, seed=11, tau=50)
+    iso = g.degrees() == 0
+    R = _np32(out["R"]).reshape(2, g.n)
+    assert np.all(R[:, iso] == 50)
+    G.close()
+
+
+def test_both_kernels_agree_and_default_is_edge_kernel():
+    g = synth.barabasi_albert(50_000, 4, 8)
+    G = fc.Graph.from_csr(g, [1.0])
+    outs = []
+    for k in (0, 1, 2):
+        G.set_kernel(k)
+        o = G.sample(4, 64, want_parents=True, want_steps=True)
+        torch.cuda.synchronize()
+        outs.append((k, G.last_kernel(), o))
+    assert outs[0][1] == 2 and outs[1][1] == 1 and outs[2][1] == 2
+    for key in ("parents", "R", "C", "steps"):
+        for _, _, o in outs[1:]:
+            assert torch.equal(o[key], outs[0][2][key]), key
+    G.close()
+
+
+def test_weighted_graph_has_no_edge_records():
+    g = synth.perturbed_grid(20, 20, 1)
+    G = fc.Graph.from_csr(g, [1.0])
+    with pytest.raises(fc.FcError):
+        G.set_kernel(2)
+    G.sample(1, 4)
+    assert G.last_kernel() == 1
+    G.close()
+
+
+def test_edge_kernel_watchdog_and_recovery():
+    g = synth.barabasi_albert(20000, 4, 1)
+    G = fc.Graph.from_csr(g, [1.0])
+    G.set_kernel(2)
+    G.set_shape(64, 0, 1)
+    with pytest.raises(fc.FcError) as e:
+        G.sample(3, 8, max_steps_per_tree=5)
+    assert e.value.status == fc.FC_ETIMEOUT
+    out = G.sample(3, 8)
+    ref = native.wilson(g, 1.0, seed=3, tau=8)
+    np.testing.assert_array_equal(_np32(out["R"]), ref["R"])
+    G.close()

@@ -17,21 +17,25 @@ def test_start_order_and_shape_invariance(kind):
     if kind == "ba":
         g, alphas, tau = synth.barabasi_albert(30_000, 4, 2), [1.0], 96
     elif kind == "grid":
-        g, alphas, tau = synth.perturbed_grid(120, 100, 3), [0.1, 10.0], 48
+        g, alphas, tau = synth.perturbed_grid(120, 100, 3, weighted=False), [0.1, 10.0], 48
     else:
         g, alphas, tau = synth.erdos_renyi(2000, 3, 5), [2.0], 128
     G = fc.Graph.from_csr(g, alphas)
     ref = None
-    for desc in (0, 1):
-        for walkers, smem in ((0, 0), (1024, 1), (64, 1), (32, 0)):
-            G.set_start_order(desc)
-            G.set_shape(walkers, 0, smem)
-            out = G.sample(17, tau, want_parents=True, want_steps=True)
-            cur = (out["parents"].cpu().numpy(), out["R"].cpu().numpy(), out["C"].cpu().numpy(),
-                   out["steps"].cpu().numpy())
-            if ref is None:
-                ref = cur
-            else:
-                for x, y in zip(cur, ref):
-                    np.testing.assert_array_equal(x, y, err_msg=f"desc={desc} walkers={walkers} smem={smem}")
+    kernels = (1, 2) if g.w is None else (1,)
+    for kernel in kernels:
+        G.set_kernel(kernel)
+        for order in ("degree", "degree_desc", "id", "id_desc"):
+            for walkers, smem in ((0, 0), (1024, 1), (64, 1), (32, 0)):
+                G.set_start_order(order)
+                G.set_shape(walkers, 0, smem)
+                out = G.sample(17, tau, want_parents=True, want_steps=True)
+                cur = (out["parents"].cpu().numpy(), out["R"].cpu().numpy(), out["C"].cpu().numpy(),
+                       out["steps"].cpu().numpy())
+                if ref is None:
+                    ref = cur
+                else:
+                    for x, y in zip(cur, ref):
+                        np.testing.assert_array_equal(
+                            x, y, err_msg=f"kernel={kernel} order={order} walkers={walkers} smem={smem}")
     G.close()
