@@ -66,17 +66,23 @@ def dist_env():
     return rank, world, local
 
 
-def profiled_traffic():
+def profiled_traffic(kname, launched):
     """DRAM bytes per sampler launch from the committed ncu summary, if the
-    sampler source is unchanged since that capture (else None)."""
+    summary covers the kernel and launch shape that ran and the kernel source
+    is unchanged since that capture (else None)."""
     import hashlib
-    prof = os.path.join(ROOT, "profiles", "k_wilson_ba_n2e20_tau1024.md")
-    src = [os.path.join(ROOT, "paper_2101_06192_gb300", "csrc", f) for f in ("fc_wilson.cu", "fc_internal.cuh")]
+    prof = os.path.join(ROOT, "profiles", "k_wilson_edge_ba_n2e20_tau1024.md")
+    src = [os.path.join(ROOT, "paper_2101_06192_gb300", "csrc", f)
+           for f in ("fc_wilson_edge.cu", "fc_wilson_common.cuh", "fc_internal.cuh")]
     try:
         txt = open(prof).read()
         h = hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()[:16]
-        vals = dict(ln.split(":", 1) for ln in txt.splitlines() if ln.startswith(("traffic_bytes:", "kernel_src")))
-        if vals.get("kernel_src_sha256_16", "").strip() != h:
+        vals = {k.strip(): v.strip() for k, v in (ln.split(":", 1) for ln in txt.splitlines()
+                                                   if ln.startswith(("traffic_bytes:", "kernel_src", "launch:")))}
+        if vals.get("kernel_src_sha256_16") != h:
+            return None
+        want = f"{kname} walkers={launched.get('walkers_per_tree')} ctas={launched.get('ctas')}"
+        if vals.get("launch") != want:
             return None
         return float(vals["traffic_bytes"])
     except Exception:
@@ -469,6 +475,7 @@ def main():
     stream = torch.cuda.current_stream()
     tree_offset = rank * tau
     shape = {}
+    launched = {}
     from paper_2101_06192_gb300 import tune
 
     def step(seed, host_inputs=False, samp_ev=None, stats=None):
@@ -486,6 +493,7 @@ def main():
             samp_ev[1].record(stream)
         if stats is not None:
             stats.append(G.sampler_stats())
+            launched.update(kernel=G.last_kernel(), **G.last_shape())
         x, _ = G.pivot_solve(rel_tol=1e-9)
         diag, far, clo = G.farness(R, tau, x_pivot=x)
         top = fc.top_k(diag, TOPK)
@@ -565,11 +573,13 @@ def main():
     samp_s = statistics.mean(samp_ms) / 1000.0
     achieved = alg_bytes / samp_s / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    traffic = profiled_traffic() if (args.n_log2 == N_LOG2 and tau == TAU) else None
+    kname = {2: "k_wilson_edge<false, {r}>", 3: "k_wilson_edge<true, {r}>"}.get(
+        launched.get("kernel"), "k_wilson<false, {r}>").format(r=launched.get("regs"))
+    traffic = profiled_traffic(kname, launched) if (args.n_log2 == N_LOG2 and tau == TAU) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_over_algorithmic": (traffic / alg_bytes) if traffic else None,
-                "kernel": "k_wilson<false>",
+                "kernel": kname, "launch": launched,
                 "peak_source": peak_kind, "kernel_ms": 1000.0 * samp_s,
                 "departures_per_launch": deps, "pops_per_launch": pops}
 

@@ -140,8 +140,12 @@ fc_status fc_set_start_order(fc_graph* g, int32_t order);
  * CSR-walk kernel), 1 = CSR-walk kernel, 2 = edge-record kernel (FC_EINVAL if
  * g has no edge records: weighted graphs and batches).  Both draw the same
  * random stacks, so the trees are identical; only speed differs.
- * fc_sampler_last_kernel returns the kernel of the last launch on g (1 or 2;
- * 0 before any launch).
+ * The edge-record kernel keeps each tree's in-tree bitmap in shared memory
+ * when it fits (n/8 bytes next to the walker arrays) unless fc_set_sampler_shape
+ * forces global tree state (smem = 1), in which case membership is a flag in
+ * the state words.  fc_sampler_last_kernel returns the kernel of the last
+ * launch on g: 1 = CSR-walk, 2 = edge-record with state flags, 3 = edge-record
+ * with the shared-memory bitmap; 0 before any launch.
  */
 fc_status fc_set_sampler_kernel(fc_graph* g, int32_t kernel);
 int32_t fc_sampler_last_kernel(const fc_graph* g);

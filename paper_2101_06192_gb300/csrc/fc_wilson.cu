@@ -482,6 +482,8 @@ static WilsonFn wilson_fn(bool smem, int regs) {
   return k_wilson<false, 64>;
 }
 
+constexpr size_t SBITS_CARVEOUT = 196 * 1024 - 1024 - 256;  // minus the per-CTA reserve and static shared memory
+
 struct Shape {
   int W = 0;
   int regs = 64;
@@ -491,8 +493,8 @@ struct Shape {
 // Launch shape: the largest walker count whose CTAs hold every tree of the
 // launch in one wave (trees of one launch take about equally long), else the
 // shape with the most walkers resident.  Walkers per tree are capped at n/8.
-static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool smem, bool edge, int nsm,
-                              Shape* out) {
+static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool smem, bool edge, bool sbits,
+                              int nsm, int smem_optin, Shape* out) {
   const int wcap = std::max(32, std::min(1024, (int)((n / 8) & ~31)));
   // measured on GB300 (BA n = 2^20, tau = 1024): the 40-register variant is
   // fastest; graphs with long walks prefer more walkers per tree, which the
@@ -504,9 +506,20 @@ static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool 
     if (g->regs > 0 && ri > 0) break;
     if (!edge && regs == 48) regs = 40;
     if (edge && regs == 32) regs = 40;
-    const WilsonFn fn = edge ? wilson_edge_fn(regs) : wilson_fn(smem, regs);
+    const WilsonFn fn = edge ? wilson_edge_fn(sbits, regs) : wilson_fn(smem, regs);
     for (int W = (g->walkers > 0 ? g->walkers : wcap); W >= 32; W -= 32) {
-      const size_t shb = edge ? wilson_edge_smem(W) : smem_bytes(W, n, smem);
+      const size_t shb = edge ? wilson_edge_smem(W, n, sbits) : smem_bytes(W, n, smem);
+      if (shb + 64 > (size_t)smem_optin) {
+        if (g->walkers > 0) break;
+        continue;
+      }
+      // measured on GB300 (BA n = 2^20): with the shared-memory bitmap, a CTA
+      // that needs more than the 196 KB shared-memory carveout step runs about
+      // 20% slower than one just below it (the L1 left for register spills
+      // shrinks); automatic shapes stay below the step when they can
+      if (sbits && g->walkers == 0 && shb > SBITS_CARVEOUT &&
+          wilson_edge_smem(32, n, true) <= SBITS_CARVEOUT)
+        continue;
       if (edge) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
       if (smem) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
       int per_sm = 0;
@@ -614,13 +627,17 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
     set_error("fc_sample_usts: the edge-record kernel needs an unweighted single graph with global state");
     return FC_EINVAL;
   }
+  // edge-record kernel: in-tree bitmap in shared memory when it fits (unless
+  // global tree state is forced)
+  const bool sbits = edge && g->smem_mode != 1 &&
+                     wilson_edge_smem(g->walkers > 0 ? g->walkers : 32, nmax, true) + 64 <= (size_t)dev_smem_optin;
   Shape sh;
   {
-    const fc_status r = choose_shape(g, nmax, total, use_smem, edge, nsm, &sh);
+    const fc_status r = choose_shape(g, nmax, total, use_smem, edge, sbits, nsm, dev_smem_optin, &sh);
     if (r != FC_OK) return r;
   }
   const int W = sh.W;
-  const size_t shb = edge ? wilson_edge_smem(W) : smem_bytes(W, nmax, use_smem);
+  const size_t shb = edge ? wilson_edge_smem(W, nmax, sbits) : smem_bytes(W, nmax, use_smem);
   int64_t grid = std::min<int64_t>(total, (int64_t)sh.per_sm * nsm);
   if (g->max_trees > 0) grid = std::min<int64_t>(grid, g->max_trees);
   void* gstate = nullptr;
@@ -640,7 +657,7 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   g->last_W = W;
   g->last_regs = sh.regs;
   g->last_grid = (int32_t)grid;
-  g->last_kernel = edge ? 2 : 1;
+  g->last_kernel = edge ? (sbits ? 3 : 2) : 1;
   WParams p;
   p.n = n;
   p.n_alpha = g->n_alpha;
@@ -702,7 +719,7 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   FC_CK(cudaMemsetAsync(g->d_counter, 0, sizeof(unsigned long long), st));
   if (sync) FC_CK(cudaMemsetAsync(g->d_err, 0, sizeof(uint32_t), st));
   FC_CK(cudaMemsetAsync(g->d_stats, 0, (2 + N_CNT) * sizeof(unsigned long long), st));
-  const WilsonFn fn = edge ? wilson_edge_fn(sh.regs) : wilson_fn(use_smem, sh.regs);
+  const WilsonFn fn = edge ? wilson_edge_fn(sbits, sh.regs) : wilson_fn(use_smem, sh.regs);
   if (use_smem || edge) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
   fn<<<(unsigned)grid, W, shb, st>>>(p);
   FC_LAUNCHED();

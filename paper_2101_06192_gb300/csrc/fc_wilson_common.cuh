@@ -122,9 +122,10 @@ __device__ __forceinline__ uint32_t ld_volatile32(const uint32_t* a) {
 
 typedef void (*WilsonFn)(WParams);
 
-// Edge-record kernel (unweighted single graphs, state in global memory) for a
-// register cap of 40, 48 or 64, and its dynamic shared memory per CTA.
-WilsonFn wilson_edge_fn(int regs);
-size_t wilson_edge_smem(int W);
+// Edge-record kernel (unweighted single graphs, state in global memory) with
+// the in-tree bitmap in shared memory (sbits) or as flags in the state words,
+// for a register cap of 40, 48 or 64, and its dynamic shared memory per CTA.
+WilsonFn wilson_edge_fn(bool sbits, int regs);
+size_t wilson_edge_smem(int W, int32_t n, bool sbits);
 
 }  // namespace fcx

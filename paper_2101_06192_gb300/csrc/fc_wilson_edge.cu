@@ -62,7 +62,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 }  // namespace
 
-template <int MAXREG>
+// SBITS: the tree's in-tree bitmap lives in shared memory (graphs whose n/8
+// bytes fit next to the walker arrays).  A claim then first tests x's bit and
+// touches neither x's state nor an edge record when x is already in the tree,
+// and finished paths are marked in the bitmap instead of the state words.
+template <bool SBITS, int MAXREG>
 __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long sh_tree, sh_pops, sh_deps;
@@ -79,6 +83,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
   uint4* sh_wri = (uint4*)(smem_raw + (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15));
   uint4* sh_wst = sh_wri + W;
   uint32_t* sh_wv = (uint32_t*)(sh_wst + W);
+  volatile uint32_t* sh_bits = (volatile uint32_t*)(sh_wv + W);  // [ceil(n / 32)] (SBITS)
   sh_wri += me & ~31;
   sh_wst += me & ~31;
   sh_wv += me & ~31;
@@ -104,6 +109,8 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
     const uint32_t tg = (uint32_t)(p.tree_offset + tloc);
     if (!(first_tree && p.pre_cleared))
       for (int32_t v = me; v < n; v += W) reinterpret_cast<uint4&>(S[v]) = make_uint4(0u, 0u, 0u, 0u);
+    if (SBITS)
+      for (int32_t q = me; q < ((n + 31) >> 5); q += W) sh_bits[q] = 0u;
     first_tree = false;
     sh_gen[me] = 1u;
     if (me == 0) {
@@ -186,7 +193,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
           const int32_t v = p.id_order ? (int32_t)ix : __ldg(p.order + ix);
           sh_wv[lane] = (uint32_t)v;
           cp_async16(&sh_wri[lane], rinfo + v);
-          cp_async16(&sh_wst[lane], &S[v]);
+          if (!SBITS) cp_async16(&sh_wst[lane], &S[v]);
         }
         cp_async_commit();
       }
@@ -196,7 +203,8 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
 
         // ---- issue: claim x and, speculatively, load the record its top selects ----
         unsigned long long old = 0ull;
-        if (mode == E_CLAIM) old = atomicCAS(&S[x].st, 0ull, mytag << K_BITS);
+        const bool hit = SBITS && mode == E_CLAIM && ((sh_bits[x >> 5] >> (x & 31)) & 1u);
+        if (mode == E_CLAIM && !hit) old = atomicCAS(&S[x].st, 0ull, mytag << K_BITS);
         else if (mode == E_CLAIM2) old = atomicCAS(&S[x].st, cexp, (mytag << K_BITS) | (cexp & K_MASK));
         else if (mode == E_WAIT) old = ld_volatile(&S[x].st);
         uint4 ri = make_uint4(0u, 0u, 0u, 0u);
@@ -204,7 +212,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
         const bool walk = (mode == E_POP) || (mode == E_RETRACE) || (mode == E_RELEASE);
         uint32_t nc = 0;
         if (walk) nc = LD_NXT(c);
-        const bool topc = (mode == E_CLAIM) || (mode == E_CLAIM2) || (mode == E_TOP);
+        const bool topc = (mode == E_CLAIM && !hit) || (mode == E_CLAIM2) || (mode == E_TOP);
         bool nb = false;
         uint4 er = make_uint4((uint32_t)n, 0u, 0u, 0u);
         if (topc) {
@@ -233,6 +241,11 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
           }
           case E_CLAIM:
           case E_CLAIM2: {
+            if (hit) {
+              CNT(CNT_TREE_HIT);
+              finished = true;
+              break;
+            }
             if (mode == E_CLAIM ? (old == 0ull) : (old == cexp)) {
               // x joins this walker's path with its top at entry kx
               CNT(CNT_CLAIM_OK);
@@ -368,7 +381,10 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             break;
           }
           case E_RETRACE: {
-            if (!rskip) OR_ST(c, IN_TREE);
+            if (!rskip) {
+              if (SBITS) atomicOr((uint32_t*)&sh_bits[c >> 5], 1u << (c & 31));
+              else OR_ST(c, IN_TREE);
+            }
             rskip = false;
             if (c == rh) mode = E_IDLE;
             else c = (int32_t)nc;
@@ -399,7 +415,11 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             ++gen;
             sh_gen[me] = gen;
             for (int i = 0; i < PB; ++i)
-              if (i < len) OR_ST(sh_pb[i * W + me], IN_TREE);
+              if (i < len) {
+                const uint32_t v = sh_pb[i * W + me];
+                if (SBITS) atomicOr((uint32_t*)&sh_bits[v >> 5], 1u << (v & 31));
+                else OR_ST(v, IN_TREE);
+              }
             if (len > PB) {
               c = (int32_t)sh_pb[(PB - 1) * W + me];
               rh = h;
@@ -420,7 +440,15 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
         // the new window: slots whose vertex is not in the tree yet
         cp_async_wait_all();
         __syncwarp();
-        const bool cand = wok && (sh_wst[lane].y & (uint32_t)(IN_TREE >> 32)) == 0u;
+        bool cand = wok;
+        if (wok) {
+          if (SBITS) {
+            const uint32_t v = sh_wv[lane];
+            cand = ((sh_bits[v >> 5] >> (v & 31)) & 1u) == 0u;
+          } else {
+            cand = (sh_wst[lane].y & (uint32_t)(IN_TREE >> 32)) == 0u;
+          }
+        }
         wmask = __ballot_sync(FULL, cand);
         if (wb + 32u >= (uint32_t)n) wdone = true;
       }
@@ -455,14 +483,20 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
 #undef ST_NXT
 }
 
-WilsonFn wilson_edge_fn(int regs) {
-  if (regs == 40) return k_wilson_edge<40>;
-  if (regs == 48) return k_wilson_edge<48>;
-  return k_wilson_edge<64>;
+WilsonFn wilson_edge_fn(bool sbits, int regs) {
+  if (sbits) {
+    if (regs == 40) return k_wilson_edge<true, 40>;
+    if (regs == 48) return k_wilson_edge<true, 48>;
+    return k_wilson_edge<true, 64>;
+  }
+  if (regs == 40) return k_wilson_edge<false, 40>;
+  if (regs == 48) return k_wilson_edge<false, 48>;
+  return k_wilson_edge<false, 64>;
 }
 
-size_t wilson_edge_smem(int W) {
-  return (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15) + (size_t)W * (16 + 16 + 4);
+size_t wilson_edge_smem(int W, int32_t n, bool sbits) {
+  return (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15) + (size_t)W * (16 + 16 + 4) +
+         (sbits ? (((size_t)n + 31) / 32) * 4 : 0);
 }
 
 }  // namespace fcx

@@ -21,7 +21,8 @@ import torch
 
 from . import build as _build
 
-CANDIDATES = [(0, 40), (0, 64), (128, 48), (256, 64), (512, 64), (1024, 48), (1024, 64)]
+CANDIDATES = [(0, 40), (0, 64), (128, 48), (256, 64), (512, 64), (640, 64), (768, 64), (896, 64), (896, 48),
+              (1024, 64)]
 ORDERS = ("degree", "id")
 _CACHE = os.path.join(_build.BUILD, "sampler_shapes.json")
 

@@ -22,7 +22,7 @@ def _np32(t):
 def _check(G, g, alphas, seed, tau, tree_offset=0):
     out = G.sample(seed, tau, tree_offset=tree_offset, want_parents=True, want_steps=True)
     torch.cuda.synchronize()
-    assert G.last_kernel() == 2
+    assert G.last_kernel() in (2, 3)
     n = g.n
     R = _np32(out["R"]).reshape(len(alphas), n)
     C = _np32(out["C"]).reshape(len(alphas), n)
@@ -39,13 +39,15 @@ def _check(G, g, alphas, seed, tau, tree_offset=0):
 
 @pytest.mark.parametrize("order", ["id", "id_desc", "degree", "degree_desc"])
 @pytest.mark.parametrize("walkers,regs", [(0, 0), (32, 40), (256, 48), (1024, 64)])
-def test_er_trees_bit_exact(order, walkers, regs):
+@pytest.mark.parametrize("smem", [0, 1])  # 0: in-tree bitmap in shared memory, 1: flags in the state words
+def test_er_trees_bit_exact(order, walkers, regs, smem):
     g = synth.erdos_renyi(1000, 8, 1)
     G = fc.Graph.from_csr(g, [1.0])
     G.set_kernel(2)
-    G.set_shape(walkers, 0, 1, regs)
+    G.set_shape(walkers, 0, smem, regs)
     G.set_start_order(order)
     _check(G, g, [1.0], seed=2021, tau=200)
+    assert G.last_kernel() == (3 if smem == 0 else 2)
     G.close()
 
 
@@ -62,8 +64,8 @@ def test_graph_families_bit_exact(kind):
         g, alphas, tau = synth.rmat(12, 8, 3), [0.5, 8.0], 32
     G = fc.Graph.from_csr(g, alphas)
     G.set_kernel(2)
-    for walkers in (0, 512):
-        G.set_shape(walkers, 0, 1)
+    for walkers, smem in ((0, 1), (512, 1), (0, 0), (1024, 0)):
+        G.set_shape(walkers, 0, smem)
         _check(G, g, alphas, seed=99, tau=tau)
     G.close()
 
@@ -93,8 +95,8 @@ def test_edge_cases_bit_exact(name):
         G.close()
         return
     G.set_kernel(2)
-    for walkers in (32, 64):
-        G.set_shape(walkers, 0, 1)
+    for walkers, smem in ((32, 1), (64, 1), (32, 0), (64, 0)):
+        G.set_shape(walkers, 0, smem)
         out = _check(G, g, alphas, seed=11, tau=50)
     iso = g.degrees() == 0
     R = _np32(out["R"]).reshape(2, g.n)
@@ -111,7 +113,7 @@ def test_both_kernels_agree_and_default_is_edge_kernel():
         o = G.sample(4, 64, want_parents=True, want_steps=True)
         torch.cuda.synchronize()
         outs.append((k, G.last_kernel(), o))
-    assert outs[0][1] == 2 and outs[1][1] == 1 and outs[2][1] == 2
+    assert outs[0][1] in (2, 3) and outs[1][1] == 1 and outs[2][1] in (2, 3)
     for key in ("parents", "R", "C", "steps"):
         for _, _, o in outs[1:]:
             assert torch.equal(o[key], outs[0][2][key]), key
@@ -128,11 +130,12 @@ def test_weighted_graph_has_no_edge_records():
     G.close()
 
 
-def test_edge_kernel_watchdog_and_recovery():
+@pytest.mark.parametrize("smem", [0, 1])
+def test_edge_kernel_watchdog_and_recovery(smem):
     g = synth.barabasi_albert(20000, 4, 1)
     G = fc.Graph.from_csr(g, [1.0])
     G.set_kernel(2)
-    G.set_shape(64, 0, 1)
+    G.set_shape(64, 0, smem)
     with pytest.raises(fc.FcError) as e:
         G.sample(3, 8, max_steps_per_tree=5)
     assert e.value.status == fc.FC_ETIMEOUT
