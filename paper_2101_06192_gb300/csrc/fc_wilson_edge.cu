@@ -19,9 +19,9 @@
 //    u53 >= T; only u_hi == T_hi (probability about 2^-32 per step) reads the
 //    full T from the row info.
 //  * Start vertices are handed out per warp from windows of 32 consecutive
-//    positions of the start order; the warp loads the 32 state words and row
-//    infos together (coalesced in vertex-id order) and keeps only vertices
-//    not yet in the tree.
+//    positions of the start order; the warp fetches the 32 row infos (and
+//    state words) together (coalesced in vertex-id order) and keeps only the
+//    vertices not yet in the tree, compacted to the front of the window.
 //
 // State word: bits 0..23 k (stack entries popped), bits 24..62 tag
 // ((gen << 10) | walker, 0 = free), bit 63 in-tree flag.
@@ -39,16 +39,6 @@ enum { E_IDLE = 0, E_START, E_CLAIM, E_CLAIM2, E_TOP, E_POP, E_RETRACE, E_RELEAS
 __device__ __forceinline__ uint32_t thr_hi(const uint4& ri) {
   const uint64_t T = (uint64_t)ri.z | ((uint64_t)ri.w << 32);
   return T >= (1ull << 53) ? 0xffffffffu : (uint32_t)(T >> 21);
-}
-
-// Position of set bit number r (0-based) of m; requires r < popc(m).  The
-// result is in [0, 31] for every input.
-__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t r) {
-  uint32_t pos = 0;
-#pragma unroll
-  for (int sh = 16; sh > 0; sh >>= 1)
-    if ((uint32_t)__popc(m & ((1u << (pos + sh)) - 1u)) <= r) pos += sh;
-  return pos;
 }
 
 // Asynchronous 16-byte global -> shared copies (through L2), used to fetch the
@@ -129,7 +119,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
     bool rskip = false;
     uint32_t gen = 1, kx = 0, iters = 0, pops = 0, deps = 0;
     unsigned long long wtag = 0, cexp = 0;
-    uint32_t wmask = 0;   // warp-uniform: window slots not handed out yet
+    uint32_t whead = 0, wcnt = 0;  // warp-uniform: window entries [whead, wcnt) not handed out yet
     bool wdone = false;   // warp-uniform: the start order is exhausted
 #if FC_WILSON_COUNTERS
     uint32_t cnt[N_CNT];
@@ -148,11 +138,11 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
       const unsigned want = __ballot_sync(FULL, need);
       bool refill = false;  // warp-uniform
       if (want) {
-        const uint32_t nw = (uint32_t)__popc(want), na = (uint32_t)__popc(wmask);
+        const uint32_t nw = (uint32_t)__popc(want), na = wcnt - whead;
         if (need) {
           const uint32_t r = (uint32_t)__popc(want & lt_mask);
           if (r < na) {
-            const uint32_t slot = nth_set_bit(wmask, r);
+            const uint32_t slot = whead + r;
             const uint4 wr = sh_wri[slot];
             s = x = (int32_t)sh_wv[slot];
             xo = wr.x;
@@ -165,7 +155,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             mode = E_DONE;
           }
         }
-        wmask = nw >= na ? 0u : (wmask & ~((2u << nth_set_bit(wmask, nw - 1u)) - 1u));
+        whead = nw >= na ? wcnt : whead + nw;
         refill = nw > na && !wdone;
       }
       bool act = !fin && mode != E_IDLE && mode != E_DONE;
@@ -449,7 +439,22 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             cand = (sh_wst[lane].y & (uint32_t)(IN_TREE >> 32)) == 0u;
           }
         }
-        wmask = __ballot_sync(FULL, cand);
+        // compact the candidates to the front of the window
+        uint4 wr = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t wv = 0;
+        if (cand) {
+          wr = sh_wri[lane];
+          wv = sh_wv[lane];
+        }
+        const unsigned cm = __ballot_sync(FULL, cand);
+        if (cand) {
+          const uint32_t pos = (uint32_t)__popc(cm & lt_mask);  // <= lane: read above, before this write
+          sh_wri[pos] = wr;
+          sh_wv[pos] = wv;
+        }
+        __syncwarp();
+        whead = 0;
+        wcnt = (uint32_t)__popc(cm);
         if (wb + 32u >= (uint32_t)n) wdone = true;
       }
     }
