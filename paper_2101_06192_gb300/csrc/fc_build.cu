@@ -341,6 +341,26 @@ __global__ void k_edge_records(int64_t nnz, const int32_t* __restrict__ colidx, 
   }
 }
 
+// Weighted edge records (64 bytes): the header above, then the high words
+// (bits 32..52) of the target's slot thresholds B_0 .. B_11 (unused entries
+// all ones).
+__global__ void k_edge_records_w(int64_t nnz, const int32_t* __restrict__ colidx, const uint4* __restrict__ rowinfo,
+                                 const uint64_t* __restrict__ B, uint4* __restrict__ edges) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t t = colidx[e];
+    const uint4 ri = rowinfo[t];
+    const uint64_t T = (uint64_t)ri.z | ((uint64_t)ri.w << 32);
+    uint32_t h[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) h[j] = (uint32_t)j + 1u < ri.y ? (uint32_t)(B[(size_t)ri.x + j] >> 32) : 0xffffffffu;
+    uint4* r = edges + (size_t)e * 4;
+    r[0] = make_uint4((uint32_t)t, ri.x, ri.y, T >= (1ull << 53) ? 0xffffffffu : (uint32_t)(T >> 21));
+    r[1] = make_uint4(h[0], h[1], h[2], h[3]);
+    r[2] = make_uint4(h[4], h[5], h[6], h[7]);
+    r[3] = make_uint4(h[8], h[9], h[10], h[11]);
+  }
+}
+
 static void free_graph_arrays(fc_graph* g, cudaStream_t st) {
   void* ptrs[] = {g->rowptr, g->colidx, g->w, g->deg, g->dw, g->S, g->order, g->rowinfo, g->B, g->edges,
                   g->alphas_d, g->d_err, g->d_counter, g->d_stats, g->voff, g->gid, g->alpha_v,
@@ -571,11 +591,16 @@ static fc_status build_impl(int32_t n, int64_t nnz, const int64_t* rowptr, const
       BUILD_CK((fcx::note_launch(), cudaGetLastError()));
     }
   }
-  if (!g->weighted && g->num_graphs == 0 && nnz > 0) {
-    BUILD_CK(cudaMallocAsync((void**)&g->edges, (size_t)nnz * n_alpha * sizeof(uint4), st));
+  if (g->num_graphs == 0 && nnz > 0) {
+    const size_t rec = g->weighted ? 4 : 1;  // uint4 per record
+    BUILD_CK(cudaMallocAsync((void**)&g->edges, (size_t)nnz * n_alpha * rec * sizeof(uint4), st));
     for (int a = 0; a < n_alpha; ++a) {
-      k_edge_records<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, g->colidx, g->rowinfo + (size_t)a * n,
-                                                        g->edges + (size_t)a * nnz);
+      if (g->weighted)
+        k_edge_records_w<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, g->colidx, g->rowinfo + (size_t)a * n,
+                                                            g->B + (size_t)a * nnz, g->edges + (size_t)a * nnz * 4);
+      else
+        k_edge_records<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, g->colidx, g->rowinfo + (size_t)a * n,
+                                                          g->edges + (size_t)a * nnz);
       BUILD_CK((fcx::note_launch(), cudaGetLastError()));
     }
   }
@@ -648,7 +673,7 @@ extern "C" fc_status fc_set_start_order(fc_graph* g, int32_t order) {
 extern "C" fc_status fc_set_sampler_kernel(fc_graph* g, int32_t kernel) {
   if (g == nullptr || kernel < 0 || kernel > 2) return FC_EINVAL;
   if (kernel == 2 && g->edges == nullptr) {
-    set_error("fc_set_sampler_kernel: edge records exist only for unweighted single graphs");
+    set_error("fc_set_sampler_kernel: edge records exist only for single graphs with edges");
     return FC_EINVAL;
   }
   g->kernel_pref = kernel;

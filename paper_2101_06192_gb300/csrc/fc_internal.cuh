@@ -158,7 +158,7 @@ struct fc_graph {
   int32_t* order = nullptr;    // [n] ascending degree, ties by id
   uint4* rowinfo = nullptr;    // [n_alpha][n] {row offset, degree, T lo, T hi}
   uint64_t* B = nullptr;       // [n_alpha][nnz] slot thresholds (weighted only)
-  uint4* edges = nullptr;      // [n_alpha][nnz] edge records (unweighted single graphs)
+  uint4* edges = nullptr;      // [n_alpha][nnz] edge records (single graphs; 64 bytes when weighted)
   double* alphas_d = nullptr;  // [n_alpha]
   int32_t max_deg = 0;
   // batch of graphs (block-diagonal union with one alpha per graph)

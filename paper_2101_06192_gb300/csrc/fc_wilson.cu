@@ -506,9 +506,9 @@ static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool 
     if (g->regs > 0 && ri > 0) break;
     if (!edge && regs == 48) regs = 40;
     if (edge && regs == 32) regs = 40;
-    const WilsonFn fn = edge ? wilson_edge_fn(sbits, regs) : wilson_fn(smem, regs);
+    const WilsonFn fn = edge ? wilson_edge_fn(sbits, g->weighted, regs) : wilson_fn(smem, regs);
     for (int W = (g->walkers > 0 ? g->walkers : wcap); W >= 32; W -= 32) {
-      const size_t shb = edge ? wilson_edge_smem(W, n, sbits) : smem_bytes(W, n, smem);
+      const size_t shb = edge ? wilson_edge_smem(W, n, sbits, g->weighted) : smem_bytes(W, n, smem);
       if (shb + 64 > (size_t)smem_optin) {
         if (g->walkers > 0) break;
         continue;
@@ -518,7 +518,7 @@ static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool 
       // 20% slower than one just below it (the L1 left for register spills
       // shrinks); automatic shapes stay below the step when they can
       if (sbits && g->walkers == 0 && shb > SBITS_CARVEOUT &&
-          wilson_edge_smem(32, n, true) <= SBITS_CARVEOUT)
+          wilson_edge_smem(32, n, true, g->weighted) <= SBITS_CARVEOUT)
         continue;
       if (edge) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
       if (smem) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
@@ -630,14 +630,15 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   // edge-record kernel: in-tree bitmap in shared memory when it fits (unless
   // global tree state is forced)
   const bool sbits = edge && g->smem_mode != 1 &&
-                     wilson_edge_smem(g->walkers > 0 ? g->walkers : 32, nmax, true) + 64 <= (size_t)dev_smem_optin;
+                     wilson_edge_smem(g->walkers > 0 ? g->walkers : 32, nmax, true, g->weighted) + 64 <=
+                         (size_t)dev_smem_optin;
   Shape sh;
   {
     const fc_status r = choose_shape(g, nmax, total, use_smem, edge, sbits, nsm, dev_smem_optin, &sh);
     if (r != FC_OK) return r;
   }
   const int W = sh.W;
-  const size_t shb = edge ? wilson_edge_smem(W, nmax, sbits) : smem_bytes(W, nmax, use_smem);
+  const size_t shb = edge ? wilson_edge_smem(W, nmax, sbits, g->weighted) : smem_bytes(W, nmax, use_smem);
   int64_t grid = std::min<int64_t>(total, (int64_t)sh.per_sm * nsm);
   if (g->max_trees > 0) grid = std::min<int64_t>(grid, g->max_trees);
   void* gstate = nullptr;
@@ -719,7 +720,7 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   FC_CK(cudaMemsetAsync(g->d_counter, 0, sizeof(unsigned long long), st));
   if (sync) FC_CK(cudaMemsetAsync(g->d_err, 0, sizeof(uint32_t), st));
   FC_CK(cudaMemsetAsync(g->d_stats, 0, (2 + N_CNT) * sizeof(unsigned long long), st));
-  const WilsonFn fn = edge ? wilson_edge_fn(sbits, sh.regs) : wilson_fn(use_smem, sh.regs);
+  const WilsonFn fn = edge ? wilson_edge_fn(sbits, g->weighted, sh.regs) : wilson_fn(use_smem, sh.regs);
   if (use_smem || edge) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
   fn<<<(unsigned)grid, W, shb, st>>>(p);
   FC_LAUNCHED();

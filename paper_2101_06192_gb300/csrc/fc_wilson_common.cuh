@@ -45,7 +45,8 @@ struct WParams {
   int descending;           // take start vertices from the high-degree end (or the high-id end)
   int id_order;             // start vertices in vertex-id order instead of the degree order
   const uint4* edges;       // [n_alpha][nnz] edge records {target, its row offset, its degree,
-                            //  its threshold >> 21} (edge-record kernel)
+                            //  its threshold >> 21} (edge-record kernel; weighted graphs: 64-byte
+                            //  records, the header followed by 12 slot-threshold high words)
   // batch of graphs: work item i samples tree (i % tau) of graph gorder[i / tau]
   int32_t num_graphs;       // 0 = single graph
   const int64_t* voff;      // [G+1]
@@ -125,7 +126,7 @@ typedef void (*WilsonFn)(WParams);
 // Edge-record kernel (unweighted single graphs, state in global memory) with
 // the in-tree bitmap in shared memory (sbits) or as flags in the state words,
 // for a register cap of 40, 48 or 64, and its dynamic shared memory per CTA.
-WilsonFn wilson_edge_fn(bool sbits, int regs);
-size_t wilson_edge_smem(int W, int32_t n, bool sbits);
+WilsonFn wilson_edge_fn(bool sbits, bool wgt, int regs);
+size_t wilson_edge_smem(int W, int32_t n, bool sbits, bool wgt);
 
 }  // namespace fcx

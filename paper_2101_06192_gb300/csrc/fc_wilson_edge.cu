@@ -1,5 +1,5 @@
 // Edge-record variant of the Wilson sampler (Algorithm 2 on G*, rooted at u*)
-// for unweighted single graphs with the per-tree state in global memory.
+// for single graphs with the per-tree state in global memory.
 //
 // It uses the same random stacks, the same cycle-popping argument (so the
 // trees are bit-identical to the sequential sampler's) and the same wait-die
@@ -34,7 +34,7 @@ namespace {
 constexpr unsigned long long IN_TREE = 1ull << 63;
 constexpr unsigned long long TAG_MASK = (1ull << (63 - K_BITS)) - 1ull;
 
-enum { E_IDLE = 0, E_START, E_CLAIM, E_CLAIM2, E_TOP, E_POP, E_RETRACE, E_RELEASE, E_WAIT, E_DONE };
+enum { E_IDLE = 0, E_START, E_THR, E_CLAIM, E_CLAIM2, E_TOP, E_POP, E_RETRACE, E_RELEASE, E_WAIT, E_DONE };
 
 __device__ __forceinline__ uint32_t thr_hi(const uint4& ri) {
   const uint64_t T = (uint64_t)ri.z | ((uint64_t)ri.w << 32);
@@ -47,6 +47,10 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
@@ -56,7 +60,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // bytes fit next to the walker arrays).  A claim then first tests x's bit and
 // touches neither x's state nor an edge record when x is already in the tree,
 // and finished paths are marked in the bitmap instead of the state words.
-template <bool SBITS, int MAXREG>
+//
+// WGT: weighted graphs.  Records are 64 bytes: the 16-byte header above plus
+// the high words (bits 32..52) of the target's first 12 slot thresholds B.
+// A walker keeps the thresholds of its current vertex in shared memory (two
+// buffers: the record of the next vertex is copied into the other one while
+// the current vertex is claimed).  A slot is decided from the high words when
+// they differ from u53 >> 32 and from the exact B (global memory) on the rare
+// tie; rows with more than 13 slots search the rest of B in global memory.
+template <bool SBITS, bool WGT, int MAXREG>
 __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long sh_tree, sh_pops, sh_deps;
@@ -73,7 +85,11 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
   uint4* sh_wri = (uint4*)(smem_raw + (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15));
   uint4* sh_wst = sh_wri + W;
   uint32_t* sh_wv = (uint32_t*)(sh_wst + W);
-  volatile uint32_t* sh_bits = (volatile uint32_t*)(sh_wv + W);  // [ceil(n / 32)] (SBITS)
+  // [2][W][12] slot-threshold high words of each walker's current / next vertex (WGT)
+  uint32_t* sh_thr = (uint32_t*)(((uintptr_t)(sh_wv + W) + 15) & ~(uintptr_t)15);
+  volatile uint32_t* sh_bits = (volatile uint32_t*)(sh_thr + (WGT ? 2 * 12 * W : 0));  // [ceil(n / 32)] (SBITS)
+  uint32_t* my_thr0 = sh_thr + (size_t)me * 12;
+  uint32_t* my_thr1 = sh_thr + (size_t)(W + me) * 12;
   sh_wri += me & ~31;
   sh_wst += me & ~31;
   sh_wv += me & ~31;
@@ -111,11 +127,13 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
     }
     __syncthreads();
     const uint4* __restrict__ rinfo = p.rowinfo + (size_t)a * n;
-    const uint4* __restrict__ edges = p.edges + (size_t)a * p.nnz;
+    const uint4* __restrict__ edges = p.edges + (size_t)a * p.nnz * (WGT ? 4 : 1);
+    const uint64_t* __restrict__ Brow = WGT ? p.B + (size_t)a * p.nnz : nullptr;
 
     int mode = E_IDLE;
     int32_t x = 0, h = -1, c = 0, rh = 0, s = 0, len = 0;
     uint32_t xo = 0, xd = 0, xth = 0;  // row offset, degree and T_hi of x
+    uint32_t cur = 0;                  // WGT: buffer holding x's slot thresholds
     bool rskip = false;
     uint32_t gen = 1, kx = 0, iters = 0, pops = 0, deps = 0;
     unsigned long long wtag = 0, cexp = 0;
@@ -150,7 +168,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             xth = thr_hi(wr);
             h = -1;
             len = 0;
-            mode = E_CLAIM;
+            mode = WGT ? E_THR : E_CLAIM;
           } else if (wdone) {
             mode = E_DONE;
           }
@@ -190,6 +208,9 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
 
       if (act) {
         const unsigned long long mytag = ((unsigned long long)gen << W_BITS) | (unsigned)me;
+        uint32_t* thr_cur = cur ? my_thr1 : my_thr0;
+        uint32_t* thr_nxt = cur ? my_thr0 : my_thr1;
+        if (WGT) cp_async_wait_all();  // x's thresholds, copied during the previous step
 
         // ---- issue: claim x and, speculatively, load the record its top selects ----
         unsigned long long old = 0ull;
@@ -199,6 +220,12 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
         else if (mode == E_WAIT) old = ld_volatile(&S[x].st);
         uint4 ri = make_uint4(0u, 0u, 0u, 0u);
         if (mode == E_START) ri = __ldg(rinfo + x);
+        if (WGT && mode == E_THR) {
+          // thresholds of a start vertex: high words of its B row
+          const uint32_t m = xd > 13u ? 12u : (xd > 0u ? xd - 1u : 0u);
+          for (uint32_t j = 0; j < m; ++j) cp_async4(thr_cur + j, (const uint32_t*)(Brow + xo + j) + 1);
+          cp_async_commit();
+        }
         const bool walk = (mode == E_POP) || (mode == E_RETRACE) || (mode == E_RELEASE);
         uint32_t nc = 0;
         if (walk) nc = LD_NXT(c);
@@ -216,7 +243,45 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             const uint4 rx = __ldg(rinfo + x);
             nb = u >= ((uint64_t)rx.z | ((uint64_t)rx.w << 32));
           }
-          if (nb) er = __ldg(edges + xo + __umulhi(o.z, xd));
+          if (nb) {
+            uint32_t slot;
+            if (!WGT) {
+              slot = __umulhi(o.z, xd);
+            } else {
+              // first slot j with u < B_j; B_{d-1} = 2^53
+              const uint32_t uh = (uint32_t)(u >> 32);
+              const uint32_t m = xd > 13u ? 12u : xd - 1u;
+              slot = 0xffffffffu;
+#pragma unroll
+              for (uint32_t j = 0; j < 12u; ++j) {
+                if (j < m && slot == 0xffffffffu) {
+                  const uint32_t b = thr_cur[j];
+                  if (uh < b || (uh == b && u < __ldg(Brow + xo + j))) slot = j;
+                }
+              }
+              if (slot == 0xffffffffu) {
+                if (xd - 1u > 12u) {
+                  uint32_t lo = 12u, hi = xd - 1u;  // search B_12 .. B_{d-2}; hi = d - 1 means none
+                  while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (u < __ldg(Brow + xo + mid)) hi = mid;
+                    else lo = mid + 1u;
+                  }
+                  slot = lo;
+                } else {
+                  slot = xd - 1u;
+                }
+              }
+            }
+            const uint4* rec = edges + (size_t)(xo + slot) * (WGT ? 4 : 1);
+            er = __ldg(rec);
+            if (WGT) {
+              cp_async16(thr_nxt, rec + 1);
+              cp_async16(thr_nxt + 4, rec + 2);
+              cp_async16(thr_nxt + 8, rec + 3);
+              cp_async_commit();
+            }
+          }
         }
 
         // ---- consume ----
@@ -226,6 +291,10 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             xo = ri.x;
             xd = ri.y;
             xth = thr_hi(ri);
+            mode = WGT ? E_THR : E_CLAIM;
+            break;
+          }
+          case E_THR: {  // thresholds of x copied: claim it next
             mode = E_CLAIM;
             break;
           }
@@ -262,6 +331,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
               xo = er.y;
               xd = er.z;
               xth = er.w;
+              cur ^= 1u;
               mode = E_CLAIM;
               break;
             }
@@ -338,6 +408,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             xo = er.y;
             xd = er.z;
             xth = er.w;
+            cur ^= 1u;
             mode = E_CLAIM;
             break;
           }
@@ -459,6 +530,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
       }
     }
 
+    cp_async_wait_all();  // no copy of this tree may land in the next one's buffers
     atomicAdd(&sh_pops, (unsigned long long)pops);
     atomicAdd(&sh_deps, (unsigned long long)deps);
 #if FC_WILSON_COUNTERS
@@ -488,19 +560,21 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
 #undef ST_NXT
 }
 
-WilsonFn wilson_edge_fn(bool sbits, int regs) {
-  if (sbits) {
-    if (regs == 40) return k_wilson_edge<true, 40>;
-    if (regs == 48) return k_wilson_edge<true, 48>;
-    return k_wilson_edge<true, 64>;
-  }
-  if (regs == 40) return k_wilson_edge<false, 40>;
-  if (regs == 48) return k_wilson_edge<false, 48>;
-  return k_wilson_edge<false, 64>;
+template <bool SBITS, bool WGT>
+static WilsonFn edge_fn_regs(int regs) {
+  if (regs == 40) return k_wilson_edge<SBITS, WGT, 40>;
+  if (regs == 48) return k_wilson_edge<SBITS, WGT, 48>;
+  return k_wilson_edge<SBITS, WGT, 64>;
 }
 
-size_t wilson_edge_smem(int W, int32_t n, bool sbits) {
-  return (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15) + (size_t)W * (16 + 16 + 4) +
+WilsonFn wilson_edge_fn(bool sbits, bool wgt, int regs) {
+  if (sbits) return wgt ? edge_fn_regs<true, true>(regs) : edge_fn_regs<true, false>(regs);
+  return wgt ? edge_fn_regs<false, true>(regs) : edge_fn_regs<false, false>(regs);
+}
+
+size_t wilson_edge_smem(int W, int32_t n, bool sbits, bool wgt) {
+  const size_t base = (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15) + (size_t)W * (16 + 16 + 4);
+  return ((base + 15) & ~(size_t)15) + (wgt ? (size_t)W * 2 * 12 * 4 : 0) +
          (sbits ? (((size_t)n + 31) / 32) * 4 : 0);
 }
 

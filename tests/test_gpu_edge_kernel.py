@@ -120,13 +120,28 @@ def test_both_kernels_agree_and_default_is_edge_kernel():
     G.close()
 
 
-def test_weighted_graph_has_no_edge_records():
-    g = synth.perturbed_grid(20, 20, 1)
-    G = fc.Graph.from_csr(g, [1.0])
-    with pytest.raises(fc.FcError):
-        G.set_kernel(2)
-    G.sample(1, 4)
-    assert G.last_kernel() == 1
+@pytest.mark.parametrize("kind", ["grid", "grid_small_alpha", "K8", "ba_hubs", "two_parts"])
+@pytest.mark.parametrize("smem", [0, 1])
+def test_weighted_trees_bit_exact(kind, smem):
+    """Weighted graphs: slot thresholds carried in the 64-byte records; rows
+    with more than 13 slots (BA hubs) search the rest of B in global memory."""
+    if kind == "grid":
+        g, alphas, tau = synth.perturbed_grid(48, 40, 3), [0.1, 1.0, 10.0], 24
+    elif kind == "grid_small_alpha":
+        g, alphas, tau = synth.perturbed_grid(40, 30, 5), [0.02, 30.0], 16
+    elif kind == "K8":
+        g, alphas, tau = synth.complete(8, weight=2.5), [0.5, 2.0], 64
+    elif kind == "ba_hubs":
+        g, alphas, tau = synth.barabasi_albert(4000, 4, 6, weighted=True), [0.3, 3.0], 32
+        assert g.degrees().max() > 13
+    else:
+        g, alphas, tau = synth.from_edges(6, [0, 1, 3, 4], [1, 2, 4, 5], [1.0, 2.0, 0.5, 3.0]), [0.5, 2.0], 64
+    G = fc.Graph.from_csr(g, alphas)
+    G.set_kernel(2)
+    for walkers in (32, 256):
+        G.set_shape(walkers, 0, smem)
+        _check(G, g, alphas, seed=41, tau=tau)
+        assert G.last_kernel() == (3 if smem == 0 else 2)
     G.close()
 
 

@@ -12,17 +12,19 @@ pytestmark = pytest.mark.gpu
 fc = pytest.importorskip("paper_2101_06192_gb300.fc")
 
 
-@pytest.mark.parametrize("kind", ["ba", "grid", "er"])
+@pytest.mark.parametrize("kind", ["ba", "grid", "grid_w", "er"])
 def test_start_order_and_shape_invariance(kind):
     if kind == "ba":
         g, alphas, tau = synth.barabasi_albert(30_000, 4, 2), [1.0], 96
     elif kind == "grid":
         g, alphas, tau = synth.perturbed_grid(120, 100, 3, weighted=False), [0.1, 10.0], 48
+    elif kind == "grid_w":
+        g, alphas, tau = synth.perturbed_grid(90, 80, 7), [0.3, 8.0], 32
     else:
         g, alphas, tau = synth.erdos_renyi(2000, 3, 5), [2.0], 128
     G = fc.Graph.from_csr(g, alphas)
     ref = None
-    kernels = (1, 2) if g.w is None else (1,)
+    kernels = (1, 2)
     for kernel in kernels:
         G.set_kernel(kernel)
         for order in ("degree", "degree_desc", "id", "id_desc"):
