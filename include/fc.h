@@ -153,6 +153,17 @@ fc_status fc_set_sampler_kernel(fc_graph* g, int32_t kernel);
 int32_t fc_sampler_last_kernel(const fc_graph* g);
 
 /*
+ * How the edge-record kernel erases a cycle that closes on a walker's own
+ * path (Wilson's loop erasure = popping the stacks of the cycle's vertices):
+ * 1 = always walk the cycle through the next pointers (one dependent load per
+ * vertex), 2 = when the cycle lies within the walker's last 8 path vertices,
+ * pop it from shared memory at once (longer cycles are walked), 0 = automatic
+ * (the default: 2 when the mean degree is below 8, where walks loop often,
+ * else 1).  Affects speed only, never results.
+ */
+fc_status fc_set_sampler_pops(fc_graph* g, int32_t mode);
+
+/*
  * Diagnostic per-iteration counters of the last fc_sample_usts on g, summed
  * over walkers and trees: [0] walker iterations, [1] claims at stack entry 0,
  * [2] tree hits, [3] tree-hit confirmations, [4] conflict waits, [5] waits

@@ -494,7 +494,7 @@ struct Shape {
 // launch in one wave (trees of one launch take about equally long), else the
 // shape with the most walkers resident.  Walkers per tree are capped at n/8.
 static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool smem, bool edge, bool sbits,
-                              int nsm, int smem_optin, Shape* out) {
+                              bool ring, int nsm, int smem_optin, Shape* out) {
   const int wcap = std::max(32, std::min(1024, (int)((n / 8) & ~31)));
   // measured on GB300 (BA n = 2^20, tau = 1024): the 40-register variant is
   // fastest; graphs with long walks prefer more walkers per tree, which the
@@ -505,8 +505,8 @@ static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool 
     int regs = g->regs > 0 ? g->regs : regs_list[ri];
     if (g->regs > 0 && ri > 0) break;
     if (!edge && regs == 48) regs = 40;
-    if (edge && regs == 32) regs = 40;
-    const WilsonFn fn = edge ? wilson_edge_fn(sbits, g->weighted, regs) : wilson_fn(smem, regs);
+    if (edge && regs < 48) regs = 48;
+    const WilsonFn fn = edge ? wilson_edge_fn(sbits, g->weighted, ring, regs) : wilson_fn(smem, regs);
     for (int W = (g->walkers > 0 ? g->walkers : wcap); W >= 32; W -= 32) {
       const size_t shb = edge ? wilson_edge_smem(W, n, sbits, g->weighted) : smem_bytes(W, n, smem);
       if (shb + 64 > (size_t)smem_optin) {
@@ -632,9 +632,13 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   const bool sbits = edge && g->smem_mode != 1 &&
                      wilson_edge_smem(g->walkers > 0 ? g->walkers : 32, nmax, true, g->weighted) + 64 <=
                          (size_t)dev_smem_optin;
+  // measured on GB300: popping short cycles from the ring gains 9% on a
+  // road-like grid (mean degree 3.7, pops 44% of departures); the prefix
+  // buffer stays 6% faster on BA m = 8 (pops 5%)
+  const bool ring = edge && (g->pops_mode == 2 || (g->pops_mode == 0 && g->nnz < 8 * (int64_t)g->n));
   Shape sh;
   {
-    const fc_status r = choose_shape(g, nmax, total, use_smem, edge, sbits, nsm, dev_smem_optin, &sh);
+    const fc_status r = choose_shape(g, nmax, total, use_smem, edge, sbits, ring, nsm, dev_smem_optin, &sh);
     if (r != FC_OK) return r;
   }
   const int W = sh.W;
@@ -671,6 +675,7 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   p.tree_offset = tree_offset;
   p.descending = g->order_desc;
   p.id_order = g->order_id;
+
   p.edges = g->edges;
   p.key0 = (uint32_t)seed;
   p.key1 = (uint32_t)(seed >> 32);
@@ -720,7 +725,7 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   FC_CK(cudaMemsetAsync(g->d_counter, 0, sizeof(unsigned long long), st));
   if (sync) FC_CK(cudaMemsetAsync(g->d_err, 0, sizeof(uint32_t), st));
   FC_CK(cudaMemsetAsync(g->d_stats, 0, (2 + N_CNT) * sizeof(unsigned long long), st));
-  const WilsonFn fn = edge ? wilson_edge_fn(sbits, g->weighted, sh.regs) : wilson_fn(use_smem, sh.regs);
+  const WilsonFn fn = edge ? wilson_edge_fn(sbits, g->weighted, ring, sh.regs) : wilson_fn(use_smem, sh.regs);
   if (use_smem || edge) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
   fn<<<(unsigned)grid, W, shb, st>>>(p);
   FC_LAUNCHED();

@@ -68,7 +68,12 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // the current vertex is claimed).  A slot is decided from the high words when
 // they differ from u53 >> 32 and from the exact B (global memory) on the rare
 // tie; rows with more than 13 slots search the rest of B in global memory.
-template <bool SBITS, bool WGT, int MAXREG>
+//
+// RINGP: the walker's shared-memory path buffer holds its last PB path
+// vertices (a ring) instead of the first PB, so a cycle closing within them is
+// popped at once without loads (graphs whose walks loop often); otherwise the
+// buffer holds the path prefix and every cycle is walked through nxt.
+template <bool SBITS, bool WGT, bool RINGP, int MAXREG>
 __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long sh_tree, sh_pops, sh_deps;
@@ -79,7 +84,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
   const int lane = me & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   volatile uint32_t* sh_gen = (volatile uint32_t*)smem_raw;               // [W]
-  uint32_t* sh_pb = (uint32_t*)(smem_raw + (size_t)W * 4);                // [PB][W] path prefix
+  uint32_t* sh_pb = (uint32_t*)(smem_raw + (size_t)W * 4);                // [PB][W] ring of the last path vertices
   // start window of this warp: row info and state record of each slot (copied
   // asynchronously) and its vertex
   uint4* sh_wri = (uint4*)(smem_raw + (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15));
@@ -100,6 +105,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
 
   // Plain memory operations: L2 eviction hints measured slower for this kernel
   // (its 16-byte edge records do not fit in L2 at the sizes where it matters).
+#define RING(pos) sh_pb[((pos) & (PB - 1)) * W + me]
 #define ADD_ST(v, d) atomicAdd(&S[v].st, (d))
 #define OR_ST(v, f) atomicOr(&S[v].st, (f))
 #define LD_NXT(v) S[v].nxt
@@ -132,6 +138,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
 
     int mode = E_IDLE;
     int32_t x = 0, h = -1, c = 0, rh = 0, s = 0, len = 0;
+    int32_t rbase = 0;  // path positions [rbase, len) are in the ring (len - rbase <= PB)
     uint32_t xo = 0, xd = 0, xth = 0;  // row offset, degree and T_hi of x
     uint32_t cur = 0;                  // WGT: buffer holding x's slot thresholds
     bool rskip = false;
@@ -168,6 +175,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             xth = thr_hi(wr);
             h = -1;
             len = 0;
+            rbase = 0;
             mode = WGT ? E_THR : E_CLAIM;
           } else if (wdone) {
             mode = E_DONE;
@@ -317,8 +325,14 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
                 break;
               }
               h = x;
-              if (len < PB) sh_pb[len * W + me] = (uint32_t)x;
-              ++len;
+              if (RINGP) {
+                RING(len) = (uint32_t)x;
+                ++len;
+                if (len - rbase > PB) rbase = len - PB;
+              } else {
+                if (len < PB) sh_pb[len * W + me] = (uint32_t)x;
+                ++len;
+              }
               ++deps;
               ST_NXT(x, er.x);  // er.x = n when the entry selects u*
               if (!nb) {
@@ -359,9 +373,44 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
               break;
             }
             if (w == (uint32_t)me && tgen == gen) {
-              // x closes a cycle on this walker's path: pop it
+              // x closes a cycle on this walker's path: pop it.  When x is
+              // among the last PB path vertices the cycle is in the ring and is
+              // popped here (no loads); otherwise it is walked through nxt.
               kx = (uint32_t)(old & K_MASK);
+              int32_t pos = -1;
+              if (RINGP) {
+#pragma unroll
+                for (int i = 0; i < PB; ++i) {
+                  const int32_t q = len - 1 - i;
+                  if (pos < 0 && q >= rbase && RING(q) == (uint32_t)x) pos = q;
+                }
+              }
+              if (RINGP && pos >= 0) {
+                CNT(CNT_POP);
+#pragma unroll
+                for (int i = 1; i < PB; ++i) {
+                  const int32_t q = pos + i;
+                  if (q < len) {
+                    ADD_ST(RING(q), 1ull - (mytag << K_BITS));
+                    ++pops;
+                  }
+                }
+                ADD_ST(x, 1ull);
+                ++pops;
+                ++kx;
+                if (kx >= (uint32_t)K_MASK) {
+                  atomicOr(p.err, ERR_OVERFLOW);
+                  sh_abort = 1u;
+                  mode = E_DONE;
+                  break;
+                }
+                len = pos + 1;
+                h = x;
+                mode = E_TOP;
+                break;
+              }
               c = x;
+              rh = 0;  // vertices popped by the walk
               rskip = true;
               mode = E_POP;
               break;
@@ -377,22 +426,39 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
               break;  // wait-die: wait
             }
             CNT(CNT_RELEASE);
-            // die: give the path back without popping anything; vertices whose
-            // nxt the release walk still needs are freed only after it is read
+            // die: give the path back without popping anything: the ring part
+            // now, the older part by a walk from s (each vertex freed after its
+            // nxt has been read)
             wtag = tag;
-            const int nfree = len > PB ? PB - 1 : len;
-            for (int i = 0; i < PB; ++i)
-              if (i < nfree) ADD_ST(sh_pb[i * W + me], 0ull - (mytag << K_BITS));
-            if (len > PB) {
-              c = (int32_t)sh_pb[(PB - 1) * W + me];
-              rh = h;
-              rskip = false;
-              mode = E_RELEASE;
+            if (RINGP) {
+              const int32_t held = len - rbase;  // ring slots in use, in any order
+#pragma unroll
+              for (int i = 0; i < PB; ++i)
+                if (((i - rbase) & (PB - 1)) < held) ADD_ST(sh_pb[i * W + me], 0ull - (mytag << K_BITS));
+              if (rbase > 0) {
+                c = s;
+                rh = rbase;  // vertices left to free
+                mode = E_RELEASE;
+              } else {
+                mode = E_WAIT;
+              }
             } else {
-              mode = E_WAIT;
+              // prefix: free it now except the last entry, whose nxt the
+              // release walk still reads
+              const int nfree = len > PB ? PB - 1 : len;
+              for (int i = 0; i < PB; ++i)
+                if (i < nfree) ADD_ST(sh_pb[i * W + me], 0ull - (mytag << K_BITS));
+              if (len > PB) {
+                c = (int32_t)sh_pb[(PB - 1) * W + me];
+                rh = h;  // the walk ends at the head
+                mode = E_RELEASE;
+              } else {
+                mode = E_WAIT;
+              }
             }
             h = -1;
             len = 0;
+            rbase = 0;
             break;
           }
           case E_TOP: {  // top of the path head x at entry kx > 0 (after a pop)
@@ -418,6 +484,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             if (!rskip) {
               ADD_ST(c, 1ull - (mytag << K_BITS));
               ++pops;
+              if (RINGP) ++rh;
             }
             rskip = false;
             c = (int32_t)nc;
@@ -431,11 +498,18 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
                 mode = E_DONE;
                 break;
               }
-              // the path now ends at x
-              int32_t pos = len;
-              for (int i = 0; i < PB; ++i)
-                if (i < len && sh_pb[i * W + me] == (uint32_t)x) pos = i;
-              if (pos < PB) len = pos + 1;
+              if (RINGP) {
+                // the path now ends at x, whose position is below the ring
+                len -= rh;
+                rbase = len - 1;
+                RING(rbase) = (uint32_t)x;
+              } else {
+                // the path now ends at x
+                int32_t pos = len;
+                for (int i = 0; i < PB; ++i)
+                  if (i < len && sh_pb[i * W + me] == (uint32_t)x) pos = i;
+                if (pos < PB) len = pos + 1;
+              }
               h = x;
               mode = E_TOP;
             }
@@ -447,13 +521,13 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
               else OR_ST(c, IN_TREE);
             }
             rskip = false;
-            if (c == rh) mode = E_IDLE;
+            if (RINGP ? --rh == 0 : c == rh) mode = E_IDLE;
             else c = (int32_t)nc;
             break;
           }
           case E_RELEASE: {
             ADD_ST(c, 0ull - (mytag << K_BITS));
-            if (c == rh) mode = E_WAIT;
+            if (RINGP ? --rh == 0 : c == rh) mode = E_WAIT;
             else c = (int32_t)nc;
             break;
           }
@@ -471,18 +545,27 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
 
         if (finished) {
           // the path s -> ... -> h joins the tree: bump the generation, then flag
-          // the remembered prefix and walk the rest
+          // the ring part and walk the older part from s
           if (len > 0) {
             ++gen;
             sh_gen[me] = gen;
-            for (int i = 0; i < PB; ++i)
-              if (i < len) {
+            // ring: slots in use in any order; prefix: the first min(len, PB)
+            const int32_t held = RINGP ? len - rbase : len;
+#pragma unroll
+            for (int i = 0; i < PB; ++i) {
+              if ((RINGP ? ((i - rbase) & (PB - 1)) : i) < held) {
                 const uint32_t v = sh_pb[i * W + me];
                 if (SBITS) atomicOr((uint32_t*)&sh_bits[v >> 5], 1u << (v & 31));
                 else OR_ST(v, IN_TREE);
               }
-            if (len > PB) {
-              c = (int32_t)sh_pb[(PB - 1) * W + me];
+            }
+            if (RINGP && rbase > 0) {
+              c = s;
+              rh = rbase;  // vertices left to flag
+              rskip = false;
+              mode = E_RETRACE;
+            } else if (!RINGP && len > PB) {
+              c = (int32_t)sh_pb[(PB - 1) * W + me];  // flagged above; the walk ends at the head
               rh = h;
               rskip = true;
               mode = E_RETRACE;
@@ -494,6 +577,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
           }
           h = -1;
           len = 0;
+          rbase = 0;
         }
       }
 
@@ -554,22 +638,26 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
     }
     __syncthreads();
   }
+#undef RING
 #undef ADD_ST
 #undef OR_ST
 #undef LD_NXT
 #undef ST_NXT
 }
 
-template <bool SBITS, bool WGT>
+template <bool SBITS, bool WGT, bool RINGP>
 static WilsonFn edge_fn_regs(int regs) {
-  if (regs == 40) return k_wilson_edge<SBITS, WGT, 40>;
-  if (regs == 48) return k_wilson_edge<SBITS, WGT, 48>;
-  return k_wilson_edge<SBITS, WGT, 64>;
+  return regs <= 48 ? k_wilson_edge<SBITS, WGT, RINGP, 48> : k_wilson_edge<SBITS, WGT, RINGP, 64>;
 }
 
-WilsonFn wilson_edge_fn(bool sbits, bool wgt, int regs) {
-  if (sbits) return wgt ? edge_fn_regs<true, true>(regs) : edge_fn_regs<true, false>(regs);
-  return wgt ? edge_fn_regs<false, true>(regs) : edge_fn_regs<false, false>(regs);
+template <bool SBITS, bool WGT>
+static WilsonFn edge_fn_ring(bool ring, int regs) {
+  return ring ? edge_fn_regs<SBITS, WGT, true>(regs) : edge_fn_regs<SBITS, WGT, false>(regs);
+}
+
+WilsonFn wilson_edge_fn(bool sbits, bool wgt, bool ring, int regs) {
+  if (sbits) return wgt ? edge_fn_ring<true, true>(ring, regs) : edge_fn_ring<true, false>(ring, regs);
+  return wgt ? edge_fn_ring<false, true>(ring, regs) : edge_fn_ring<false, false>(ring, regs);
 }
 
 size_t wilson_edge_smem(int W, int32_t n, bool sbits, bool wgt) {

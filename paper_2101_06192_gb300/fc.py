@@ -45,6 +45,7 @@ def lib():
             "fc_set_start_order": ([P, I32], ctypes.c_int),
             "fc_set_sampler_kernel": ([P, I32], ctypes.c_int),
             "fc_sampler_last_kernel": ([P], I32),
+            "fc_set_sampler_pops": ([P, I32], ctypes.c_int),
             "fc_sampler_counters": ([P, P, I32], ctypes.c_int),
             "fc_sample_usts": ([P, U64, I64, I64, P, P, P, U64, P, P], ctypes.c_int),
             "fc_sampler_stats": ([P, P, P], ctypes.c_int),
@@ -204,6 +205,10 @@ class Graph:
         """fc_set_sampler_kernel: 0 automatic, 1 CSR-walk, 2 edge-record."""
         _check(lib().fc_set_sampler_kernel(self._h, int(kernel)), "fc_set_sampler_kernel")
         self.kernel_pref = int(kernel)
+
+    def set_pops(self, mode: int = 0):
+        """fc_set_sampler_pops: 0 automatic, 1 walk every cycle, 2 pop short cycles from the ring."""
+        _check(lib().fc_set_sampler_pops(self._h, int(mode)), "fc_set_sampler_pops")
 
     def last_kernel(self) -> int:
         return int(lib().fc_sampler_last_kernel(self._h))

@@ -64,8 +64,9 @@ def test_graph_families_bit_exact(kind):
         g, alphas, tau = synth.rmat(12, 8, 3), [0.5, 8.0], 32
     G = fc.Graph.from_csr(g, alphas)
     G.set_kernel(2)
-    for walkers, smem in ((0, 1), (512, 1), (0, 0), (1024, 0)):
+    for walkers, smem, pops in ((0, 1, 1), (512, 1, 2), (0, 0, 2), (1024, 0, 1)):
         G.set_shape(walkers, 0, smem)
+        G.set_pops(pops)
         _check(G, g, alphas, seed=99, tau=tau)
     G.close()
 
@@ -138,8 +139,9 @@ def test_weighted_trees_bit_exact(kind, smem):
         g, alphas, tau = synth.from_edges(6, [0, 1, 3, 4], [1, 2, 4, 5], [1.0, 2.0, 0.5, 3.0]), [0.5, 2.0], 64
     G = fc.Graph.from_csr(g, alphas)
     G.set_kernel(2)
-    for walkers in (32, 256):
+    for walkers, pops in ((32, 2), (256, 1), (256, 2)):
         G.set_shape(walkers, 0, smem)
+        G.set_pops(pops)
         _check(G, g, alphas, seed=41, tau=tau)
         assert G.last_kernel() == (3 if smem == 0 else 2)
     G.close()
