@@ -142,12 +142,10 @@ fc_status fc_set_start_order(fc_graph* g, int32_t order);
  * per CSR entry (64 bytes for weighted graphs, which also carry slot
  * thresholds) per alpha.  Both kernels draw the same random stacks, so the
  * trees are identical; only speed differs.
- * The edge-record kernel keeps each tree's in-tree bitmap in shared memory
- * when it fits (n/8 bytes next to the walker arrays) unless fc_set_sampler_shape
- * forces global tree state (smem = 1), in which case membership is a flag in
- * the state words.  fc_sampler_last_kernel returns the kernel of the last
- * launch on g: 1 = CSR-walk, 2 = edge-record with state flags, 3 = edge-record
- * with the shared-memory bitmap; 0 before any launch.
+ * fc_sampler_last_kernel returns the kernel of the last launch on g: 1 =
+ * CSR-walk, 2 = edge-record with tree membership as state flags, 3 =
+ * edge-record with the in-tree bitmap in shared memory, 4 = edge-record with
+ * the in-tree bitmap in global memory; 0 before any launch.
  */
 fc_status fc_set_sampler_kernel(fc_graph* g, int32_t kernel);
 int32_t fc_sampler_last_kernel(const fc_graph* g);
@@ -162,6 +160,18 @@ int32_t fc_sampler_last_kernel(const fc_graph* g);
  * else 1).  Affects speed only, never results.
  */
 fc_status fc_set_sampler_pops(fc_graph* g, int32_t mode);
+
+/*
+ * Where the edge-record kernel keeps tree membership: 1 = a flag bit in each
+ * vertex's state word (the claiming CAS reads it), 2 = a per-tree in-tree
+ * bitmap in shared memory (FC_EINVAL at sampling when n/8 bytes do not fit
+ * next to the walker arrays), 3 = a per-tree bitmap in global memory, 0 =
+ * automatic (the default: shared memory when it fits and fc_set_sampler_shape
+ * does not force global tree state, else flags).  With a bitmap, claims on
+ * vertices already in the tree touch no state word and no edge record.
+ * Affects speed only, never results.
+ */
+fc_status fc_set_sampler_bitmap(fc_graph* g, int32_t mode);
 
 /*
  * Diagnostic per-iteration counters of the last fc_sample_usts on g, summed

@@ -682,6 +682,12 @@ extern "C" fc_status fc_set_sampler_kernel(fc_graph* g, int32_t kernel) {
 
 extern "C" int32_t fc_sampler_last_kernel(const fc_graph* g) { return g ? g->last_kernel : -1; }
 
+extern "C" fc_status fc_set_sampler_bitmap(fc_graph* g, int32_t mode) {
+  if (g == nullptr || mode < 0 || mode > 3) return FC_EINVAL;
+  g->bitmap_mode = mode;
+  return FC_OK;
+}
+
 extern "C" fc_status fc_set_sampler_pops(fc_graph* g, int32_t mode) {
   if (g == nullptr || mode < 0 || mode > 2) return FC_EINVAL;
   g->pops_mode = mode;

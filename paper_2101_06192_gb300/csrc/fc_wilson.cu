@@ -493,8 +493,9 @@ struct Shape {
 // Launch shape: the largest walker count whose CTAs hold every tree of the
 // launch in one wave (trees of one launch take about equally long), else the
 // shape with the most walkers resident.  Walkers per tree are capped at n/8.
-static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool smem, bool edge, bool sbits,
+static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool smem, bool edge, int bits,
                               bool ring, int nsm, int smem_optin, Shape* out) {
+  const bool sbits = bits == 1;
   const int wcap = std::max(32, std::min(1024, (int)((n / 8) & ~31)));
   // measured on GB300 (BA n = 2^20, tau = 1024): the 40-register variant is
   // fastest; graphs with long walks prefer more walkers per tree, which the
@@ -506,7 +507,7 @@ static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool 
     if (g->regs > 0 && ri > 0) break;
     if (!edge && regs == 48) regs = 40;
     if (edge && regs < 48) regs = 48;
-    const WilsonFn fn = edge ? wilson_edge_fn(sbits, g->weighted, ring, regs) : wilson_fn(smem, regs);
+    const WilsonFn fn = edge ? wilson_edge_fn(bits, g->weighted, ring, regs) : wilson_fn(smem, regs);
     for (int W = (g->walkers > 0 ? g->walkers : wcap); W >= 32; W -= 32) {
       const size_t shb = edge ? wilson_edge_smem(W, n, sbits, g->weighted) : smem_bytes(W, n, smem);
       if (shb + 64 > (size_t)smem_optin) {
@@ -627,18 +628,28 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
     set_error("fc_sample_usts: the edge-record kernel needs an unweighted single graph with global state");
     return FC_EINVAL;
   }
-  // edge-record kernel: in-tree bitmap in shared memory when it fits (unless
-  // global tree state is forced)
-  const bool sbits = edge && g->smem_mode != 1 &&
-                     wilson_edge_smem(g->walkers > 0 ? g->walkers : 32, nmax, true, g->weighted) + 64 <=
+  // edge-record kernel, tree membership: the in-tree bitmap in shared memory
+  // when it fits, else flags in the state words (fc_set_sampler_bitmap; with
+  // global tree state forced by the shape, flags)
+  const bool fits_smem = wilson_edge_smem(g->walkers > 0 ? g->walkers : 32, nmax, true, g->weighted) + 64 <=
                          (size_t)dev_smem_optin;
+  int bits = 0;
+  if (edge) {
+    if (g->bitmap_mode == 0) bits = (g->smem_mode != 1 && fits_smem) ? 1 : 0;
+    else bits = g->bitmap_mode - 1;
+    if (bits == 1 && !fits_smem) {
+      set_error("fc_sample_usts: the in-tree bitmap does not fit in shared memory");
+      return FC_EINVAL;
+    }
+  }
+  const bool sbits = bits == 1;
   // measured on GB300: popping short cycles from the ring gains 9% on a
   // road-like grid (mean degree 3.7, pops 44% of departures); the prefix
   // buffer stays 6% faster on BA m = 8 (pops 5%)
   const bool ring = edge && (g->pops_mode == 2 || (g->pops_mode == 0 && g->nnz < 8 * (int64_t)g->n));
   Shape sh;
   {
-    const fc_status r = choose_shape(g, nmax, total, use_smem, edge, sbits, ring, nsm, dev_smem_optin, &sh);
+    const fc_status r = choose_shape(g, nmax, total, use_smem, edge, bits, ring, nsm, dev_smem_optin, &sh);
     if (r != FC_OK) return r;
   }
   const int W = sh.W;
@@ -649,7 +660,7 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   uint32_t* gbits = nullptr;
   if (!use_smem) {
     // keep the per-tree state within a quarter of the device memory
-    const size_t words = edge ? 0 : ((size_t)nmax + 31) / 32;  // the edge-record kernel keeps no bitmap
+    const size_t words = (edge && bits != 2) ? 0 : ((size_t)nmax + 31) / 32;  // global in-tree bitmaps
     const size_t per_tree = (size_t)nmax * sizeof(VState) + ((words * 4 + 255) & ~(size_t)255);
     const size_t cap_trees = std::max<size_t>(1, (g->device_bytes / 4) / per_tree);
     grid = std::min<int64_t>(grid, (int64_t)cap_trees);
@@ -662,7 +673,7 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   g->last_W = W;
   g->last_regs = sh.regs;
   g->last_grid = (int32_t)grid;
-  g->last_kernel = edge ? (sbits ? 3 : 2) : 1;
+  g->last_kernel = edge ? 2 + bits : 1;
   WParams p;
   p.n = n;
   p.n_alpha = g->n_alpha;
@@ -718,14 +729,14 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   p.pre_cleared = 0;
   if (!use_smem) {
     // clear the state and bitmaps of the first wave in one pass
-    const size_t words = edge ? 0 : ((size_t)nmax + 31) / 32;
+    const size_t words = (edge && bits != 2) ? 0 : ((size_t)nmax + 31) / 32;
     FC_CK(cudaMemsetAsync(gstate, 0, (size_t)grid * nmax * sizeof(VState) + (size_t)grid * words * 4, st));
     p.pre_cleared = 1;
   }
   FC_CK(cudaMemsetAsync(g->d_counter, 0, sizeof(unsigned long long), st));
   if (sync) FC_CK(cudaMemsetAsync(g->d_err, 0, sizeof(uint32_t), st));
   FC_CK(cudaMemsetAsync(g->d_stats, 0, (2 + N_CNT) * sizeof(unsigned long long), st));
-  const WilsonFn fn = edge ? wilson_edge_fn(sbits, g->weighted, ring, sh.regs) : wilson_fn(use_smem, sh.regs);
+  const WilsonFn fn = edge ? wilson_edge_fn(bits, g->weighted, ring, sh.regs) : wilson_fn(use_smem, sh.regs);
   if (use_smem || edge) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
   fn<<<(unsigned)grid, W, shb, st>>>(p);
   FC_LAUNCHED();

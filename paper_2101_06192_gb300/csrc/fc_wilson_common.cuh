@@ -123,12 +123,13 @@ __device__ __forceinline__ uint32_t ld_volatile32(const uint32_t* a) {
 
 typedef void (*WilsonFn)(WParams);
 
-// Edge-record kernel (single graphs, state in global memory) with the in-tree
-// bitmap in shared memory (sbits) or as flags in the state words, weighted or
+// Edge-record kernel (single graphs, state in global memory) with tree
+// membership as flags in the state words (bits 0), an in-tree bitmap in shared
+// memory (1) or in global memory (2), weighted or
 // not, popping short cycles from a ring of the last path vertices (ring) or
 // walking them, for a register cap of 48 or 64 (lower caps map to 48), and
 // its dynamic shared memory per CTA.
-WilsonFn wilson_edge_fn(bool sbits, bool wgt, bool ring, int regs);
+WilsonFn wilson_edge_fn(int bits, bool wgt, bool ring, int regs);
 size_t wilson_edge_smem(int W, int32_t n, bool sbits, bool wgt);
 
 }  // namespace fcx

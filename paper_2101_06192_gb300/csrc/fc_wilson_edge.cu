@@ -56,10 +56,13 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 }  // namespace
 
-// SBITS: the tree's in-tree bitmap lives in shared memory (graphs whose n/8
-// bytes fit next to the walker arrays).  A claim then first tests x's bit and
-// touches neither x's state nor an edge record when x is already in the tree,
-// and finished paths are marked in the bitmap instead of the state words.
+// BITS: where tree membership lives.  0: the flag bit of the state words (the
+// claiming CAS answers "in the tree?").  1: an in-tree bitmap in shared memory
+// (graphs whose n/8 bytes fit next to the walker arrays).  2: an in-tree
+// bitmap per CTA in global memory (L2-resident for the trees in flight).  With
+// a bitmap a claim first tests x's bit and touches neither x's state nor an
+// edge record when x is already in the tree, and finished paths are marked in
+// the bitmap instead of the state words.
 //
 // WGT: weighted graphs.  Records are 64 bytes: the 16-byte header above plus
 // the high words (bits 32..52) of the target's first 12 slot thresholds B.
@@ -73,7 +76,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // vertices (a ring) instead of the first PB, so a cycle closing within them is
 // popped at once without loads (graphs whose walks loop often); otherwise the
 // buffer holds the path prefix and every cycle is walked through nxt.
-template <bool SBITS, bool WGT, bool RINGP, int MAXREG>
+template <int BITS, bool WGT, bool RINGP, int MAXREG>
 __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long sh_tree, sh_pops, sh_deps;
@@ -92,7 +95,9 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
   uint32_t* sh_wv = (uint32_t*)(sh_wst + W);
   // [2][W][12] slot-threshold high words of each walker's current / next vertex (WGT)
   uint32_t* sh_thr = (uint32_t*)(((uintptr_t)(sh_wv + W) + 15) & ~(uintptr_t)15);
-  volatile uint32_t* sh_bits = (volatile uint32_t*)(sh_thr + (WGT ? 2 * 12 * W : 0));  // [ceil(n / 32)] (SBITS)
+  // in-tree bitmap [ceil(n / 32)] (BITS = 1: shared memory, 2: this CTA's global region)
+  volatile uint32_t* sh_bits = BITS == 1 ? (volatile uint32_t*)(sh_thr + (WGT ? 2 * 12 * W : 0))
+                                         : (volatile uint32_t*)(p.gbits + (size_t)blockIdx.x * p.words);
   uint32_t* my_thr0 = sh_thr + (size_t)me * 12;
   uint32_t* my_thr1 = sh_thr + (size_t)(W + me) * 12;
   sh_wri += me & ~31;
@@ -121,7 +126,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
     const uint32_t tg = (uint32_t)(p.tree_offset + tloc);
     if (!(first_tree && p.pre_cleared))
       for (int32_t v = me; v < n; v += W) reinterpret_cast<uint4&>(S[v]) = make_uint4(0u, 0u, 0u, 0u);
-    if (SBITS)
+    if (BITS == 1 || (BITS == 2 && !(first_tree && p.pre_cleared)))
       for (int32_t q = me; q < ((n + 31) >> 5); q += W) sh_bits[q] = 0u;
     first_tree = false;
     sh_gen[me] = 1u;
@@ -209,7 +214,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
           const int32_t v = p.id_order ? (int32_t)ix : __ldg(p.order + ix);
           sh_wv[lane] = (uint32_t)v;
           cp_async16(&sh_wri[lane], rinfo + v);
-          if (!SBITS) cp_async16(&sh_wst[lane], &S[v]);
+          if (BITS == 0) cp_async16(&sh_wst[lane], &S[v]);
         }
         cp_async_commit();
       }
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
 
         // ---- issue: claim x and, speculatively, load the record its top selects ----
         unsigned long long old = 0ull;
-        const bool hit = SBITS && mode == E_CLAIM && ((sh_bits[x >> 5] >> (x & 31)) & 1u);
+        const bool hit = BITS != 0 && mode == E_CLAIM && ((sh_bits[x >> 5] >> (x & 31)) & 1u);
         if (mode == E_CLAIM && !hit) old = atomicCAS(&S[x].st, 0ull, mytag << K_BITS);
         else if (mode == E_CLAIM2) old = atomicCAS(&S[x].st, cexp, (mytag << K_BITS) | (cexp & K_MASK));
         else if (mode == E_WAIT) old = ld_volatile(&S[x].st);
@@ -517,7 +522,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
           }
           case E_RETRACE: {
             if (!rskip) {
-              if (SBITS) atomicOr((uint32_t*)&sh_bits[c >> 5], 1u << (c & 31));
+              if (BITS != 0) atomicOr((uint32_t*)&sh_bits[c >> 5], 1u << (c & 31));
               else OR_ST(c, IN_TREE);
             }
             rskip = false;
@@ -555,7 +560,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             for (int i = 0; i < PB; ++i) {
               if ((RINGP ? ((i - rbase) & (PB - 1)) : i) < held) {
                 const uint32_t v = sh_pb[i * W + me];
-                if (SBITS) atomicOr((uint32_t*)&sh_bits[v >> 5], 1u << (v & 31));
+                if (BITS != 0) atomicOr((uint32_t*)&sh_bits[v >> 5], 1u << (v & 31));
                 else OR_ST(v, IN_TREE);
               }
             }
@@ -587,7 +592,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
         __syncwarp();
         bool cand = wok;
         if (wok) {
-          if (SBITS) {
+          if (BITS != 0) {
             const uint32_t v = sh_wv[lane];
             cand = ((sh_bits[v >> 5] >> (v & 31)) & 1u) == 0u;
           } else {
@@ -645,22 +650,28 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
 #undef ST_NXT
 }
 
-template <bool SBITS, bool WGT, bool RINGP>
+template <int BITS, bool WGT, bool RINGP>
 static WilsonFn edge_fn_regs(int regs) {
-  return regs <= 48 ? k_wilson_edge<SBITS, WGT, RINGP, 48> : k_wilson_edge<SBITS, WGT, RINGP, 64>;
+  return regs <= 48 ? k_wilson_edge<BITS, WGT, RINGP, 48> : k_wilson_edge<BITS, WGT, RINGP, 64>;
 }
 
-template <bool SBITS, bool WGT>
+template <int BITS, bool WGT>
 static WilsonFn edge_fn_ring(bool ring, int regs) {
-  return ring ? edge_fn_regs<SBITS, WGT, true>(regs) : edge_fn_regs<SBITS, WGT, false>(regs);
+  return ring ? edge_fn_regs<BITS, WGT, true>(regs) : edge_fn_regs<BITS, WGT, false>(regs);
 }
 
-WilsonFn wilson_edge_fn(bool sbits, bool wgt, bool ring, int regs) {
-  if (sbits) return wgt ? edge_fn_ring<true, true>(ring, regs) : edge_fn_ring<true, false>(ring, regs);
-  return wgt ? edge_fn_ring<false, true>(ring, regs) : edge_fn_ring<false, false>(ring, regs);
+template <int BITS>
+static WilsonFn edge_fn_wgt(bool wgt, bool ring, int regs) {
+  return wgt ? edge_fn_ring<BITS, true>(ring, regs) : edge_fn_ring<BITS, false>(ring, regs);
 }
 
-size_t wilson_edge_smem(int W, int32_t n, bool sbits, bool wgt) {
+WilsonFn wilson_edge_fn(int bits, bool wgt, bool ring, int regs) {
+  if (bits == 1) return edge_fn_wgt<1>(wgt, ring, regs);
+  if (bits == 2) return edge_fn_wgt<2>(wgt, ring, regs);
+  return edge_fn_wgt<0>(wgt, ring, regs);
+}
+
+size_t wilson_edge_smem(int W, int32_t n, bool sbits, bool wgt) {  // sbits: bitmap in shared memory
   const size_t base = (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15) + (size_t)W * (16 + 16 + 4);
   return ((base + 15) & ~(size_t)15) + (wgt ? (size_t)W * 2 * 12 * 4 : 0) +
          (sbits ? (((size_t)n + 31) / 32) * 4 : 0);

@@ -46,6 +46,7 @@ def lib():
             "fc_set_sampler_kernel": ([P, I32], ctypes.c_int),
             "fc_sampler_last_kernel": ([P], I32),
             "fc_set_sampler_pops": ([P, I32], ctypes.c_int),
+            "fc_set_sampler_bitmap": ([P, I32], ctypes.c_int),
             "fc_sampler_counters": ([P, P, I32], ctypes.c_int),
             "fc_sample_usts": ([P, U64, I64, I64, P, P, P, U64, P, P], ctypes.c_int),
             "fc_sampler_stats": ([P, P, P], ctypes.c_int),
@@ -209,6 +210,10 @@ class Graph:
     def set_pops(self, mode: int = 0):
         """fc_set_sampler_pops: 0 automatic, 1 walk every cycle, 2 pop short cycles from the ring."""
         _check(lib().fc_set_sampler_pops(self._h, int(mode)), "fc_set_sampler_pops")
+
+    def set_bitmap(self, mode: int = 0):
+        """fc_set_sampler_bitmap: 0 automatic, 1 state flags, 2 shared memory, 3 global memory."""
+        _check(lib().fc_set_sampler_bitmap(self._h, int(mode)), "fc_set_sampler_bitmap")
 
     def last_kernel(self) -> int:
         return int(lib().fc_sampler_last_kernel(self._h))

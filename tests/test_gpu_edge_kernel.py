@@ -22,7 +22,7 @@ def _np32(t):
 def _check(G, g, alphas, seed, tau, tree_offset=0):
     out = G.sample(seed, tau, tree_offset=tree_offset, want_parents=True, want_steps=True)
     torch.cuda.synchronize()
-    assert G.last_kernel() in (2, 3)
+    assert G.last_kernel() in (2, 3, 4)
     n = g.n
     R = _np32(out["R"]).reshape(len(alphas), n)
     C = _np32(out["C"]).reshape(len(alphas), n)
@@ -39,15 +39,16 @@ def _check(G, g, alphas, seed, tau, tree_offset=0):
 
 @pytest.mark.parametrize("order", ["id", "id_desc", "degree", "degree_desc"])
 @pytest.mark.parametrize("walkers,regs", [(0, 0), (32, 40), (256, 48), (1024, 64)])
-@pytest.mark.parametrize("smem", [0, 1])  # 0: in-tree bitmap in shared memory, 1: flags in the state words
-def test_er_trees_bit_exact(order, walkers, regs, smem):
+@pytest.mark.parametrize("bitmap", [1, 2, 3])  # state flags, shared-memory bitmap, global bitmap
+def test_er_trees_bit_exact(order, walkers, regs, bitmap):
     g = synth.erdos_renyi(1000, 8, 1)
     G = fc.Graph.from_csr(g, [1.0])
     G.set_kernel(2)
-    G.set_shape(walkers, 0, smem, regs)
+    G.set_shape(walkers, 0, 0, regs)
+    G.set_bitmap(bitmap)
     G.set_start_order(order)
     _check(G, g, [1.0], seed=2021, tau=200)
-    assert G.last_kernel() == (3 if smem == 0 else 2)
+    assert G.last_kernel() == bitmap + 1
     G.close()
 
 
@@ -64,10 +65,12 @@ def test_graph_families_bit_exact(kind):
         g, alphas, tau = synth.rmat(12, 8, 3), [0.5, 8.0], 32
     G = fc.Graph.from_csr(g, alphas)
     G.set_kernel(2)
-    for walkers, smem, pops in ((0, 1, 1), (512, 1, 2), (0, 0, 2), (1024, 0, 1)):
-        G.set_shape(walkers, 0, smem)
+    for walkers, bitmap, pops in ((0, 1, 1), (512, 1, 2), (0, 2, 2), (1024, 2, 1), (256, 3, 1), (1024, 3, 2)):
+        G.set_shape(walkers, 0, 0)
+        G.set_bitmap(bitmap)
         G.set_pops(pops)
         _check(G, g, alphas, seed=99, tau=tau)
+        assert G.last_kernel() == bitmap + 1
     G.close()
 
 
@@ -96,8 +99,9 @@ def test_edge_cases_bit_exact(name):
         G.close()
         return
     G.set_kernel(2)
-    for walkers, smem in ((32, 1), (64, 1), (32, 0), (64, 0)):
+    for walkers, smem, bitmap in ((32, 1, 0), (64, 1, 0), (32, 0, 0), (64, 0, 0), (64, 0, 3)):
         G.set_shape(walkers, 0, smem)
+        G.set_bitmap(bitmap)
         out = _check(G, g, alphas, seed=11, tau=50)
     iso = g.degrees() == 0
     R = _np32(out["R"]).reshape(2, g.n)
@@ -114,7 +118,7 @@ def test_both_kernels_agree_and_default_is_edge_kernel():
         o = G.sample(4, 64, want_parents=True, want_steps=True)
         torch.cuda.synchronize()
         outs.append((k, G.last_kernel(), o))
-    assert outs[0][1] in (2, 3) and outs[1][1] == 1 and outs[2][1] in (2, 3)
+    assert outs[0][1] in (2, 3, 4) and outs[1][1] == 1 and outs[2][1] in (2, 3, 4)
     for key in ("parents", "R", "C", "steps"):
         for _, _, o in outs[1:]:
             assert torch.equal(o[key], outs[0][2][key]), key
@@ -122,8 +126,8 @@ def test_both_kernels_agree_and_default_is_edge_kernel():
 
 
 @pytest.mark.parametrize("kind", ["grid", "grid_small_alpha", "K8", "ba_hubs", "two_parts"])
-@pytest.mark.parametrize("smem", [0, 1])
-def test_weighted_trees_bit_exact(kind, smem):
+@pytest.mark.parametrize("bitmap", [1, 2, 3])
+def test_weighted_trees_bit_exact(kind, bitmap):
     """Weighted graphs: slot thresholds carried in the 64-byte records; rows
     with more than 13 slots (BA hubs) search the rest of B in global memory."""
     if kind == "grid":
@@ -139,20 +143,22 @@ def test_weighted_trees_bit_exact(kind, smem):
         g, alphas, tau = synth.from_edges(6, [0, 1, 3, 4], [1, 2, 4, 5], [1.0, 2.0, 0.5, 3.0]), [0.5, 2.0], 64
     G = fc.Graph.from_csr(g, alphas)
     G.set_kernel(2)
+    G.set_bitmap(bitmap)
     for walkers, pops in ((32, 2), (256, 1), (256, 2)):
-        G.set_shape(walkers, 0, smem)
+        G.set_shape(walkers, 0, 0)
         G.set_pops(pops)
         _check(G, g, alphas, seed=41, tau=tau)
-        assert G.last_kernel() == (3 if smem == 0 else 2)
+        assert G.last_kernel() == bitmap + 1
     G.close()
 
 
-@pytest.mark.parametrize("smem", [0, 1])
-def test_edge_kernel_watchdog_and_recovery(smem):
+@pytest.mark.parametrize("bitmap", [1, 2, 3])
+def test_edge_kernel_watchdog_and_recovery(bitmap):
     g = synth.barabasi_albert(20000, 4, 1)
     G = fc.Graph.from_csr(g, [1.0])
     G.set_kernel(2)
-    G.set_shape(64, 0, smem)
+    G.set_bitmap(bitmap)
+    G.set_shape(64, 0, 0)
     with pytest.raises(fc.FcError) as e:
         G.sample(3, 8, max_steps_per_tree=5)
     assert e.value.status == fc.FC_ETIMEOUT
