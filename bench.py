@@ -219,12 +219,17 @@ def run_cv(args):
     import numpy as np
     import torch
     import synth
-    from paper_2101_06192_gb300 import cvnet, fc
+    from paper_2101_06192_gb300 import cvnet, fc, tune
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
     g = synth.rmat(args.rmat_scale, 16, 4)
     gen_s = time.perf_counter() - t0
     G = fc.Graph.from_csr(g, [1.0])
+    # start order and register variant tuned at the checkpoint scale (tens of
+    # trees per launch), untimed; walkers per tree and CTAs per tree stay
+    # automatic because the checkpoint launches range from 16 to 1024 trees
+    shape = tune.autotune(G, 64)
+    G.set_shape(0, 0, 0, shape.get("regs", 0))
     J = judge_vertices(g, 4096, 5)
     Jt = torch.from_numpy(J).cuda()
     TJ = 16384
@@ -307,7 +312,7 @@ def run_cv(args):
         "train": {"graphs": "R-MAT scale 16-18 x2, plain targets tau=4096", "steps": 500,
                   "loss_first_last": [hist[0][1], hist[-1][1]], "seconds": train_s},
         "config": {"workload": f"R-MAT scale {args.rmat_scale} ef 16 (0.57,0.19,0.19), alpha=1",
-                   "n": g.n, "m_edges": g.m, "gen_seconds": gen_s},
+                   "n": g.n, "m_edges": g.m, "gen_seconds": gen_s, "sampler_shape": shape},
         "dtype": "u32/f64 (MLP bf16/fp32)", "data": "synthetic", "runs": results,
     }
     print(json.dumps(line), flush=True)

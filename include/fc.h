@@ -174,6 +174,19 @@ fc_status fc_set_sampler_pops(fc_graph* g, int32_t mode);
 fc_status fc_set_sampler_bitmap(fc_graph* g, int32_t mode);
 
 /*
+ * CTAs per tree of the edge-record kernel: 1, 2, 4 or 8 CTAs of a
+ * thread-block cluster share one tree (its walkers, start vertices and, with
+ * the shared-memory bitmap, the bitmap split over their shared memories); 0 =
+ * automatic (the default: the smallest power of two up to 8 that lets a
+ * launch of few trees occupy the GPU; with fc_set_sampler_bitmap(2), grown
+ * until the bitmap's share fits).  A global-memory bitmap runs with 1.
+ * fc_sampler_last_cluster returns the value used by the last launch.
+ * Affects speed only, never results.
+ */
+fc_status fc_set_sampler_cluster(fc_graph* g, int32_t ctas_per_tree);
+int32_t fc_sampler_last_cluster(const fc_graph* g);
+
+/*
  * Diagnostic per-iteration counters of the last fc_sample_usts on g, summed
  * over walkers and trees: [0] walker iterations, [1] claims at stack entry 0,
  * [2] tree hits, [3] tree-hit confirmations, [4] conflict waits, [5] waits

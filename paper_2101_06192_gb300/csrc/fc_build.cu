@@ -682,6 +682,16 @@ extern "C" fc_status fc_set_sampler_kernel(fc_graph* g, int32_t kernel) {
 
 extern "C" int32_t fc_sampler_last_kernel(const fc_graph* g) { return g ? g->last_kernel : -1; }
 
+extern "C" fc_status fc_set_sampler_cluster(fc_graph* g, int32_t ctas_per_tree) {
+  if (g == nullptr || !(ctas_per_tree == 0 || ctas_per_tree == 1 || ctas_per_tree == 2 || ctas_per_tree == 4 ||
+                        ctas_per_tree == 8))
+    return FC_EINVAL;
+  g->cluster = ctas_per_tree;
+  return FC_OK;
+}
+
+extern "C" int32_t fc_sampler_last_cluster(const fc_graph* g) { return g ? g->last_cluster : -1; }
+
 extern "C" fc_status fc_set_sampler_bitmap(fc_graph* g, int32_t mode) {
   if (g == nullptr || mode < 0 || mode > 3) return FC_EINVAL;
   g->bitmap_mode = mode;

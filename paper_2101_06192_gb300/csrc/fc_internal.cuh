@@ -184,6 +184,8 @@ struct fc_graph {
   int32_t kernel_pref = 0;     // 0 = automatic, 1 = CSR-walk kernel, 2 = edge-record kernel
   int32_t pops_mode = 0;       // 0 = automatic, 1 = walk every cycle, 2 = pop from the ring (fc_set_sampler_pops)
   int32_t bitmap_mode = 0;     // 0 = automatic, 1 = state flags, 2 = shared, 3 = global (fc_set_sampler_bitmap)
+  int32_t cluster = 0;         // CTAs per tree of the edge-record kernel (0 = automatic; fc_set_sampler_cluster)
+  int32_t last_cluster = 0;    // CTAs per tree of the last launch
   int32_t last_kernel = 0;     // kernel of the last launch (1 or 2)
   int32_t last_W = 0, last_regs = 0, last_grid = 0;  // shape of the last launch
   // scratch owned by the graph

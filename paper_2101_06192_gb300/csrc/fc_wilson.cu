@@ -488,13 +488,14 @@ struct Shape {
   int W = 0;
   int regs = 64;
   int per_sm = 0;
+  int64_t slots = 0;  // trees that can be in flight at once
 };
 
 // Launch shape: the largest walker count whose CTAs hold every tree of the
 // launch in one wave (trees of one launch take about equally long), else the
 // shape with the most walkers resident.  Walkers per tree are capped at n/8.
 static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool smem, bool edge, int bits,
-                              bool ring, int nsm, int smem_optin, Shape* out) {
+                              bool ring, int cl, int nsm, int smem_optin, Shape* out) {
   const bool sbits = bits == 1;
   const int wcap = std::max(32, std::min(1024, (int)((n / 8) & ~31)));
   // measured on GB300 (BA n = 2^20, tau = 1024): the 40-register variant is
@@ -507,9 +508,9 @@ static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool 
     if (g->regs > 0 && ri > 0) break;
     if (!edge && regs == 48) regs = 40;
     if (edge && regs < 48) regs = 48;
-    const WilsonFn fn = edge ? wilson_edge_fn(bits, g->weighted, ring, regs) : wilson_fn(smem, regs);
+    const WilsonFn fn = edge ? wilson_edge_fn(bits, g->weighted, ring, cl > 1, regs) : wilson_fn(smem, regs);
     for (int W = (g->walkers > 0 ? g->walkers : wcap); W >= 32; W -= 32) {
-      const size_t shb = edge ? wilson_edge_smem(W, n, sbits, g->weighted) : smem_bytes(W, n, smem);
+      const size_t shb = edge ? wilson_edge_smem(W, n, sbits, g->weighted, cl) : smem_bytes(W, n, smem);
       if (shb + 64 > (size_t)smem_optin) {
         if (g->walkers > 0) break;
         continue;
@@ -519,14 +520,31 @@ static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool 
       // 20% slower than one just below it (the L1 left for register spills
       // shrinks); automatic shapes stay below the step when they can
       if (sbits && g->walkers == 0 && shb > SBITS_CARVEOUT &&
-          wilson_edge_smem(32, n, true, g->weighted) <= SBITS_CARVEOUT)
+          wilson_edge_smem(32, n, true, g->weighted, cl) <= SBITS_CARVEOUT)
         continue;
       if (edge) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
       if (smem) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
       int per_sm = 0;
       FC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, W, shb));
-      if (per_sm > 0) {
-        const int64_t slots = (int64_t)per_sm * nsm;
+      int64_t slots = (int64_t)per_sm * nsm / cl;  // trees in flight
+      if (cl > 1 && per_sm > 0) {
+        // clusters are placed within a GPC: ask how many fit at once
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(cl * nsm));
+        cfg.blockDim = dim3((unsigned)W);
+        cfg.dynamicSmemBytes = shb;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int resident = 0;
+        FC_CK(cudaOccupancyMaxActiveClusters(&resident, fn, &cfg));
+        slots = resident;
+      }
+      if (per_sm > 0 && slots > 0) {
         const int64_t waves = (total + slots - 1) / slots;
         // walkers busy per wave, averaged over the waves
         const double score = (double)W * (double)std::min<int64_t>(total, slots) * (double)total /
@@ -536,6 +554,7 @@ static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool 
           out->W = W;
           out->regs = regs;
           out->per_sm = per_sm;
+          out->slots = slots;
         }
       }
       if (g->walkers > 0) break;
@@ -628,18 +647,32 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
     set_error("fc_sample_usts: the edge-record kernel needs an unweighted single graph with global state");
     return FC_EINVAL;
   }
-  // edge-record kernel, tree membership: the in-tree bitmap in shared memory
-  // when it fits, else flags in the state words (fc_set_sampler_bitmap; with
-  // global tree state forced by the shape, flags)
-  const bool fits_smem = wilson_edge_smem(g->walkers > 0 ? g->walkers : 32, nmax, true, g->weighted) + 64 <=
-                         (size_t)dev_smem_optin;
-  int bits = 0;
+  // edge-record kernel: CTAs per tree (a thread-block cluster) and where tree
+  // membership lives.  Automatic clusters give a launch of few trees enough
+  // CTAs to fill the GPU (fc_set_sampler_cluster); the in-tree bitmap goes to
+  // shared memory when its share per CTA fits, else membership is a flag in
+  // the state words (fc_set_sampler_bitmap; with global tree state forced by
+  // the shape, flags); a global-memory bitmap runs without clusters.
+  int cl = 1, bits = 0;
   if (edge) {
-    if (g->bitmap_mode == 0) bits = (g->smem_mode != 1 && fits_smem) ? 1 : 0;
-    else bits = g->bitmap_mode - 1;
-    if (bits == 1 && !fits_smem) {
-      set_error("fc_sample_usts: the in-tree bitmap does not fit in shared memory");
-      return FC_EINVAL;
+    const int wmin_e = g->walkers > 0 ? g->walkers : 32;
+    auto fits_c = [&](int c) {
+      return wilson_edge_smem(wmin_e, nmax, true, g->weighted, c) + 64 <= (size_t)dev_smem_optin;
+    };
+    int c_util = 1;
+    while (c_util < 8 && total * (int64_t)(c_util * 2) <= (int64_t)nsm) c_util *= 2;
+    cl = g->cluster > 0 ? g->cluster : c_util;
+    if (g->bitmap_mode == 0) {
+      bits = (g->smem_mode != 1 && fits_c(cl)) ? 1 : 0;
+    } else {
+      bits = g->bitmap_mode - 1;
+      if (bits == 1 && g->cluster == 0)
+        while (cl < 8 && !fits_c(cl)) cl *= 2;  // split the bitmap over a larger cluster
+      if (bits == 1 && !fits_c(cl)) {
+        set_error("fc_sample_usts: the in-tree bitmap does not fit in the shared memory of the cluster");
+        return FC_EINVAL;
+      }
+      if (bits == 2) cl = 1;
     }
   }
   const bool sbits = bits == 1;
@@ -649,12 +682,13 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   const bool ring = edge && (g->pops_mode == 2 || (g->pops_mode == 0 && g->nnz < 8 * (int64_t)g->n));
   Shape sh;
   {
-    const fc_status r = choose_shape(g, nmax, total, use_smem, edge, bits, ring, nsm, dev_smem_optin, &sh);
+    const fc_status r = choose_shape(g, nmax, total, use_smem, edge, bits, ring, cl, nsm, dev_smem_optin, &sh);
     if (r != FC_OK) return r;
   }
   const int W = sh.W;
-  const size_t shb = edge ? wilson_edge_smem(W, nmax, sbits, g->weighted) : smem_bytes(W, nmax, use_smem);
-  int64_t grid = std::min<int64_t>(total, (int64_t)sh.per_sm * nsm);
+  const size_t shb = edge ? wilson_edge_smem(W, nmax, sbits, g->weighted, cl) : smem_bytes(W, nmax, use_smem);
+  // trees in flight (each on cl CTAs)
+  int64_t grid = std::min<int64_t>(total, std::max<int64_t>(1, sh.slots));
   if (g->max_trees > 0) grid = std::min<int64_t>(grid, g->max_trees);
   void* gstate = nullptr;
   uint32_t* gbits = nullptr;
@@ -664,7 +698,7 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
     const size_t per_tree = (size_t)nmax * sizeof(VState) + ((words * 4 + 255) & ~(size_t)255);
     const size_t cap_trees = std::max<size_t>(1, (g->device_bytes / 4) / per_tree);
     grid = std::min<int64_t>(grid, (int64_t)cap_trees);
-    void* ws = nullptr;
+    void* ws = nullptr;  // state (and global bitmaps) of `grid` tree slots
     const fc_status s = sampler_scratch(g->device, (size_t)grid * per_tree, st, &ws, capturing);
     if (s != FC_OK) return s;
     gstate = ws;
@@ -672,8 +706,9 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   }
   g->last_W = W;
   g->last_regs = sh.regs;
-  g->last_grid = (int32_t)grid;
+  g->last_grid = (int32_t)(grid * cl);
   g->last_kernel = edge ? 2 + bits : 1;
+  g->last_cluster = cl;
   WParams p;
   p.n = n;
   p.n_alpha = g->n_alpha;
@@ -736,9 +771,31 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   FC_CK(cudaMemsetAsync(g->d_counter, 0, sizeof(unsigned long long), st));
   if (sync) FC_CK(cudaMemsetAsync(g->d_err, 0, sizeof(uint32_t), st));
   FC_CK(cudaMemsetAsync(g->d_stats, 0, (2 + N_CNT) * sizeof(unsigned long long), st));
-  const WilsonFn fn = edge ? wilson_edge_fn(bits, g->weighted, ring, sh.regs) : wilson_fn(use_smem, sh.regs);
+  const WilsonFn fn = edge ? wilson_edge_fn(bits, g->weighted, ring, cl > 1, sh.regs) : wilson_fn(use_smem, sh.regs);
   if (use_smem || edge) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
-  fn<<<(unsigned)grid, W, shb, st>>>(p);
+  if (cl > 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(grid * cl));
+    cfg.blockDim = dim3((unsigned)W);
+    cfg.dynamicSmemBytes = shb;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int resident = 0;
+    FC_CK(cudaOccupancyMaxActiveClusters(&resident, fn, &cfg));
+    if (resident < 1) {
+      set_error("fc_sample_usts: a cluster of this size and shape cannot be resident");
+      return FC_EINVAL;
+    }
+    FC_CK(cudaLaunchKernelEx(&cfg, fn, p));
+  } else {
+    fn<<<(unsigned)grid, W, shb, st>>>(p);
+  }
   FC_LAUNCHED();
   if (!sync) return FC_OK;
   uint32_t herr = 0;

@@ -127,9 +127,10 @@ typedef void (*WilsonFn)(WParams);
 // membership as flags in the state words (bits 0), an in-tree bitmap in shared
 // memory (1) or in global memory (2), weighted or
 // not, popping short cycles from a ring of the last path vertices (ring) or
-// walking them, for a register cap of 48 or 64 (lower caps map to 48), and
-// its dynamic shared memory per CTA.
-WilsonFn wilson_edge_fn(int bits, bool wgt, bool ring, int regs);
-size_t wilson_edge_smem(int W, int32_t n, bool sbits, bool wgt);
+// walking them, one CTA per tree or a cluster of CTAs per tree (cl; bits 0 or
+// 1), for a register cap of 48 or 64 (lower caps map to 48), and its dynamic
+// shared memory per CTA in a cluster of C CTAs.
+WilsonFn wilson_edge_fn(int bits, bool wgt, bool ring, bool cl, int regs);
+size_t wilson_edge_smem(int W, int32_t n, bool sbits, bool wgt, int C);
 
 }  // namespace fcx

@@ -25,7 +25,11 @@
 //
 // State word: bits 0..23 k (stack entries popped), bits 24..62 tag
 // ((gen << 10) | walker, 0 = free), bit 63 in-tree flag.
+#include <cooperative_groups.h>
+
 #include "fc_wilson_common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace fcx {
 
@@ -35,6 +39,12 @@ constexpr unsigned long long IN_TREE = 1ull << 63;
 constexpr unsigned long long TAG_MASK = (1ull << (63 - K_BITS)) - 1ull;
 
 enum { E_IDLE = 0, E_START, E_THR, E_CLAIM, E_CLAIM2, E_TOP, E_POP, E_RETRACE, E_RELEASE, E_WAIT, E_DONE };
+
+// Walker ids are tree-wide (a tree may span a cluster of up to 8 CTAs of up
+// to 1024 walkers); the tag's generation gets the remaining 26 bits.
+constexpr int EW_BITS = 13;
+constexpr uint32_t EW_MASK = (1u << EW_BITS) - 1u;
+constexpr uint32_t GEN_LIMIT = (1u << (39 - EW_BITS)) - 1u;
 
 __device__ __forceinline__ uint32_t thr_hi(const uint4& ri) {
   const uint64_t T = (uint64_t)ri.z | ((uint64_t)ri.w << 32);
@@ -76,7 +86,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // vertices (a ring) instead of the first PB, so a cycle closing within them is
 // popped at once without loads (graphs whose walks loop often); otherwise the
 // buffer holds the path prefix and every cycle is walked through nxt.
-template <int BITS, bool WGT, bool RINGP, int MAXREG>
+//
+// CL: a tree is shared by the C CTAs of a thread-block cluster (launched with
+// cluster dimension C; grids of few trees then still fill the GPU, and the
+// in-tree bitmap of a large graph fits when split over C shared memories).
+// Rank 0 holds the tree index, the start-window counter and the tree's pop
+// and departure totals; the bitmap is interleaved by 32-bit word over the
+// ranks; walker generations are read across the cluster (distributed shared
+// memory).  Cluster barriers separate the trees.
+template <int BITS, bool WGT, bool RINGP, bool CL, int MAXREG>
 __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long sh_tree, sh_pops, sh_deps;
@@ -98,36 +116,80 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
   // in-tree bitmap [ceil(n / 32)] (BITS = 1: shared memory, 2: this CTA's global region)
   volatile uint32_t* sh_bits = BITS == 1 ? (volatile uint32_t*)(sh_thr + (WGT ? 2 * 12 * W : 0))
                                          : (volatile uint32_t*)(p.gbits + (size_t)blockIdx.x * p.words);
+  // cluster geometry (C = 1 without clusters)
+  uint32_t rank = 0, C = 1, clog = 0;
+  if (CL) {
+    rank = cg::this_cluster().block_rank();
+    C = cg::this_cluster().num_blocks();
+    clog = (uint32_t)(__ffs((int)C) - 1);  // C is a power of two
+  }
+  const uint32_t wid = rank * (uint32_t)W + (uint32_t)me;  // walker id within the tree
+  const uint32_t WT = C * (uint32_t)W;                     // walkers per tree
+  const size_t tslot = CL ? blockIdx.x / C : blockIdx.x;   // tree slot of this CTA
+  if (BITS == 2) sh_bits = (volatile uint32_t*)(p.gbits + tslot * p.words);
   uint32_t* my_thr0 = sh_thr + (size_t)me * 12;
   uint32_t* my_thr1 = sh_thr + (size_t)(W + me) * 12;
   sh_wri += me & ~31;
   sh_wst += me & ~31;
   sh_wv += me & ~31;
   const int32_t n = p.n;  // u* = n
-  VState* S = p.gstate + (size_t)blockIdx.x * p.nmax;
+  VState* S = p.gstate + tslot * p.nmax;
   const int64_t total = (int64_t)p.n_alpha * p.tau;
   bool first_tree = true;
 
   // Plain memory operations: L2 eviction hints measured slower for this kernel
   // (its 16-byte edge records do not fit in L2 at the sizes where it matters).
 #define RING(pos) sh_pb[((pos) & (PB - 1)) * W + me]
+  // shared-memory word of another CTA of the cluster (the own one without clusters)
+#define REMOTE(ptr, r) (CL ? (volatile uint32_t*)cg::this_cluster().map_shared_rank((uint32_t*)(ptr), (r)) \
+                           : (volatile uint32_t*)(ptr))
+  // the in-tree bitmap word of vertex v
+#define BITW(v) ((BITS == 1 && CL) ? REMOTE(&sh_bits[((uint32_t)(v) >> 5) >> clog], ((uint32_t)(v) >> 5) & (C - 1)) \
+                                   : &sh_bits[(uint32_t)(v) >> 5])
+  // current generation of walker w of this tree
+#define GEN_OF(w) (CL ? *REMOTE(&sh_gen[(w) % (uint32_t)W], (w) / (uint32_t)W) : sh_gen[(w)])
+  // stop every CTA working on this tree
+#define ABORT_TREE()                                                     \
+  do {                                                                   \
+    if (CL) {                                                            \
+      for (uint32_t r_ = 0; r_ < C; ++r_) *REMOTE(&sh_abort, r_) = 1u;   \
+    } else {                                                             \
+      sh_abort = 1u;                                                     \
+    }                                                                    \
+  } while (0)
 #define ADD_ST(v, d) atomicAdd(&S[v].st, (d))
 #define OR_ST(v, f) atomicOr(&S[v].st, (f))
 #define LD_NXT(v) S[v].nxt
 #define ST_NXT(v, t) (S[v].nxt = (t))
 
   for (;;) {
-    if (me == 0) sh_tree = atomicAdd(p.counter, 1ull);
-    __syncthreads();
-    const unsigned long long tree = sh_tree;
-    if ((int64_t)tree >= total || *(volatile uint32_t*)p.err != 0u) break;
+    unsigned long long tree;
+    if (!CL) {
+      if (me == 0) sh_tree = atomicAdd(p.counter, 1ull);
+      __syncthreads();
+      tree = sh_tree;
+      if ((int64_t)tree >= total || *(volatile uint32_t*)p.err != 0u) break;
+    } else {
+      // rank 0 takes the next tree (or ends the loop for the whole cluster)
+      if (rank == 0 && me == 0) {
+        const unsigned long long t = atomicAdd(p.counter, 1ull);
+        sh_tree = *(volatile uint32_t*)p.err != 0u ? (unsigned long long)total : t;
+      }
+      cg::this_cluster().sync();
+      tree = *(volatile unsigned long long*)cg::this_cluster().map_shared_rank(&sh_tree, 0u);
+      cg::this_cluster().sync();  // every CTA has read rank 0's value
+      if ((int64_t)tree >= total) break;
+    }
     const int a = (int)(tree / (unsigned long long)p.tau);
     const int64_t tloc = (int64_t)(tree % (unsigned long long)p.tau);
     const uint32_t tg = (uint32_t)(p.tree_offset + tloc);
     if (!(first_tree && p.pre_cleared))
-      for (int32_t v = me; v < n; v += W) reinterpret_cast<uint4&>(S[v]) = make_uint4(0u, 0u, 0u, 0u);
-    if (BITS == 1 || (BITS == 2 && !(first_tree && p.pre_cleared)))
-      for (int32_t q = me; q < ((n + 31) >> 5); q += W) sh_bits[q] = 0u;
+      for (int32_t v = (int32_t)wid; v < n; v += (int32_t)WT)
+        reinterpret_cast<uint4&>(S[v]) = make_uint4(0u, 0u, 0u, 0u);
+    if (BITS == 1)  // this CTA's share of the words (all of them without clusters)
+      for (int32_t q = me; q < ((((n + 31) >> 5) + (int32_t)C - 1) >> clog); q += W) sh_bits[q] = 0u;
+    if (BITS == 2 && !(first_tree && p.pre_cleared))
+      for (int32_t q = (int32_t)wid; q < ((n + 31) >> 5); q += (int32_t)WT) sh_bits[q] = 0u;
     first_tree = false;
     sh_gen[me] = 1u;
     if (me == 0) {
@@ -136,7 +198,8 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
       sh_pops = 0;
       sh_deps = 0;
     }
-    __syncthreads();
+    if (CL) cg::this_cluster().sync();
+    else __syncthreads();
     const uint4* __restrict__ rinfo = p.rowinfo + (size_t)a * n;
     const uint4* __restrict__ edges = p.edges + (size_t)a * p.nnz * (WGT ? 4 : 1);
     const uint64_t* __restrict__ Brow = WGT ? p.B + (size_t)a * p.nnz : nullptr;
@@ -194,7 +257,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
         CNT(CNT_ITER);
         if (++iters > p.max_iters) {
           atomicOr(p.err, ERR_TIMEOUT);
-          sh_abort = 1u;
+          ABORT_TREE();
           mode = E_DONE;
           act = false;
         }
@@ -205,7 +268,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
       bool wok = false;
       if (refill) {
         __syncwarp();  // the slots handed out above are read before they are overwritten
-        if (lane == 0) wb = atomicAdd(&sh_next, 32u);
+        if (lane == 0) wb = atomicAdd(CL ? cg::this_cluster().map_shared_rank(&sh_next, 0u) : &sh_next, 32u);
         wb = __shfl_sync(FULL, wb, 0);
         const uint32_t i = wb + (uint32_t)lane;
         wok = i < (uint32_t)n;
@@ -220,14 +283,14 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
       }
 
       if (act) {
-        const unsigned long long mytag = ((unsigned long long)gen << W_BITS) | (unsigned)me;
+        const unsigned long long mytag = ((unsigned long long)gen << EW_BITS) | wid;
         uint32_t* thr_cur = cur ? my_thr1 : my_thr0;
         uint32_t* thr_nxt = cur ? my_thr0 : my_thr1;
         if (WGT) cp_async_wait_all();  // x's thresholds, copied during the previous step
 
         // ---- issue: claim x and, speculatively, load the record its top selects ----
         unsigned long long old = 0ull;
-        const bool hit = BITS != 0 && mode == E_CLAIM && ((sh_bits[x >> 5] >> (x & 31)) & 1u);
+        const bool hit = BITS != 0 && mode == E_CLAIM && ((*BITW(x) >> (x & 31)) & 1u);
         if (mode == E_CLAIM && !hit) old = atomicCAS(&S[x].st, 0ull, mytag << K_BITS);
         else if (mode == E_CLAIM2) old = atomicCAS(&S[x].st, cexp, (mytag << K_BITS) | (cexp & K_MASK));
         else if (mode == E_WAIT) old = ld_volatile(&S[x].st);
@@ -325,7 +388,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
               if (kx >= (uint32_t)K_MASK - 1u) {
                 // a pop while x is owned adds at most one more: keep k below 2^24
                 atomicOr(p.err, ERR_OVERFLOW);
-                sh_abort = 1u;
+                ABORT_TREE();
                 mode = E_DONE;
                 break;
               }
@@ -369,15 +432,15 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
               mode = E_CLAIM2;
               break;
             }
-            const uint32_t w = (uint32_t)(tag & ((1u << W_BITS) - 1));
-            const uint32_t tgen = (uint32_t)(tag >> W_BITS);
-            if (w >= (uint32_t)W) {
+            const uint32_t w = (uint32_t)(tag & EW_MASK);
+            const uint32_t tgen = (uint32_t)(tag >> EW_BITS);
+            if (w >= WT) {
               atomicOr(p.err, ERR_INVAL);
-              sh_abort = 1u;
+              ABORT_TREE();
               mode = E_DONE;
               break;
             }
-            if (w == (uint32_t)me && tgen == gen) {
+            if (w == wid && tgen == gen) {
               // x closes a cycle on this walker's path: pop it.  When x is
               // among the last PB path vertices the cycle is in the ring and is
               // popped here (no loads); otherwise it is walked through nxt.
@@ -405,7 +468,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
                 ++kx;
                 if (kx >= (uint32_t)K_MASK) {
                   atomicOr(p.err, ERR_OVERFLOW);
-                  sh_abort = 1u;
+                  ABORT_TREE();
                   mode = E_DONE;
                   break;
                 }
@@ -422,11 +485,11 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             }
             // w finished that path (its flag is on its way) or gave x up after
             // our read: look again
-            if (sh_gen[w] != tgen) {
+            if (GEN_OF(w) != tgen) {
               CNT(CNT_CONFIRM);
               break;
             }
-            if (h < 0 || (uint32_t)me < w) {
+            if (h < 0 || wid < w) {
               CNT(CNT_SPIN);
               break;  // wait-die: wait
             }
@@ -499,7 +562,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
               ++kx;
               if (kx >= (uint32_t)K_MASK) {
                 atomicOr(p.err, ERR_OVERFLOW);
-                sh_abort = 1u;
+                ABORT_TREE();
                 mode = E_DONE;
                 break;
               }
@@ -522,7 +585,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
           }
           case E_RETRACE: {
             if (!rskip) {
-              if (BITS != 0) atomicOr((uint32_t*)&sh_bits[c >> 5], 1u << (c & 31));
+              if (BITS != 0) atomicOr((uint32_t*)BITW(c), 1u << (c & 31));
               else OR_ST(c, IN_TREE);
             }
             rskip = false;
@@ -538,8 +601,8 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
           }
           case E_WAIT: {
             CNT(CNT_WAIT);
-            const uint32_t ww = (uint32_t)(wtag & ((1u << W_BITS) - 1));
-            if ((old >> K_BITS) == wtag && sh_gen[ww] == (uint32_t)(wtag >> W_BITS)) break;
+            const uint32_t ww = (uint32_t)(wtag & EW_MASK);
+            if ((old >> K_BITS) == wtag && GEN_OF(ww) == (uint32_t)(wtag >> EW_BITS)) break;
             x = s;
             mode = E_START;
             break;
@@ -553,6 +616,10 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
           // the ring part and walk the older part from s
           if (len > 0) {
             ++gen;
+            if (gen >= GEN_LIMIT) {  // the tag has 26 generation bits
+              atomicOr(p.err, ERR_OVERFLOW);
+              ABORT_TREE();
+            }
             sh_gen[me] = gen;
             // ring: slots in use in any order; prefix: the first min(len, PB)
             const int32_t held = RINGP ? len - rbase : len;
@@ -560,7 +627,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             for (int i = 0; i < PB; ++i) {
               if ((RINGP ? ((i - rbase) & (PB - 1)) : i) < held) {
                 const uint32_t v = sh_pb[i * W + me];
-                if (BITS != 0) atomicOr((uint32_t*)&sh_bits[v >> 5], 1u << (v & 31));
+                if (BITS != 0) atomicOr((uint32_t*)BITW(v), 1u << (v & 31));
                 else OR_ST(v, IN_TREE);
               }
             }
@@ -594,7 +661,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
         if (wok) {
           if (BITS != 0) {
             const uint32_t v = sh_wv[lane];
-            cand = ((sh_bits[v >> 5] >> (v & 31)) & 1u) == 0u;
+            cand = ((*BITW(v) >> (v & 31)) & 1u) == 0u;
           } else {
             cand = (sh_wst[lane].y & (uint32_t)(IN_TREE >> 32)) == 0u;
           }
@@ -620,8 +687,13 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
     }
 
     cp_async_wait_all();  // no copy of this tree may land in the next one's buffers
-    atomicAdd(&sh_pops, (unsigned long long)pops);
-    atomicAdd(&sh_deps, (unsigned long long)deps);
+    if (CL) {  // the tree's totals are kept by rank 0
+      atomicAdd(cg::this_cluster().map_shared_rank(&sh_pops, 0u), (unsigned long long)pops);
+      atomicAdd(cg::this_cluster().map_shared_rank(&sh_deps, 0u), (unsigned long long)deps);
+    } else {
+      atomicAdd(&sh_pops, (unsigned long long)pops);
+      atomicAdd(&sh_deps, (unsigned long long)deps);
+    }
 #if FC_WILSON_COUNTERS
 #pragma unroll
     for (int q = 0; q < N_CNT; ++q) {
@@ -631,50 +703,58 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
       if (lane == 0 && vq) atomicAdd(&p.stats[2 + q], vq);
     }
 #endif
-    __syncthreads();
+    if (CL) cg::this_cluster().sync();  // every walker of the tree has finished
+    else __syncthreads();
     if (p.parents != nullptr) {
       int32_t* par = p.parents + (size_t)tree * n;
-      for (int32_t v = me; v < n; v += W) par[v] = (int32_t)S[v].nxt;
+      for (int32_t v = (int32_t)wid; v < n; v += (int32_t)WT) par[v] = (int32_t)S[v].nxt;
     }
-    if (me == 0) {
+    if (me == 0 && rank == 0) {
       if (p.steps != nullptr) p.steps[tree] = (uint64_t)n + sh_pops;
       atomicAdd(&p.stats[0], sh_pops);
       atomicAdd(&p.stats[1], sh_deps);
     }
-    __syncthreads();
+    if (CL) cg::this_cluster().sync();  // parents read before the state is cleared again
+    else __syncthreads();
   }
 #undef RING
+#undef REMOTE
+#undef BITW
+#undef GEN_OF
+#undef ABORT_TREE
 #undef ADD_ST
 #undef OR_ST
 #undef LD_NXT
 #undef ST_NXT
 }
 
-template <int BITS, bool WGT, bool RINGP>
+template <int BITS, bool WGT, bool RINGP, bool CL>
 static WilsonFn edge_fn_regs(int regs) {
-  return regs <= 48 ? k_wilson_edge<BITS, WGT, RINGP, 48> : k_wilson_edge<BITS, WGT, RINGP, 64>;
+  return regs <= 48 ? k_wilson_edge<BITS, WGT, RINGP, CL, 48> : k_wilson_edge<BITS, WGT, RINGP, CL, 64>;
 }
 
-template <int BITS, bool WGT>
+template <int BITS, bool WGT, bool CL>
 static WilsonFn edge_fn_ring(bool ring, int regs) {
-  return ring ? edge_fn_regs<BITS, WGT, true>(regs) : edge_fn_regs<BITS, WGT, false>(regs);
+  return ring ? edge_fn_regs<BITS, WGT, true, CL>(regs) : edge_fn_regs<BITS, WGT, false, CL>(regs);
 }
 
-template <int BITS>
+template <int BITS, bool CL>
 static WilsonFn edge_fn_wgt(bool wgt, bool ring, int regs) {
-  return wgt ? edge_fn_ring<BITS, true>(ring, regs) : edge_fn_ring<BITS, false>(ring, regs);
+  return wgt ? edge_fn_ring<BITS, true, CL>(ring, regs) : edge_fn_ring<BITS, false, CL>(ring, regs);
 }
 
-WilsonFn wilson_edge_fn(int bits, bool wgt, bool ring, int regs) {
-  if (bits == 1) return edge_fn_wgt<1>(wgt, ring, regs);
-  if (bits == 2) return edge_fn_wgt<2>(wgt, ring, regs);
-  return edge_fn_wgt<0>(wgt, ring, regs);
+WilsonFn wilson_edge_fn(int bits, bool wgt, bool ring, bool cl, int regs) {
+  if (cl) return bits == 1 ? edge_fn_wgt<1, true>(wgt, ring, regs) : edge_fn_wgt<0, true>(wgt, ring, regs);
+  if (bits == 1) return edge_fn_wgt<1, false>(wgt, ring, regs);
+  if (bits == 2) return edge_fn_wgt<2, false>(wgt, ring, regs);
+  return edge_fn_wgt<0, false>(wgt, ring, regs);
 }
 
-size_t wilson_edge_smem(int W, int32_t n, bool sbits, bool wgt) {  // sbits: bitmap in shared memory
+size_t wilson_edge_smem(int W, int32_t n, bool sbits, bool wgt, int C) {  // sbits: bitmap in shared memory
   const size_t base = (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15) + (size_t)W * (16 + 16 + 4);
+  const size_t words = ((size_t)n + 31) / 32;
   return ((base + 15) & ~(size_t)15) + (wgt ? (size_t)W * 2 * 12 * 4 : 0) +
-         (sbits ? (((size_t)n + 31) / 32) * 4 : 0);
+         (sbits ? ((words + (size_t)C - 1) / (size_t)C) * 4 : 0);
 }
 
 }  // namespace fcx

@@ -47,6 +47,8 @@ def lib():
             "fc_sampler_last_kernel": ([P], I32),
             "fc_set_sampler_pops": ([P, I32], ctypes.c_int),
             "fc_set_sampler_bitmap": ([P, I32], ctypes.c_int),
+            "fc_set_sampler_cluster": ([P, I32], ctypes.c_int),
+            "fc_sampler_last_cluster": ([P], I32),
             "fc_sampler_counters": ([P, P, I32], ctypes.c_int),
             "fc_sample_usts": ([P, U64, I64, I64, P, P, P, U64, P, P], ctypes.c_int),
             "fc_sampler_stats": ([P, P, P], ctypes.c_int),
@@ -214,6 +216,13 @@ class Graph:
     def set_bitmap(self, mode: int = 0):
         """fc_set_sampler_bitmap: 0 automatic, 1 state flags, 2 shared memory, 3 global memory."""
         _check(lib().fc_set_sampler_bitmap(self._h, int(mode)), "fc_set_sampler_bitmap")
+
+    def set_cluster(self, ctas_per_tree: int = 0):
+        """fc_set_sampler_cluster: CTAs per tree (0 automatic, 1, 2, 4 or 8)."""
+        _check(lib().fc_set_sampler_cluster(self._h, int(ctas_per_tree)), "fc_set_sampler_cluster")
+
+    def last_cluster(self) -> int:
+        return int(lib().fc_sampler_last_cluster(self._h))
 
     def last_kernel(self) -> int:
         return int(lib().fc_sampler_last_kernel(self._h))

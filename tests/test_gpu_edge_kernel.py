@@ -166,3 +166,48 @@ def test_edge_kernel_watchdog_and_recovery(bitmap):
     ref = native.wilson(g, 1.0, seed=3, tau=8)
     np.testing.assert_array_equal(_np32(out["R"]), ref["R"])
     G.close()
+
+
+@pytest.mark.parametrize("cluster", [2, 4, 8])
+@pytest.mark.parametrize("bitmap", [1, 2])
+def test_cluster_trees_bit_exact(cluster, bitmap):
+    """Trees shared by the CTAs of a thread-block cluster (walkers, start
+    windows and, with the shared-memory bitmap, the bitmap split over the
+    CTAs' shared memories) give the oracle's trees."""
+    cases = [(synth.barabasi_albert(20000, 4, 3), [1.0], 16),
+             (synth.perturbed_grid(90, 70, 5), [0.2, 6.0], 8),
+             (synth.erdos_renyi(3000, 5, 9), [0.7], 24)]
+    for g, alphas, tau in cases:
+        G = fc.Graph.from_csr(g, alphas)
+        G.set_kernel(2)
+        G.set_bitmap(bitmap)
+        G.set_cluster(cluster)
+        for walkers in (64, 256):
+            G.set_shape(walkers, 0, 0)
+            _check(G, g, alphas, seed=5, tau=tau)
+            assert G.last_cluster() == cluster
+            assert G.last_kernel() == bitmap + 1
+        G.close()
+
+
+def test_bitmap_split_over_cluster_for_large_graph():
+    """2.1 M vertices: the in-tree bitmap (262 KB) fits in shared memory only
+    when split over a cluster; the automatic cluster grows until it does."""
+    g = synth.torus(1448, 1448)
+    G = fc.Graph.from_csr(g, [0.5])
+    G.set_kernel(2)
+    G.set_bitmap(2)
+    G.set_shape(256, 0, 0)
+    _check(G, g, [0.5], seed=8, tau=2)
+    assert G.last_cluster() >= 2 and G.last_kernel() == 3
+    G.close()
+
+
+def test_automatic_cluster_for_few_trees():
+    g = synth.barabasi_albert(50_000, 4, 2)
+    G = fc.Graph.from_csr(g, [1.0])
+    _check(G, g, [1.0], seed=3, tau=4)   # 4 trees: clusters of 8 CTAs
+    assert G.last_cluster() == 8
+    _check(G, g, [1.0], seed=3, tau=300)  # enough trees: one CTA each
+    assert G.last_cluster() == 1
+    G.close()
