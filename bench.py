@@ -578,8 +578,9 @@ def main():
     samp_s = statistics.mean(samp_ms) / 1000.0
     achieved = alg_bytes / samp_s / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    kname = {2: "k_wilson_edge<false, {r}>", 3: "k_wilson_edge<true, {r}>"}.get(
-        launched.get("kernel"), "k_wilson<false, {r}>").format(r=launched.get("regs"))
+    kname = {2: "k_wilson_edge<flags, {r}>", 3: "k_wilson_edge<smem bitmap, {r}>",
+             4: "k_wilson_edge<global bitmap, {r}>"}.get(
+        launched.get("kernel"), "k_wilson<global state, {r}>").format(r=launched.get("regs"))
     traffic = profiled_traffic(kname, launched) if (args.n_log2 == N_LOG2 and tau == TAU) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
