@@ -135,10 +135,10 @@ fc_status fc_set_sampler_shape(fc_graph* g, int32_t walkers_per_tree, int32_t ma
 fc_status fc_set_start_order(fc_graph* g, int32_t order);
 
 /*
- * Sampler kernel: 0 = automatic (the default: the edge-record kernel for a
- * single graph whose tree state lives in global memory, else the CSR-walk
- * kernel), 1 = CSR-walk kernel, 2 = edge-record kernel (FC_EINVAL if g has no
- * edge records: batches and graphs without edges).  Edge records are 16 bytes
+ * Sampler kernel: 0 = automatic (the default: the edge-record kernel when the
+ * tree state lives in global memory, else the CSR-walk kernel with the state
+ * in shared memory), 1 = CSR-walk kernel, 2 = edge-record kernel (FC_EINVAL if
+ * g has no edge records: graphs without edges).  Edge records are 16 bytes
  * per CSR entry (64 bytes for weighted graphs, which also carry slot
  * thresholds) per alpha.  Both kernels draw the same random stacks, so the
  * trees are identical; only speed differs.

@@ -591,7 +591,7 @@ static fc_status build_impl(int32_t n, int64_t nnz, const int64_t* rowptr, const
       BUILD_CK((fcx::note_launch(), cudaGetLastError()));
     }
   }
-  if (g->num_graphs == 0 && nnz > 0) {
+  if (nnz > 0) {
     const size_t rec = g->weighted ? 4 : 1;  // uint4 per record
     BUILD_CK(cudaMallocAsync((void**)&g->edges, (size_t)nnz * n_alpha * rec * sizeof(uint4), st));
     for (int a = 0; a < n_alpha; ++a) {
@@ -673,7 +673,7 @@ extern "C" fc_status fc_set_start_order(fc_graph* g, int32_t order) {
 extern "C" fc_status fc_set_sampler_kernel(fc_graph* g, int32_t kernel) {
   if (g == nullptr || kernel < 0 || kernel > 2) return FC_EINVAL;
   if (kernel == 2 && g->edges == nullptr) {
-    set_error("fc_set_sampler_kernel: edge records exist only for single graphs with edges");
+    set_error("fc_set_sampler_kernel: edge records exist only for graphs with edges");
     return FC_EINVAL;
   }
   g->kernel_pref = kernel;

@@ -642,9 +642,9 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
     set_error("fc_sample_usts: tree state does not fit in shared memory");
     return FC_EINVAL;
   }
-  const bool edge = !use_smem && !batch && g->edges != nullptr && g->kernel_pref != 1;
+  const bool edge = !use_smem && g->edges != nullptr && g->kernel_pref != 1;
   if (g->kernel_pref == 2 && !edge) {
-    set_error("fc_sample_usts: the edge-record kernel needs an unweighted single graph with global state");
+    set_error("fc_sample_usts: the edge-record kernel needs edge records and global tree state");
     return FC_EINVAL;
   }
   // edge-record kernel: CTAs per tree (a thread-block cluster) and where tree

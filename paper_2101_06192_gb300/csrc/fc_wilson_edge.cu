@@ -133,8 +133,9 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
   sh_wst += me & ~31;
   sh_wv += me & ~31;
   const int32_t n = p.n;  // u* = n
+  if (p.t0_ns != nullptr && threadIdx.x == 0) atomicMin(p.t0_ns, global_ns());
   VState* S = p.gstate + tslot * p.nmax;
-  const int64_t total = (int64_t)p.n_alpha * p.tau;
+  const int64_t total = (int64_t)(p.num_graphs > 0 ? p.num_graphs : p.n_alpha) * p.tau;  // work items
   bool first_tree = true;
 
   // Plain memory operations: L2 eviction hints measured slower for this kernel
@@ -144,8 +145,9 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
 #define REMOTE(ptr, r) (CL ? (volatile uint32_t*)cg::this_cluster().map_shared_rank((uint32_t*)(ptr), (r)) \
                            : (volatile uint32_t*)(ptr))
   // the in-tree bitmap word of vertex v
-#define BITW(v) ((BITS == 1 && CL) ? REMOTE(&sh_bits[((uint32_t)(v) >> 5) >> clog], ((uint32_t)(v) >> 5) & (C - 1)) \
-                                   : &sh_bits[(uint32_t)(v) >> 5])
+#define BITW(v) ((BITS == 1 && CL) ? REMOTE(&sh_bits[((uint32_t)((v) - base) >> 5) >> clog],          \
+                                          ((uint32_t)((v) - base) >> 5) & (C - 1))                   \
+                                   : &sh_bits[(uint32_t)((v) - base) >> 5])
   // current generation of walker w of this tree
 #define GEN_OF(w) (CL ? *REMOTE(&sh_gen[(w) % (uint32_t)W], (w) / (uint32_t)W) : sh_gen[(w)])
   // stop every CTA working on this tree
@@ -157,10 +159,13 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
       sh_abort = 1u;                                                     \
     }                                                                    \
   } while (0)
-#define ADD_ST(v, d) atomicAdd(&S[v].st, (d))
-#define OR_ST(v, f) atomicOr(&S[v].st, (f))
-#define LD_NXT(v) S[v].nxt
-#define ST_NXT(v, t) (S[v].nxt = (t))
+  // state record of vertex v (global id) in this tree's slot; a batch tree
+  // covers the vertex range [base, base + nl) of its graph
+#define SV(v) S[(v) - base]
+#define ADD_ST(v, d) atomicAdd(&SV(v).st, (d))
+#define OR_ST(v, f) atomicOr(&SV(v).st, (f))
+#define LD_NXT(v) SV(v).nxt
+#define ST_NXT(v, t) (SV(v).nxt = (t))
 
   for (;;) {
     unsigned long long tree;
@@ -180,16 +185,24 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
       cg::this_cluster().sync();  // every CTA has read rank 0's value
       if ((int64_t)tree >= total) break;
     }
-    const int a = (int)(tree / (unsigned long long)p.tau);
+    // item -> (alpha index or graph, tree); the tree's vertices are [base, base + nl)
+    int a = (int)(tree / (unsigned long long)p.tau);
     const int64_t tloc = (int64_t)(tree % (unsigned long long)p.tau);
     const uint32_t tg = (uint32_t)(p.tree_offset + tloc);
+    int32_t base = 0, nl = n, gi = 0;
+    if (p.num_graphs > 0) {
+      gi = p.gorder[a];
+      a = 0;
+      base = (int32_t)p.voff[gi];
+      nl = (int32_t)(p.voff[gi + 1] - p.voff[gi]);
+    }
     if (!(first_tree && p.pre_cleared))
-      for (int32_t v = (int32_t)wid; v < n; v += (int32_t)WT)
+      for (int32_t v = (int32_t)wid; v < nl; v += (int32_t)WT)
         reinterpret_cast<uint4&>(S[v]) = make_uint4(0u, 0u, 0u, 0u);
     if (BITS == 1)  // this CTA's share of the words (all of them without clusters)
-      for (int32_t q = me; q < ((((n + 31) >> 5) + (int32_t)C - 1) >> clog); q += W) sh_bits[q] = 0u;
+      for (int32_t q = me; q < ((((nl + 31) >> 5) + (int32_t)C - 1) >> clog); q += W) sh_bits[q] = 0u;
     if (BITS == 2 && !(first_tree && p.pre_cleared))
-      for (int32_t q = (int32_t)wid; q < ((n + 31) >> 5); q += (int32_t)WT) sh_bits[q] = 0u;
+      for (int32_t q = (int32_t)wid; q < ((nl + 31) >> 5); q += (int32_t)WT) sh_bits[q] = 0u;
     first_tree = false;
     sh_gen[me] = 1u;
     if (me == 0) {
@@ -271,13 +284,18 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
         if (lane == 0) wb = atomicAdd(CL ? cg::this_cluster().map_shared_rank(&sh_next, 0u) : &sh_next, 32u);
         wb = __shfl_sync(FULL, wb, 0);
         const uint32_t i = wb + (uint32_t)lane;
-        wok = i < (uint32_t)n;
+        wok = i < (uint32_t)nl;
         if (wok) {
-          const uint32_t ix = p.descending ? (uint32_t)n - 1u - i : i;
-          const int32_t v = p.id_order ? (int32_t)ix : __ldg(p.order + ix);
+          const uint32_t ix = p.descending ? (uint32_t)nl - 1u - i : i;
+          int32_t v = p.id_order ? base + (int32_t)ix : __ldg(p.order + base + ix);
+          if (v < base || v >= base + nl) {  // the start order must stay inside the tree's vertex range
+            atomicOr(p.err, ERR_INVAL);
+            ABORT_TREE();
+            v = base;
+          }
           sh_wv[lane] = (uint32_t)v;
           cp_async16(&sh_wri[lane], rinfo + v);
-          if (BITS == 0) cp_async16(&sh_wst[lane], &S[v]);
+          if (BITS == 0) cp_async16(&sh_wst[lane], &SV(v));
         }
         cp_async_commit();
       }
@@ -291,9 +309,9 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
         // ---- issue: claim x and, speculatively, load the record its top selects ----
         unsigned long long old = 0ull;
         const bool hit = BITS != 0 && mode == E_CLAIM && ((*BITW(x) >> (x & 31)) & 1u);
-        if (mode == E_CLAIM && !hit) old = atomicCAS(&S[x].st, 0ull, mytag << K_BITS);
-        else if (mode == E_CLAIM2) old = atomicCAS(&S[x].st, cexp, (mytag << K_BITS) | (cexp & K_MASK));
-        else if (mode == E_WAIT) old = ld_volatile(&S[x].st);
+        if (mode == E_CLAIM && !hit) old = atomicCAS(&SV(x).st, 0ull, mytag << K_BITS);
+        else if (mode == E_CLAIM2) old = atomicCAS(&SV(x).st, cexp, (mytag << K_BITS) | (cexp & K_MASK));
+        else if (mode == E_WAIT) old = ld_volatile(&SV(x).st);
         uint4 ri = make_uint4(0u, 0u, 0u, 0u);
         if (mode == E_START) ri = __ldg(rinfo + x);
         if (WGT && mode == E_THR) {
@@ -682,7 +700,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
         __syncwarp();
         whead = 0;
         wcnt = (uint32_t)__popc(cm);
-        if (wb + 32u >= (uint32_t)n) wdone = true;
+        if (wb + 32u >= (uint32_t)nl) wdone = true;
       }
     }
 
@@ -705,12 +723,14 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
 #endif
     if (CL) cg::this_cluster().sync();  // every walker of the tree has finished
     else __syncthreads();
+    const size_t item = p.num_graphs > 0 ? (size_t)gi * (size_t)p.tau + (size_t)tloc : (size_t)tree;
     if (p.parents != nullptr) {
-      int32_t* par = p.parents + (size_t)tree * n;
-      for (int32_t v = (int32_t)wid; v < n; v += (int32_t)WT) par[v] = (int32_t)S[v].nxt;
+      int32_t* par = p.parents + (p.num_graphs > 0 ? (size_t)tloc : (size_t)tree) * n + base;
+      for (int32_t v = (int32_t)wid; v < nl; v += (int32_t)WT) par[v] = (int32_t)S[v].nxt;
     }
     if (me == 0 && rank == 0) {
-      if (p.steps != nullptr) p.steps[tree] = (uint64_t)n + sh_pops;
+      if (p.steps != nullptr) p.steps[item] = (uint64_t)nl + sh_pops;
+      if (p.item_ns != nullptr) p.item_ns[item] = global_ns();
       atomicAdd(&p.stats[0], sh_pops);
       atomicAdd(&p.stats[1], sh_deps);
     }
@@ -718,6 +738,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
     else __syncthreads();
   }
 #undef RING
+#undef SV
 #undef REMOTE
 #undef BITW
 #undef GEN_OF

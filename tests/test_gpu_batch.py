@@ -23,11 +23,17 @@ def _batch(seed=1):
     return graphs, alphas, u, offs
 
 
-@pytest.mark.parametrize("walkers,smem", [(0, 0), (64, 1), (32, 2)])
-def test_batch_trees_match_union_oracle(walkers, smem):
+@pytest.mark.parametrize("walkers,smem,kernel,bitmap", [(0, 0, 0, 0), (64, 1, 1, 0), (32, 2, 1, 0),
+                                                        (64, 0, 2, 2), (256, 0, 2, 1), (128, 0, 2, 3)])
+def test_batch_trees_match_union_oracle(walkers, smem, kernel, bitmap):
+    """Both sampler kernels: the CSR-walk kernel (state in shared or global
+    memory) and the edge-record kernel with each tree-membership mode."""
     graphs, alphas, u, offs = _batch()
     G = fc.Graph.batch(u, offs, alphas)
     G.set_shape(walkers, 0, smem)
+    if kernel:
+        G.set_kernel(kernel)
+    G.set_bitmap(bitmap)
     tau = 24
     out = G.sample(99, tau, want_parents=True, want_steps=True)
     av = np.repeat(alphas, np.diff(offs))
@@ -39,6 +45,8 @@ def test_batch_trees_match_union_oracle(walkers, smem):
     np.testing.assert_array_equal(steps.sum(axis=0).astype(np.uint64), ref["steps"])
     lat = G.batch_latency_ms()
     assert lat.shape == (len(graphs),) and np.all(lat > 0)
+    if kernel == 2:
+        assert G.last_kernel() == bitmap + 1
     G.close()
 
 
