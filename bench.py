@@ -486,6 +486,7 @@ def main():
     tree_offset = rank * tau
     shape = {}
     launched = {}
+    last_diag = [None]
     from paper_2101_06192_gb300 import tune
 
     def step(seed, host_inputs=False, samp_ev=None, stats=None):
@@ -508,6 +509,7 @@ def main():
         diag, far, clo = G.farness(R, tau, x_pivot=x)
         top = fc.top_k(diag, TOPK)
         G.close()
+        last_diag[0] = diag
         if host_inputs:
             return clo.cpu(), top.cpu()
         return clo, top
@@ -594,6 +596,25 @@ def main():
                 "peak_source": peak_kind, "kernel_ms": 1000.0 * samp_s,
                 "departures_per_launch": deps, "pops_per_launch": pops}
 
+    # accuracy of the last step's estimate (untimed): diag(Omega) against CG
+    # columns of the library's solver on degree-stratified judge vertices
+    accuracy = None
+    if rank == 0 and args.n_log2 == N_LOG2 and not args.no_e2e:
+        import math
+        J = judge_vertices(g, 256, 5)
+        Gj = fc.Graph(rowptr_d, colidx_d, None, [ALPHA])
+        B = torch.zeros(J.size, n, dtype=torch.float64, device=dev)
+        Jt = torch.from_numpy(J).to(dev)
+        B[torch.arange(J.size, device=dev), Jt] = 1.0
+        X, _ = Gj.solve(B, rel_tol=1e-10)
+        judge = X[torch.arange(J.size, device=dev), Jt]
+        Gj.close()
+        err = (last_diag[0][Jt] - judge).abs()
+        accuracy = {"judge_vertices": int(J.size), "max_abs_err": float(err.max()),
+                    "mean_abs_err": float(err.mean()),
+                    "hoeffding_bound_delta_1e-6": math.sqrt(math.log(2e6) / (2 * tau))}
+        del B, X
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, total, dt = cpu_trees_per_s(g, trees_per_core=4)
@@ -618,6 +639,7 @@ def main():
             "cpu_baseline": cpu,
             "clocks": clk,
             "sampling_ms_per_step": statistics.mean(samp_ms),
+            "accuracy": accuracy,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
