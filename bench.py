@@ -523,7 +523,7 @@ def main():
     if args.shape:
         parts = args.shape.split(",")
         shape = {"walkers": int(parts[0]), "regs": int(parts[1]),
-                 "order": parts[2] if len(parts) > 2 else "degree", "fixed": True}
+                 "order": parts[2] if len(parts) > 2 else "auto", "fixed": True}
     else:
         shape_probe = fc.Graph(rowptr_d, colidx_d, None, [ALPHA])
         shape = tune.autotune(shape_probe, tau)

@@ -126,10 +126,12 @@ fc_status fc_set_sampler_shape(fc_graph* g, int32_t walkers_per_tree, int32_t ma
 
 /*
  * Order in which the sampler's walkers take start vertices: 0 = ascending
- * degree (Algorithm 2's order, the default), 1 = descending degree, 2 =
- * ascending vertex id, 3 = descending vertex id.  The trees do not depend on
- * it (cycle popping); only the amount of waiting between concurrent walkers
- * and the locality of the first steps do (vertex-id order loads start windows
+ * degree (Algorithm 2's order), 1 = descending degree, 2 = ascending vertex
+ * id, 3 = descending vertex id, 4 = automatic (the default: ascending vertex id
+ * unless more than a quarter of the CSR entries join vertices at most 32 ids
+ * apart, then ascending degree).  The trees do not depend on it (cycle
+ * popping); only the amount of waiting between concurrent walkers and the
+ * locality of the first steps do (vertex-id order loads start windows
  * coalesced but makes walkers collide on graphs whose ids follow geometry).
  */
 fc_status fc_set_start_order(fc_graph* g, int32_t order);

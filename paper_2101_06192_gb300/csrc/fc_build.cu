@@ -329,6 +329,20 @@ static int grid_for(int64_t items, int threads) {
   return (int)b;
 }
 
+// Locality of the vertex numbering: CSR entries whose endpoints are at most 32
+// ids apart (high for meshes and road networks numbered along their geometry).
+__global__ void k_id_locality(int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                              unsigned long long* count) {
+  unsigned long long local = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+      const int64_t d = (int64_t)colidx[e] - v;
+      local += (d >= -32 && d <= 32) ? 1ull : 0ull;
+    }
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+}
+
 // Edge records of the edge-record sampler: for CSR entry e with target t,
 // {t, row offset of t, degree of t, min(T_t >> 21, 2^32 - 1)}.
 __global__ void k_edge_records(int64_t nnz, const int32_t* __restrict__ colidx, const uint4* __restrict__ rowinfo,
@@ -591,7 +605,15 @@ static fc_status build_impl(int32_t n, int64_t nnz, const int64_t* rowptr, const
       BUILD_CK((fcx::note_launch(), cudaGetLastError()));
     }
   }
+  unsigned long long* d_local = nullptr;
+  unsigned long long h_local = 0;
   if (nnz > 0) {
+    BUILD_CK(cudaMallocAsync((void**)&d_local, sizeof(unsigned long long), st));
+    BUILD_CK(cudaMemsetAsync(d_local, 0, sizeof(unsigned long long), st));
+    k_id_locality<<<grid_for(n, 256), 256, 0, st>>>(n, g->rowptr, g->colidx, d_local);
+    BUILD_CK((fcx::note_launch(), cudaGetLastError()));
+    BUILD_CK(cudaMemcpyAsync(&h_local, d_local, sizeof(h_local), cudaMemcpyDeviceToHost, st));
+    BUILD_CK(cudaFreeAsync(d_local, st));
     const size_t rec = g->weighted ? 4 : 1;  // uint4 per record
     BUILD_CK(cudaMallocAsync((void**)&g->edges, (size_t)nnz * n_alpha * rec * sizeof(uint4), st));
     for (int a = 0; a < n_alpha; ++a) {
@@ -605,6 +627,7 @@ static fc_status build_impl(int32_t n, int64_t nnz, const int64_t* rowptr, const
     }
   }
   BUILD_CK(cudaStreamSynchronize(st));
+  g->id_local = nnz > 0 && h_local * 4 > (unsigned long long)nnz;
   *out = g;
   return FC_OK;
 }
@@ -664,9 +687,10 @@ extern "C" fc_status fc_set_sampler_shape(fc_graph* g, int32_t walkers_per_tree,
 }
 
 extern "C" fc_status fc_set_start_order(fc_graph* g, int32_t order) {
-  if (g == nullptr || order < 0 || order > 3) return FC_EINVAL;
-  g->order_desc = order & 1;
-  g->order_id = order >> 1;
+  if (g == nullptr || order < 0 || order > 4) return FC_EINVAL;
+  g->order_auto = order == 4;
+  g->order_desc = order == 4 ? 0 : (order & 1);
+  g->order_id = order == 4 ? 0 : (order >> 1);
   return FC_OK;
 }
 

@@ -180,7 +180,9 @@ struct fc_graph {
   int32_t smem_mode = 0;
   int32_t regs = 0;            // register cap of the sampler variant (0 = automatic)
   int32_t order_desc = 0;      // sampler takes start vertices from the high end of the order
-  int32_t order_id = 0;        // start order: 0 = degree (the default), 1 = vertex id (fc_set_start_order)
+  int32_t order_id = 0;        // start order: 0 = degree, 1 = vertex id (fc_set_start_order)
+  bool order_auto = true;      // automatic start order (the default): vertex id unless id_local
+  bool id_local = false;       // the vertex numbering follows the graph's geometry (build-time statistic)
   int32_t kernel_pref = 0;     // 0 = automatic, 1 = CSR-walk kernel, 2 = edge-record kernel
   int32_t pops_mode = 0;       // 0 = automatic, 1 = walk every cycle, 2 = pop from the ring (fc_set_sampler_pops)
   int32_t bitmap_mode = 0;     // 0 = automatic, 1 = state flags, 2 = shared, 3 = global (fc_set_sampler_bitmap)

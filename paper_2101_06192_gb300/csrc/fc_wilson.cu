@@ -491,9 +491,10 @@ struct Shape {
   int64_t slots = 0;  // trees that can be in flight at once
 };
 
-// Launch shape: the largest walker count whose CTAs hold every tree of the
-// launch in one wave (trees of one launch take about equally long), else the
-// shape with the most walkers resident.  Walkers per tree are capped at n/8.
+// Launch shape: the walker count and register variant with the most walkers
+// resident, weighted by how full the waves of trees are (a last wave that is
+// mostly empty costs about as much as a full one).  Walkers per tree are
+// capped at n/8.
 static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool smem, bool edge, int bits,
                               bool ring, int cl, int nsm, int smem_optin, Shape* out) {
   const bool sbits = bits == 1;
@@ -501,9 +502,11 @@ static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool 
   // measured on GB300 (BA n = 2^20, tau = 1024): the 40-register variant is
   // fastest; graphs with long walks prefer more walkers per tree, which the
   // score below already favours
-  const int regs_list[2] = {40, 64};
+  // (edge-record kernel: the 64-register variants; its 48-register ones spill,
+  // the weighted ones heavily, and measured up to 2x slower)
+  const int regs_list[2] = {edge ? 64 : 40, 64};
   double best = -1.0;
-  for (int ri = 0; ri < 2; ++ri) {
+  for (int ri = 0; ri < (edge ? 1 : 2); ++ri) {
     int regs = g->regs > 0 ? g->regs : regs_list[ri];
     if (g->regs > 0 && ri > 0) break;
     if (!edge && regs == 48) regs = 40;
@@ -546,9 +549,9 @@ static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool 
       }
       if (per_sm > 0 && slots > 0) {
         const int64_t waves = (total + slots - 1) / slots;
-        // walkers busy per wave, averaged over the waves
+        // walkers resident, times the average fill of the waves
         const double score = (double)W * (double)std::min<int64_t>(total, slots) * (double)total /
-                             ((double)waves * (double)std::min<int64_t>(total, slots) * (double)waves + 1e-9);
+                             ((double)waves * (double)slots);
         if (score > best * 1.0001) {
           best = score;
           out->W = W;
@@ -719,8 +722,10 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   p.B = g->weighted ? g->B : nullptr;
   p.tau = tau;
   p.tree_offset = tree_offset;
-  p.descending = g->order_desc;
-  p.id_order = g->order_id;
+  // automatic start order: vertex id (start windows load coalesced), except
+  // when the numbering follows the geometry (neighbouring starts would collide)
+  p.descending = g->order_auto ? 0 : g->order_desc;
+  p.id_order = g->order_auto ? !g->id_local : g->order_id;
 
   p.edges = g->edges;
   p.key0 = (uint32_t)seed;

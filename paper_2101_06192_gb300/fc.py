@@ -189,10 +189,10 @@ class Graph:
         _check(lib().fc_set_sampler_shape(self._h, walkers_per_tree, max_trees_resident, smem, regs),
                "fc_set_sampler_shape")
 
-    START_ORDERS = {"degree": 0, "degree_desc": 1, "id": 2, "id_desc": 3}
+    START_ORDERS = {"degree": 0, "degree_desc": 1, "id": 2, "id_desc": 3, "auto": 4}
 
     def set_start_order(self, order):
-        """fc_set_start_order: "degree" (default), "degree_desc", "id", "id_desc"
+        """fc_set_start_order: "auto" (default), "degree", "degree_desc", "id", "id_desc"
         (or the integer code; True/False select descending/ascending degree)."""
         if isinstance(order, bool):
             code = int(order)

@@ -21,8 +21,8 @@ import torch
 
 from . import build as _build
 
-CANDIDATES = [(0, 40), (0, 64), (128, 48), (256, 64), (512, 64), (640, 64), (768, 64), (896, 64), (896, 48),
-              (1024, 64)]
+CANDIDATES = [(0, 64), (32, 64), (64, 64), (128, 64), (256, 64), (512, 64), (640, 64), (768, 64), (896, 64),
+              (1024, 64), (0, 40)]
 ORDERS = ("degree", "id")
 _CACHE = os.path.join(_build.BUILD, "sampler_shapes.json")
 
@@ -53,7 +53,7 @@ def _time(G, seed: int, probe: int):
 
 def apply(G, entry: dict):
     """Apply a tuner entry (start order and shape) to a graph."""
-    G.set_start_order(entry.get("order", "degree"))
+    G.set_start_order(entry.get("order", "auto"))
     G.set_shape(entry.get("walkers", 0), 0, 0, entry.get("regs", 0))
 
 
@@ -67,7 +67,7 @@ def autotune(G, tau: int, probe_trees: int | None = None, seed: int = 12345) -> 
         return dict(cache[key], cached=True)
     probe = probe_trees or max(1, min(tau, 1024 // max(1, G.n_alpha)))
     G.set_shape(0, 0, 0, 0)
-    order, best_t = "degree", None
+    order, best_t = "auto", None
     for o in ORDERS:
         try:
             G.set_start_order(o)

@@ -27,7 +27,7 @@ def test_start_order_and_shape_invariance(kind):
     kernels = (1, 2)
     for kernel in kernels:
         G.set_kernel(kernel)
-        for order in ("degree", "degree_desc", "id", "id_desc"):
+        for order in ("degree", "degree_desc", "id", "id_desc", "auto"):
             for walkers, smem in ((0, 0), (1024, 1), (64, 1), (32, 0)):
                 G.set_start_order(order)
                 G.set_shape(walkers, 0, smem)
