@@ -250,6 +250,34 @@ fc_status fc_sample_usts_async(fc_graph* g, uint64_t seed, int64_t tau, int64_t 
 fc_status fc_sampler_check(fc_graph* g, void* stream);
 
 /*
+ * Rao-Blackwellised estimate of diag(Omega) from sampled trees (an estimator
+ * on the samples of Prop. 1, not in the paper).  With the parents of every
+ * other vertex fixed, v's parent is u* with probability
+ *   1 / (1 + alpha * sum of w_vw over neighbours w outside v's subtree),
+ * which is unbiased for Omega[v, v] and has at most the variance of the
+ * indicator "parent(v) = u*".  fc_rb_accumulate adds, for each of the T trees
+ * in parents (device int32 [T][n], parent n = u*, as written by
+ * fc_sample_usts), floor(value * 2^48 + 1/2) to acc[v] (device uint64 [n],
+ * caller-owned, accumulates; totals do not depend on the order of the trees).
+ * alpha_idx selects the alpha of g (batches: each vertex's graph alpha).
+ * Values are computed in FP64 with one rounding per operation, the sum over
+ * v's CSR row in order.  FC_EINVAL if a parent is out of range or the parents
+ * do not form spanning trees of G* rooted at u*.  Synchronous.  fc_rb_diag
+ * writes diag_out[v] = acc[v] / (2^48 T) (device double [n]), asynchronously.
+ */
+fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int32_t* parents, int64_t T, uint64_t* acc,
+                           void* stream);
+fc_status fc_rb_diag(const uint64_t* acc, int32_t n, int64_t T, double* diag_out, void* stream);
+
+/*
+ * Forest farness (Eq. 3) and closeness (Def. 2) of the vertices of g from a
+ * given estimate diag (device double [n]; batches: per graph).  Either output
+ * may be NULL.  Asynchronous.
+ */
+fc_status fc_farness_from_diag(fc_graph* g, const double* diag, double* farness_out, double* closeness_out,
+                               void* stream);
+
+/*
  * Solve (I + alpha_a L) x_j = b_j for n_rhs right-hand sides by Jacobi-
  * preconditioned CG with FP32 inner iterations and FP64 residual / iterative
  * refinement (the paper's ground truth uses CG at tolerance 1e-9, Sec. 6.1;

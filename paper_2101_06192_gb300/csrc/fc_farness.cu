@@ -181,6 +181,19 @@ __global__ void k_tk_scatter(int32_t n, const uint64_t* __restrict__ kin, const 
   }
 }
 
+// per-block sums of diag in the same fixed tree order as k_combine's
+__global__ void k_block_sums(int32_t n, const double* __restrict__ diag, double* __restrict__ partial) {
+  __shared__ double red[RED_THREADS];
+  const int64_t v = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x;
+  red[threadIdx.x] = v < n ? diag[v] : 0.0;
+  __syncthreads();
+  for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
 }  // namespace fcx
 
 using namespace fcx;
@@ -223,6 +236,39 @@ extern "C" fc_status fc_forest_farness(fc_graph* g, int32_t alpha_idx, const uin
     k_farness<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, diag_out, partial + nb, farness_out, closeness_out);
     FC_LAUNCHED();
   }
+  FC_CK(cudaFreeAsync(partial, st));
+  return FC_OK;
+}
+
+extern "C" fc_status fc_farness_from_diag(fc_graph* g, const double* diag, double* farness_out,
+                                          double* closeness_out, void* stream) {
+  if (g == nullptr || diag == nullptr) {
+    set_error("fc_farness_from_diag: bad argument");
+    return FC_EINVAL;
+  }
+  if (farness_out == nullptr && closeness_out == nullptr) return FC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int32_t n = g->n;
+  if (g->num_graphs > 0) {
+    double* tr = nullptr;
+    FC_CK(cudaMallocAsync((void**)&tr, (size_t)g->num_graphs * sizeof(double), st));
+    k_seg_trace<<<g->num_graphs, RED_THREADS, 0, st>>>(g->voff, diag, tr);
+    FC_LAUNCHED();
+    k_farness_seg<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, g->gid, g->voff, diag, tr, farness_out,
+                                                               closeness_out);
+    FC_LAUNCHED();
+    FC_CK(cudaFreeAsync(tr, st));
+    return FC_OK;
+  }
+  const int64_t nb = (n + RED_THREADS - 1) / RED_THREADS;
+  double* partial = nullptr;
+  FC_CK(cudaMallocAsync((void**)&partial, (nb + 1) * sizeof(double), st));
+  k_block_sums<<<(unsigned)nb, RED_THREADS, 0, st>>>(n, diag, partial);
+  FC_LAUNCHED();
+  k_sum_partials<<<1, 1024, 0, st>>>(partial, nb, partial + nb);
+  FC_LAUNCHED();
+  k_farness<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, diag, partial + nb, farness_out, closeness_out);
+  FC_LAUNCHED();
   FC_CK(cudaFreeAsync(partial, st));
   return FC_OK;
 }

@@ -62,6 +62,9 @@ def lib():
             "fc_p_root": ([P, I32, P, P], ctypes.c_int),
             "fc_top_k": ([P, I32, I32, P, P], ctypes.c_int),
             "fc_tree_roots": ([P, I32, I64, P, P, P], ctypes.c_int),
+            "fc_rb_accumulate": ([P, I32, P, I64, P, P], ctypes.c_int),
+            "fc_rb_diag": ([P, I32, I64, P, P], ctypes.c_int),
+            "fc_farness_from_diag": ([P, P, P, P, P], ctypes.c_int),
             "fc_root_counts": ([P, I32, I64, P, I32, P, P], ctypes.c_int),
             "fc_mlp_param_count": ([], I32),
             "fc_vertex_features": ([P, I32, P, P], ctypes.c_int),
@@ -329,6 +332,32 @@ class Graph:
                                        int(tau), _ptr(diag), _ptr(far), _ptr(clo), _stream(stream)),
                "fc_forest_farness")
         return diag, far, clo
+
+    def rb_accumulate(self, parents, acc=None, alpha_idx: int = 0, stream=None):
+        """fc_rb_accumulate: add the Rao-Blackwellised values of the trees in
+        parents ([T, n] or [n_alpha, T, n] sliced by the caller; int32 CUDA) to acc
+        (uint64 as int64 CUDA, allocated zeroed when not given)."""
+        n = self.n
+        par = parents.reshape(-1, n).contiguous()
+        if acc is None:
+            acc = torch.zeros(n, dtype=torch.int64, device=par.device)
+        _check(lib().fc_rb_accumulate(self._h, int(alpha_idx), _ptr(par), int(par.shape[0]), _ptr(acc),
+                                      _stream(stream)), "fc_rb_accumulate")
+        return acc
+
+    def rb_diag(self, acc, trees: int, stream=None):
+        diag = torch.empty(self.n, dtype=torch.float64, device=acc.device)
+        _check(lib().fc_rb_diag(_ptr(acc), int(self.n), int(trees), _ptr(diag), _stream(stream)), "fc_rb_diag")
+        return diag
+
+    def farness_from_diag(self, diag, stream=None):
+        """fc_farness_from_diag: (farness, closeness) of a diag(Omega) estimate."""
+        _dev_tensor(diag, torch.float64, self.n, "diag")
+        far = torch.empty_like(diag)
+        clo = torch.empty_like(diag)
+        _check(lib().fc_farness_from_diag(self._h, _ptr(diag), _ptr(far), _ptr(clo), _stream(stream)),
+               "fc_farness_from_diag")
+        return far, clo
 
     # ---- learned control variate ----
     def features(self, alpha_idx: int = 0, stream=None):
