@@ -268,11 +268,12 @@ def run_cv(args):
         return r, a.elapsed_time(b)
 
     results = {}
-    for form in ("plain", "cv"):
+    for form in ("plain", "cv", "rb"):
         per_seed = []
         for sd in range(args.seeds):
             R = torch.zeros(g.n, dtype=torch.int32, device="cuda")
             C = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+            acc = torch.zeros(g.n, dtype=torch.int64, device="cuda")
             ms = 0.0
             gp = None
             if form == "cv":
@@ -281,14 +282,25 @@ def run_cv(args):
             done = 0
             hit = None
             for cp in checkpoints:
-                _, dt = timed(lambda: G.sample(50_000 + 1000 * sd, cp - done, tree_offset=done, R=R, C=C))
-                ms += dt
-                done = cp
-                if form == "cv":
-                    (d, _, _), dt = timed(lambda: G.farness(R, cp, C=C, g_pred=gp))
+                if form == "rb":
+                    # the same trees, with their parents, summarised by the
+                    # Rao-Blackwellised conditional probabilities
+                    def rb_step():
+                        o = G.sample(50_000 + 1000 * sd, cp - done, tree_offset=done, R=R, C=C, want_parents=True)
+                        G.rb_accumulate(o["parents"][0], acc=acc)
+                        return G.rb_diag(acc, cp)
+                    d, dt = timed(rb_step)
+                    ms += dt
+                    done = cp
                 else:
-                    (d, _, _), dt = timed(lambda: G.farness(R, cp))
-                ms += dt
+                    _, dt = timed(lambda: G.sample(50_000 + 1000 * sd, cp - done, tree_offset=done, R=R, C=C))
+                    ms += dt
+                    done = cp
+                    if form == "cv":
+                        (d, _, _), dt = timed(lambda: G.farness(R, cp, C=C, g_pred=gp))
+                    else:
+                        (d, _, _), dt = timed(lambda: G.farness(R, cp))
+                    ms += dt
                 err = float((d[Jt] - dj).abs().max())
                 if err <= 0.1:
                     hit = {"trees": cp, "ms": ms, "max_err": err}
@@ -307,6 +319,7 @@ def run_cv(args):
         "speedup_cv_over_plain": (results["plain"]["median_ms"] / results["cv"]["median_ms"]
                                   if results["cv"]["median_ms"] and results["plain"]["median_ms"] else None),
         "trees_plain": results["plain"]["median_trees"], "trees_cv": results["cv"]["median_trees"],
+        "rao_blackwell_ms": results["rb"]["median_ms"], "trees_rao_blackwell": results["rb"]["median_trees"],
         "seeds": args.seeds, "judge": {"vertices": int(J.size), "plain_trees": TJ,
                                        "judge_vs_cg_max_abs": judge_vs_cg},
         "train": {"graphs": "R-MAT scale 16-18 x2, plain targets tau=4096", "steps": 500,

@@ -14,13 +14,21 @@
 // once per operation; per tree it is added in fixed point, floor(value *
 // 2^48 + 1/2), so totals do not depend on the order of the additions.
 //
-// One cooperative kernel handles a chunk of trees with every resident CTA;
-// grid-wide barriers separate the phases: child counts (with validation), a
-// grid-wide exclusive scan, children and roots, level-synchronous BFS from
-// the roots, subtree sizes bottom-up, preorder numbers top-down, and one
-// thread per (tree, vertex) scanning the vertex's row.  Every loop bound and
-// every early exit is read from global memory after a barrier, so all CTAs
-// take the same path through the barriers.
+// One cooperative kernel handles a chunk of up to 32 trees with every
+// resident CTA; grid-wide barriers separate the phases, and none of them
+// takes a barrier per tree level, so deep trees cost no more barriers than
+// shallow ones: child counts (with validation); subtree sizes and sibling
+// offsets by peeling leaves (one atomic per tree node, the node finished by
+// whichever thread delivers its last child); preorder numbers by pointer
+// jumping down the paths (O(log depth) rounds); the rows; and the
+// per-vertex sums.  Preorder numbers and sizes are stored vertex-major
+// across the chunk's trees, so a warp scanning a row with one lane per tree
+// reads each neighbour's numbers for all trees in one 128-byte line.  Long
+// unweighted rows are split into segments of 256 entries whose counts add
+// up exactly; a weighted row stays with one warp so that each lane adds its
+// tree's weights in row order.  Every loop bound and every early exit is
+// read from global memory after a barrier, so all CTAs take the same path
+// through the barriers.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -35,10 +43,12 @@ namespace {
 
 constexpr int RB_T = 256;
 constexpr int RB_FRAC = 48;
+constexpr int RB_SEG = 256;  // entries per segment of a long unweighted row
+constexpr int RB_TMAX = 32;  // trees per chunk: one per lane of a warp
 
 struct RBParams {
   int32_t n;
-  int32_t Tc;                 // trees in this chunk
+  int32_t Tc;                 // trees in this chunk (at most 32: one per lane)
   const int64_t* rowptr;
   const int32_t* colidx;
   const float* w;             // or null
@@ -46,17 +56,21 @@ struct RBParams {
   const double* alpha_v;      // per-vertex alpha (batches) or null
   const int32_t* parents;     // [Tc][n]
   uint64_t* acc;              // [n] fixed-point sums
-  // scratch, flat index i = t * n + v
-  uint32_t* cnt;              // children counts
-  uint32_t* off;              // exclusive prefix of cnt (flat)
-  int32_t* child;             // children of every (tree, vertex), contiguous
-  int32_t* ordr;              // flat ids level by level (BFS order)
-  int32_t* lvl;               // [n + 2] level offsets into ordr
-  int32_t* size;              // fill counter during the scatter, then subtree sizes
-  int32_t* tin;               // preorder numbers
+  const int2* segs;           // row segments {v, k}: entries [rowptr[v] + k RB_SEG, ...) of row v
+  const uint32_t* nseg;       // number of segments
+  // scratch.  Per tree node flat index i = t (n + 1) + v, where v = n is the
+  // tree's u*; vertex-major index v Tc + t.
+  uint32_t* cnt;              // [Tc (n + 1)] children counts (zeroed by the host)
+  unsigned long long* word;   // [Tc][16 wb] {summed sizes of finished children, finished children} (zeroed)
+  int64_t wb;                 // ceil((n + 1) / 16): the words of vertices v and v + 1 lie wb apart
+  unsigned long long* jw;     // [Tc (n + 1)] pointer-jumping words {ancestor, partial preorder number}
+  int32_t* size;              // [n][Tc] subtree sizes (vertex-major)
+  int32_t* tin;               // [n][Tc] preorder numbers (vertex-major)
+  double* sout;               // [n][Tc] weighted: sum over neighbours outside the subtree
+  uint32_t* outc;             // [n][Tc] unweighted: count of neighbours outside the subtree
+  uint32_t* rsum;             // [Tc (n + 1)] exclusive scan of the roots' subtree sizes
   uint32_t* bsum;             // [gridDim.x] block totals of the scan
-  uint32_t* ctr;              // [0] ordr appends, [2] error
-  uint32_t* next_tin;         // [Tc] next free preorder number per tree
+  uint32_t* ctr;              // [2] error, [4..6] active counts of the jumping rounds (zeroed by the host)
 };
 
 __device__ __forceinline__ uint32_t block_exscan_u32(uint32_t x, uint32_t* total, uint32_t* wsum) {
@@ -85,161 +99,344 @@ __device__ __forceinline__ uint32_t block_exscan_u32(uint32_t x, uint32_t* total
   return ex;
 }
 
+// Grid-wide exclusive scan out[i] = sum_{j < i} val(j) (mod 2^32) over
+// [0, len): each CTA scans a contiguous range, CTA 0 scans the range totals,
+// and each CTA adds its carry.  Ends without a trailing barrier.
+template <class F>
+__device__ void grid_exscan(cg::grid_group& grid, F val, uint32_t* out, int64_t len, uint32_t* bsum,
+                            uint32_t* wsum, uint32_t* carry) {
+  const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+  const int64_t b0 = std::min<int64_t>(len, (int64_t)blockIdx.x * chunk);
+  const int64_t b1 = std::min<int64_t>(len, b0 + chunk);
+  if (threadIdx.x == 0) *carry = 0;
+  __syncthreads();
+  for (int64_t base = b0; base < b1; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const uint32_t x = i < b1 ? val(i) : 0u;
+    uint32_t tot = 0;
+    const uint32_t ex = block_exscan_u32(x, &tot, wsum);
+    if (i < b1) out[i] = *carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) *carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[blockIdx.x] = *carry;
+  grid.sync();
+  if (blockIdx.x == 0) {
+    if (threadIdx.x == 0) *carry = 0;
+    __syncthreads();
+    for (int base = 0; base < (int)gridDim.x; base += blockDim.x) {
+      const int j = base + threadIdx.x;
+      const uint32_t x = j < (int)gridDim.x ? bsum[j] : 0u;
+      uint32_t tot = 0;
+      const uint32_t ex = block_exscan_u32(x, &tot, wsum);
+      if (j < (int)gridDim.x) bsum[j] = *carry + ex;
+      __syncthreads();
+      if (threadIdx.x == 0) *carry += tot;
+      __syncthreads();
+    }
+  }
+  grid.sync();
+  const uint32_t add = bsum[blockIdx.x];
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) out[i] += add;
+}
+
+__device__ __forceinline__ unsigned long long jw_pack(int32_t anc, int32_t sum) {
+  return (unsigned long long)(uint32_t)anc | ((unsigned long long)(uint32_t)sum << 32);
+}
+
+constexpr int RB_TILE = 256;  // vertices per tile of the vertex-major transpose
+
 __global__ void __launch_bounds__(RB_T) k_rb(RBParams p) {
   cg::grid_group grid = cg::this_grid();
+  __shared__ int32_t tile[RB_TMAX][RB_TILE + 1];
   __shared__ uint32_t wsum[32];
-  __shared__ uint32_t sh_carry;
+  __shared__ uint32_t carry;
   const int32_t n = p.n;
-  const int64_t N = (int64_t)p.Tc * n;
+  const int32_t n1 = n + 1;
+  const int32_t Tc = p.Tc;
+  const int64_t N1 = (int64_t)Tc * n1;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = gtid >> 5, nwarps = gstride >> 5;
+#define VT(t, v) ((int64_t)(v) * Tc + (t))
+  // Low vertex ids are often the hubs (the parents of many nodes); spreading
+  // consecutive ids over 16 columns keeps their atomics off one cache line.
+#define WI(t, v) ((int64_t)(t) * 16 * p.wb + (int64_t)((v) & 15) * p.wb + ((v) >> 4))
 
   // ---- child counts; parents must lie in [0, n] and differ from the vertex ----
-  for (int64_t i = gtid; i < N; i += gstride) {
-    const int32_t v = (int32_t)(i % n);
-    const int32_t par = p.parents[i];
-    p.size[i] = 0;
+  for (int64_t i = gtid; i < N1; i += gstride) {
+    const int32_t t = (int32_t)(i / n1), v = (int32_t)(i - (int64_t)t * n1);
+    if (v == n) {
+      p.jw[i] = jw_pack(-1, -1);
+      continue;
+    }
+    const int32_t par = p.parents[(int64_t)t * n + v];
     if (par < 0 || par > n || par == v) atomicOr(&p.ctr[2], ERR_INVAL);
-    else if (par < n) atomicAdd(&p.cnt[i - v + par], 1u);
+    else if (par < n) atomicAdd(&p.cnt[(int64_t)t * n1 + par], 1u);  // u*'s children: a scan below
   }
   grid.sync();
   if (*(volatile uint32_t*)&p.ctr[2] != 0u) return;  // uniform: read after the barrier
 
-  // ---- exclusive scan of cnt over the flat index: block ranges, then block totals ----
-  const int64_t chunk = (N + gridDim.x - 1) / gridDim.x;
-  const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = std::min<int64_t>(N, b0 + chunk);
-  if (threadIdx.x == 0) sh_carry = 0;
-  __syncthreads();
-  for (int64_t base = b0; base < b1; base += blockDim.x) {
-    const int64_t i = base + threadIdx.x;
-    const uint32_t x = i < b1 ? p.cnt[i] : 0u;
-    uint32_t tot = 0;
-    const uint32_t ex = block_exscan_u32(x, &tot, wsum);
-    if (i < b1) p.off[i] = sh_carry + ex;
-    __syncthreads();
-    if (threadIdx.x == 0) sh_carry += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) p.bsum[blockIdx.x] = sh_carry;
-  grid.sync();
-  if (blockIdx.x == 0) {
-    if (threadIdx.x == 0) sh_carry = 0;
-    __syncthreads();
-    for (int base = 0; base < (int)gridDim.x; base += blockDim.x) {
-      const int j = base + threadIdx.x;
-      const uint32_t x = j < (int)gridDim.x ? p.bsum[j] : 0u;
-      uint32_t tot = 0;
-      const uint32_t ex = block_exscan_u32(x, &tot, wsum);
-      if (j < (int)gridDim.x) p.bsum[j] = sh_carry + ex;
-      __syncthreads();
-      if (threadIdx.x == 0) sh_carry += tot;
-      __syncthreads();
-    }
-  }
-  grid.sync();
+  // ---- subtree sizes and sibling offsets by peeling leaves.  A finished
+  // child adds {its size, 1} to its parent's word in one atomic; the sizes
+  // already there are its earlier-finished siblings', so 1 + that sum is its
+  // offset in the parent's preorder interval (any sibling order gives valid
+  // intervals, and subtree membership does not depend on it).  The thread
+  // that delivers a parent's last child carries on with the parent: no
+  // barrier per tree level.  The roots (u*'s children, often most vertices)
+  // take their offsets from a scan instead of one contended word. ----
+  // Each warp loads its candidates 32 at a time (coalesced, one chunk
+  // ahead) and hands the leaves among them to whichever lanes are idle, so
+  // a lane that keeps delivering last (and so carries chain after chain)
+  // does not hold up the warp's other leaves.  A step loads the parent's
+  // child count and the grandparent before its atomic, so all three are in
+  // flight together.
   {
-    const uint32_t add = p.bsum[blockIdx.x];
-    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) p.off[i] += add;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t nchunks = (N1 + 31) / 32;
+    const int64_t nmine = gwarp < nchunks ? (nchunks - gwarp + nwarps - 1) / nwarps : 0;
+    int32_t nt = 0, nv = n, np = 0;  // prefetched chunk: this lane's node
+    uint32_t nc = 1u;
+    auto load = [&](int64_t j) {
+      const int64_t i = (gwarp + j * nwarps) * 32 + lane;
+      nt = 0;
+      nv = n;
+      nc = 1u;
+      np = 0;
+      if (j < nmine && i < N1) {
+        nt = (int32_t)(i / n1);
+        nv = (int32_t)(i - (int64_t)nt * n1);
+        if (nv != n) {
+          nc = p.cnt[i];
+          np = p.parents[(int64_t)nt * n + nv];
+        }
+      }
+    };
+    load(0);
+    int64_t jn = 1;      // chunks loaded so far (warp-uniform)
+    unsigned lmask = 0;  // leaves of the current chunk not yet taken (warp-uniform)
+    int32_t ct = 0, cv = 0, cpar = 0;  // this lane's node of the current chunk
+    int32_t t = -1, v = 0, par = 0;
+    uint32_t s = 0;
+    for (;;) {
+      if (lmask == 0u && jn <= nmine) {  // the prefetched chunk becomes current
+        ct = nt;
+        cv = nv;
+        cpar = np;
+        lmask = __ballot_sync(0xffffffffu, nv != n && nc == 0u);
+        load(jn);
+        ++jn;
+      }
+      const unsigned need = __ballot_sync(0xffffffffu, t < 0);
+      if (need == 0xffffffffu && lmask == 0u && jn > nmine) break;  // uniform
+      const int avail = __popc(lmask);
+      const int ntake = min(__popc(need), avail);
+      const int r = __popc(need & lt);
+      const bool take = t < 0 && r < avail;
+      const int src = take ? (int)__fns(lmask, 0, r + 1) : lane;
+      const int32_t tt = __shfl_sync(0xffffffffu, ct, src);
+      const int32_t tv = __shfl_sync(0xffffffffu, cv, src);
+      const int32_t tp = __shfl_sync(0xffffffffu, cpar, src);
+      // the first ntake leaves are taken
+      lmask = ntake == avail ? 0u : lmask & ~((1u << __fns(lmask, 0, ntake + 1)) - 1u);
+      if (take) {
+        t = tt;
+        v = tv;
+        par = tp;
+        s = 1u;
+        p.size[VT(t, v)] = 1;
+      }
+      if (t < 0) continue;
+      if (par == n) {  // a root: offsets from the scan below
+        t = -1;
+        continue;
+      }
+      const int64_t pi = (int64_t)t * n1 + par;
+      const uint32_t cp = p.cnt[pi];
+      const int32_t gp = p.parents[(int64_t)t * n + par];
+      const unsigned long long old = atomicAdd(&p.word[WI(t, par)], (1ull << 32) | s);
+      p.jw[(int64_t)t * n1 + v] = jw_pack((int32_t)pi, (int32_t)(1u + (uint32_t)old));
+      if ((uint32_t)(old >> 32) + 1u != cp) {
+        t = -1;
+        continue;
+      }
+      s = 1u + (uint32_t)old + s;
+      v = par;
+      par = gp;
+      p.size[VT(t, v)] = (int32_t)s;
+    }
   }
   grid.sync();
+  // roots in vertex order: preorder number = sizes of the tree's earlier roots
+  grid_exscan(
+      grid,
+      [&](int64_t i) {
+        const int32_t t = (int32_t)(i / n1), v = (int32_t)(i - (int64_t)t * n1);
+        return (v < n && p.parents[(int64_t)t * n + v] == n) ? 1u + (uint32_t)p.word[WI(t, v)] : 0u;
+      },
+      p.rsum, N1, p.bsum, wsum, &carry);
+  grid.sync();
+  for (int64_t i = gtid; i < N1; i += gstride) {
+    const int32_t t = (int32_t)(i / n1), v = (int32_t)(i - (int64_t)t * n1);
+    const uint32_t base = p.rsum[(int64_t)t * n1];
+    if (v == n) {
+      // a parent cycle leaves its vertices and their subtrees outside u*'s tree
+      if (p.rsum[i] - base != (uint32_t)n) atomicOr(&p.ctr[2], ERR_INVAL);
+    } else if (p.parents[(int64_t)t * n + v] == n) {
+      p.jw[i] = jw_pack(-1, (int32_t)(p.rsum[i] - base));
+    }
+  }
+  grid.sync();
+  if (*(volatile uint32_t*)&p.ctr[2] != 0u) return;
 
-  // ---- children (in any order) and the roots as BFS level 0 ----
-  for (int64_t i = gtid; i < N; i += gstride) {
-    const int32_t v = (int32_t)(i % n);
-    const int32_t par = p.parents[i];
-    if (par < n) {
-      const int64_t pi = i - v + par;
-      p.child[p.off[pi] + (uint32_t)atomicAdd(&p.size[pi], 1)] = v;
-    } else {
-      p.ordr[atomicAdd(&p.ctr[0], 1u)] = (int32_t)i;
+  // ---- preorder numbers: each node's number is its parent's plus its
+  // offset, summed down the path by pointer jumping.  Invariant: tin(i) =
+  // sum(i) + tin(anc(i)), with anc = -1 once sum is the number itself; words
+  // are read and written whole, so a node may read an ancestor's word of
+  // this round or the last one.  O(log depth) rounds. ----
+  for (int r = 0;; ++r) {
+    uint32_t active = 0;
+    for (int64_t i = gtid; i < N1; i += gstride) {
+      volatile unsigned long long* jv = p.jw;
+      const unsigned long long w0 = jv[i];
+      const int32_t a = (int32_t)(uint32_t)w0;
+      if (a < 0) continue;
+      const unsigned long long w1 = jv[a];
+      const int32_t a1 = (int32_t)(uint32_t)w1;
+      jv[i] = jw_pack(a1, (int32_t)((uint32_t)(w0 >> 32) + (uint32_t)(w1 >> 32)));
+      active += a1 >= 0;
     }
-  }
-  grid.sync();
-  if (gtid == 0) {
-    p.lvl[0] = 0;
-    p.lvl[1] = (int32_t)p.ctr[0];
-  }
-  grid.sync();
-
-  // ---- BFS levels: level d is ordr[lvl[d], lvl[d + 1]) ----
-  int32_t D = 0;  // levels
-  for (int32_t d = 0; d <= n; ++d) {
-    const int32_t a0 = *(volatile int32_t*)&p.lvl[d], a1 = *(volatile int32_t*)&p.lvl[d + 1];
-    if (a1 == a0) {
-      D = d;
-      break;
-    }
-    for (int64_t j = a0 + gtid; j < a1; j += gstride) {
-      const int32_t i = p.ordr[j];
-      const int32_t t0 = i - i % n;
-      const uint32_t c0 = p.off[i], cn = p.cnt[i];
-      for (uint32_t k = 0; k < cn; ++k) p.ordr[atomicAdd(&p.ctr[0], 1u)] = t0 + p.child[c0 + k];
-    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) active += __shfl_xor_sync(0xffffffffu, active, o);
+    if (lane == 0 && active) atomicAdd(&p.ctr[4 + r % 3], active);
+    if (gtid == 0) p.ctr[4 + (r + 1) % 3] = 0u;  // read two rounds ago, after that round's barrier
     grid.sync();
-    if (gtid == 0) p.lvl[d + 2] = (int32_t)p.ctr[0];
-    grid.sync();
-  }
-  if (*(volatile int32_t*)&p.lvl[D] != (int32_t)N) {  // a parent cycle: not a forest rooted at u*
-    if (gtid == 0) atomicOr(&p.ctr[2], ERR_INVAL);
-    return;  // uniform: every CTA read the same lvl[D]
-  }
-
-  // ---- subtree sizes, deepest level first ----
-  for (int32_t d = D - 1; d >= 0; --d) {
-    const int32_t a0 = p.lvl[d], a1 = p.lvl[d + 1];
-    for (int64_t j = a0 + gtid; j < a1; j += gstride) {
-      const int32_t i = p.ordr[j];
-      const int32_t t0 = i - i % n;
-      const uint32_t c0 = p.off[i], cn = p.cnt[i];
-      int32_t s = 1;
-      for (uint32_t k = 0; k < cn; ++k) s += p.size[t0 + p.child[c0 + k]];
-      p.size[i] = s;
+    if (*(volatile uint32_t*)&p.ctr[4 + r % 3] == 0u) break;  // uniform
+    if (r >= 64) {  // depth below 2^31 needs at most 32 rounds
+      if (gtid == 0) atomicOr(&p.ctr[2], ERR_INVAL);
+      return;
     }
-    grid.sync();
   }
-
-  // ---- preorder numbers, roots first, then each vertex numbers its children ----
-  for (int64_t j = gtid; j < p.lvl[1]; j += gstride) {
-    const int32_t i = p.ordr[j];
-    p.tin[i] = (int32_t)atomicAdd(&p.next_tin[i / n], (uint32_t)p.size[i]);
+  // preorder numbers to vertex-major order through a shared-memory tile
+  // (coalesced on both sides); the per-row sums start at zero
+  for (int64_t v0 = (int64_t)blockIdx.x * RB_TILE; v0 < n; v0 += (int64_t)gridDim.x * RB_TILE) {
+    const int32_t nv = (int32_t)std::min<int64_t>(RB_TILE, n - v0);
+    for (int t = 0; t < Tc; ++t)
+      for (int x = threadIdx.x; x < nv; x += blockDim.x) tile[t][x] = (int32_t)(p.jw[(int64_t)t * n1 + v0 + x] >> 32);
+    __syncthreads();
+    const int64_t k1 = (int64_t)nv * Tc;
+    for (int64_t k = threadIdx.x; k < k1; k += blockDim.x) {
+      const int32_t x = (int32_t)(k / Tc), t = (int32_t)(k - (int64_t)x * Tc);
+      p.tin[v0 * Tc + k] = tile[t][x];
+      if (p.w) p.sout[v0 * Tc + k] = 0.0;
+      else p.outc[v0 * Tc + k] = 0u;
+    }
+    __syncthreads();
   }
   grid.sync();
-  for (int32_t d = 0; d + 1 < D; ++d) {
-    const int32_t a0 = p.lvl[d], a1 = p.lvl[d + 1];
-    for (int64_t j = a0 + gtid; j < a1; j += gstride) {
-      const int32_t i = p.ordr[j];
-      const int32_t t0 = i - i % n;
-      const uint32_t c0 = p.off[i], cn = p.cnt[i];
-      int32_t run = p.tin[i] + 1;
-      for (uint32_t k = 0; k < cn; ++k) {
-        const int32_t ci = t0 + p.child[c0 + k];
-        p.tin[ci] = run;
-        run += p.size[ci];
+
+  // ---- neighbours outside the subtree: a warp per row segment, a lane per
+  // tree (each lane sums its tree's weights in row order; unweighted counts
+  // of the segments of a long row add up exactly) ----
+  const int64_t nseg = *p.nseg;
+  for (int64_t sg = gwarp; sg < nseg; sg += nwarps) {
+    const int2 sv = p.segs[sg];
+    const int32_t v = sv.x;
+    const int64_t r1 = p.rowptr[v + 1];
+    const int64_t e0 = p.rowptr[v] + (int64_t)sv.y * RB_SEG;
+    const int64_t e1 = p.w ? r1 : std::min<int64_t>(r1, e0 + RB_SEG);
+    const bool on = lane < Tc;
+    int32_t lo = 0, hi = 0;
+    if (on) {
+      lo = p.tin[VT(lane, v)];
+      hi = lo + p.size[VT(lane, v)];
+    }
+    double s = 0.0;
+    uint32_t c = 0;
+    // 32 entries at a time: lane j loads entry j, the warp broadcasts them
+    // and each lane tests its own tree, in row order
+    for (int64_t eb = e0; eb < e1; eb += 32) {
+      const int32_t m = (int32_t)std::min<int64_t>(32, e1 - eb);
+      const int32_t uj = lane < m ? __ldg(p.colidx + eb + lane) : 0;
+      const float wj = (p.w && lane < m) ? __ldg(p.w + eb + lane) : 0.f;
+      if (m == 32) {
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+          const int32_t u = __shfl_sync(0xffffffffu, uj, k);
+          const float wk = __shfl_sync(0xffffffffu, wj, k);
+          if (on) {
+            const int32_t tu = p.tin[VT(lane, u)];
+            if (tu < lo || tu >= hi) {
+              if (p.w) s = __dadd_rn(s, (double)wk);
+              else ++c;
+            }
+          }
+        }
+      } else {
+        for (int k = 0; k < m; ++k) {
+          const int32_t u = __shfl_sync(0xffffffffu, uj, k);
+          const float wk = __shfl_sync(0xffffffffu, wj, k);
+          if (on) {
+            const int32_t tu = p.tin[VT(lane, u)];
+            if (tu < lo || tu >= hi) {
+              if (p.w) s = __dadd_rn(s, (double)wk);
+              else ++c;
+            }
+          }
+        }
       }
     }
-    grid.sync();
-  }
-
-  // ---- the conditional probability of every (tree, vertex) ----
-  for (int64_t i = gtid; i < N; i += gstride) {
-    const int32_t v = (int32_t)(i % n);
-    const int64_t t0 = i - v;
-    const int32_t lo = p.tin[i], hi = lo + p.size[i];
-    double s = 0.0;
-    for (int64_t e = p.rowptr[v]; e < p.rowptr[v + 1]; ++e) {
-      const int32_t tu = p.tin[t0 + p.colidx[e]];
-      if (tu < lo || tu >= hi) s = __dadd_rn(s, p.w ? (double)p.w[e] : 1.0);
+    if (on) {
+      if (p.w) p.sout[VT(lane, v)] = s;  // weighted rows are one segment
+      else if (c) atomicAdd(&p.outc[VT(lane, v)], c);
     }
-    const double a = p.alpha_v ? p.alpha_v[v] : p.alpha;
-    const double val = __ddiv_rn(1.0, __dadd_rn(1.0, __dmul_rn(a, s)));
-    const uint64_t q = (uint64_t)__dadd_rn(__dmul_rn(val, (double)(1ull << RB_FRAC)), 0.5);
-    atomicAdd((unsigned long long*)&p.acc[v], (unsigned long long)q);
   }
+  grid.sync();
+
+  // ---- the conditional probabilities, summed over the chunk's trees ----
+  for (int64_t v = gwarp; v < n; v += nwarps) {
+    uint64_t q = 0;
+    if (lane < Tc) {
+      const double s = p.w ? p.sout[VT(lane, v)] : (double)p.outc[VT(lane, v)];
+      const double a = p.alpha_v ? p.alpha_v[v] : p.alpha;
+      const double val = __ddiv_rn(1.0, __dadd_rn(1.0, __dmul_rn(a, s)));
+      q = (uint64_t)__dadd_rn(__dmul_rn(val, (double)(1ull << RB_FRAC)), 0.5);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0) atomicAdd((unsigned long long*)&p.acc[v], (unsigned long long)q);
+  }
+#undef VT
+#undef WI
 }
 
 __global__ void k_rb_diag(int32_t n, const uint64_t* __restrict__ acc, double denom, double* __restrict__ diag) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
     diag[v] = __ddiv_rn((double)acc[v], denom);
+}
+
+// Segments per row: unweighted rows split every RB_SEG entries (their
+// integer counts add up exactly); weighted rows stay whole so that each
+// tree's sum keeps the row order.  cnt has n + 1 entries, the last 0.
+__global__ void k_seg_count(int32_t n, const int64_t* __restrict__ rowptr, bool weighted, uint32_t* __restrict__ cnt) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t c = 0;
+    if (v < n) {
+      const int64_t d = rowptr[v + 1] - rowptr[v];
+      c = weighted ? (d > 0 ? 1u : 0u) : (uint32_t)((d + RB_SEG - 1) / RB_SEG);
+    }
+    cnt[v] = c;
+  }
+}
+
+__global__ void k_seg_fill(int32_t n, const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off,
+                           int2* __restrict__ segs) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t o = off[v];
+    for (uint32_t k = 0; k < cnt[v]; ++k) segs[o + k] = make_int2((int32_t)v, (int32_t)k);
+  }
 }
 
 }  // namespace
@@ -267,14 +464,19 @@ extern "C" fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int3
   }
   FC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rb, RB_T, 0));
   const int grid = std::max(1, per_sm) * nsm;  // every CTA resident: required by the grid barriers
-  // trees per chunk: 24 bytes of scratch per (tree, vertex), at most 4 GB and
-  // flat ids below 2^31
-  const int64_t cap = std::max<int64_t>(1, std::min<int64_t>((int64_t)(4ull << 30) / (24ll * n),
+  // trees per chunk: one per lane, 32 bytes of scratch per (tree, vertex), at
+  // most 4 GB and flat ids below 2^31
+  // trees per chunk: one per lane, 40 bytes of scratch per (tree, vertex)
+  // within a sixteenth of the device (1 to 16 GB), flat ids below 2^31
+  const int64_t budget = std::max<int64_t>(1ll << 30, std::min<int64_t>(16ll << 30, (int64_t)(g->device_bytes / 16)));
+  const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(budget / (40ll * (n + 1)),
                                                              ((int64_t)1 << 31) / ((int64_t)n + 1) - 1));
-  const int64_t Tc_max = std::min<int64_t>(T, cap);
-  const size_t N = (size_t)Tc_max * n;
+  const int64_t Tc_max = std::min<int64_t>(std::min<int64_t>(T, RB_TMAX), cap);
+  const size_t N1 = (size_t)Tc_max * (n + 1), N = (size_t)Tc_max * n;
+  const int64_t seg_max = (int64_t)n + g->nnz / RB_SEG + 1;  // bound on the number of segments
   char* ws = nullptr;
-  const size_t bytes = N * 4 * 6 + ((size_t)n + 2) * 4 + (size_t)grid * 4 + 16 + (size_t)Tc_max * 4 + 256 * 8;
+  const size_t bytes = N1 * 4 * 2 + (size_t)grid * 4 + (N1 + 16 * (size_t)Tc_max) * 8 * 2 + N * 4 * 2 + N * 8 + 32 +
+                       ((size_t)n + 1) * 8 + (size_t)seg_max * 8 + 256 * 12;
   FC_CK(cudaMallocAsync((void**)&ws, bytes, st));
   auto carve = [&](size_t b) {
     char* r = ws;
@@ -290,26 +492,43 @@ extern "C" fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int3
   p.alpha = g->alphas[alpha_idx];
   p.alpha_v = g->num_graphs > 0 ? g->alpha_v : nullptr;
   p.acc = acc;
-  p.cnt = (uint32_t*)carve(N * 4);
-  p.off = (uint32_t*)carve(N * 4);
-  p.child = (int32_t*)carve(N * 4);
-  p.ordr = (int32_t*)carve(N * 4);
+  p.cnt = (uint32_t*)carve(N1 * 4);
+  p.wb = ((int64_t)n + 1 + 15) / 16;
+  p.word = (unsigned long long*)carve((size_t)Tc_max * 16 * p.wb * 8);
+  p.jw = (unsigned long long*)carve(N1 * 8);
   p.size = (int32_t*)carve(N * 4);
   p.tin = (int32_t*)carve(N * 4);
-  p.lvl = (int32_t*)carve(((size_t)n + 2) * 4);
+  p.sout = (double*)carve(N * 8);  // the unweighted counts use its first half
+  p.outc = (uint32_t*)p.sout;
+  p.rsum = (uint32_t*)carve(N1 * 4);
   p.bsum = (uint32_t*)carve((size_t)grid * 4);
-  p.ctr = (uint32_t*)carve(16);
-  p.next_tin = (uint32_t*)carve((size_t)Tc_max * 4);
+  p.ctr = (uint32_t*)carve(32);
+  uint32_t* scnt = (uint32_t*)carve(((size_t)n + 1) * 4);
+  uint32_t* soff = (uint32_t*)carve(((size_t)n + 1) * 4);
+  int2* segs = (int2*)carve((size_t)seg_max * 8);
   ws = base;
+  p.segs = segs;
+  p.nseg = soff + n;
+  {
+    const unsigned b = (unsigned)std::min<int64_t>(((int64_t)n + 256) / 256, (int64_t)nsm * 16);
+    k_seg_count<<<b, 256, 0, st>>>(n, g->rowptr, g->w != nullptr, scnt);
+    FC_LAUNCHED();
+    const fc_status r = exclusive_scan(scnt, soff, (int64_t)n + 1, st);
+    if (r != FC_OK) {
+      FC_CK(cudaFreeAsync(base, st));
+      return r;
+    }
+    k_seg_fill<<<b, 256, 0, st>>>(n, scnt, soff, segs);
+    FC_LAUNCHED();
+  }
   fc_status status = FC_OK;
   for (int64_t t0 = 0; t0 < T && status == FC_OK; t0 += Tc_max) {
     const int32_t Tc = (int32_t)std::min<int64_t>(Tc_max, T - t0);
     p.Tc = Tc;
     p.parents = parents + (size_t)t0 * n;
-    const size_t Nc = (size_t)Tc * n;
-    FC_CK(cudaMemsetAsync(p.cnt, 0, Nc * 4, st));
-    FC_CK(cudaMemsetAsync(p.ctr, 0, 16, st));
-    FC_CK(cudaMemsetAsync(p.next_tin, 0, (size_t)Tc * 4, st));
+    FC_CK(cudaMemsetAsync(p.cnt, 0, (size_t)Tc * (n + 1) * 4, st));
+    FC_CK(cudaMemsetAsync(p.word, 0, (size_t)Tc * 16 * p.wb * 8, st));
+    FC_CK(cudaMemsetAsync(p.ctr, 0, 32, st));
     void* args[] = {&p};
     FC_CK(cudaLaunchCooperativeKernel((void*)k_rb, dim3(grid), dim3(RB_T), args, 0, st));
     FC_LAUNCHED();

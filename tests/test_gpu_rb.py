@@ -19,7 +19,21 @@ def _u64(t):
     return t.cpu().numpy().view(np.uint64)
 
 
-@pytest.mark.parametrize("kind", ["er", "er_w", "grid_w", "ba_hubs_w", "isolated"])
+def _hubs(weighted):
+    """ER plus two hubs joined to 700 and 300 vertices: rows longer than one
+    256-entry segment."""
+    base = synth.erdos_renyi(1000, 4, 13)
+    u, v, _ = base.edges()
+    rng = np.random.default_rng(14)
+    hu = np.concatenate([np.zeros(700, np.int64), np.ones(300, np.int64)])
+    hv = np.concatenate([rng.choice(np.arange(2, 1000), 700, replace=False),
+                         rng.choice(np.arange(2, 1000), 300, replace=False)])
+    u, v = np.concatenate([u, hu]), np.concatenate([v, hv])
+    w = rng.uniform(0.25, 4.0, u.size).astype(np.float32) if weighted else None
+    return synth.from_edges(1000, u, v, w)
+
+
+@pytest.mark.parametrize("kind", ["er", "er_w", "grid_w", "ba_hubs_w", "isolated", "hubs", "hubs_w"])
 def test_fixed_point_sums_bit_exact(kind):
     if kind == "er":
         g, alpha, tau = synth.erdos_renyi(1500, 6, 3), 1.0, 12
@@ -29,6 +43,10 @@ def test_fixed_point_sums_bit_exact(kind):
         g, alpha, tau = synth.perturbed_grid(40, 35, 2), 3.0, 8
     elif kind == "ba_hubs_w":
         g, alpha, tau = synth.barabasi_albert(3000, 4, 5, weighted=True), 0.3, 6
+    elif kind == "hubs":  # long unweighted rows split, three chunks of trees
+        g, alpha, tau = _hubs(False), 0.7, 70
+    elif kind == "hubs_w":  # long weighted rows, two chunks
+        g, alpha, tau = _hubs(True), 0.4, 40
     else:
         base = synth.barabasi_albert(300, 2, 9)
         u, v, _ = base.edges()
