@@ -56,7 +56,7 @@ struct RBParams {
   const double* alpha_v;      // per-vertex alpha (batches) or null
   const int32_t* parents;     // [Tc][n]
   uint64_t* acc;              // [n] fixed-point sums
-  const int2* segs;           // row segments {v, k}: entries [rowptr[v] + k RB_SEG, ...) of row v
+  const int4* segs;           // row segments {v, entries, first entry (low, high word)}
   const uint32_t* nseg;       // number of segments
   // scratch.  Per tree node flat index i = t (n + 1) + v, where v = n is the
   // tree's u*; vertex-major index v Tc + t.
@@ -70,7 +70,7 @@ struct RBParams {
   uint32_t* outc;             // [n][Tc] unweighted: count of neighbours outside the subtree
   uint32_t* rsum;             // [Tc (n + 1)] exclusive scan of the roots' subtree sizes
   uint32_t* bsum;             // [gridDim.x] block totals of the scan
-  uint32_t* ctr;              // [2] error, [4..6] active counts of the jumping rounds (zeroed by the host)
+  uint32_t* ctr;              // [2] error, [4..6] active counts of the jumping rounds, [7] chunk grabs (zeroed)
 };
 
 __device__ __forceinline__ uint32_t block_exscan_u32(uint32_t x, uint32_t* total, uint32_t* wsum) {
@@ -187,25 +187,43 @@ __global__ void __launch_bounds__(RB_T) k_rb(RBParams p) {
   // that delivers a parent's last child carries on with the parent: no
   // barrier per tree level.  The roots (u*'s children, often most vertices)
   // take their offsets from a scan instead of one contended word. ----
-  // Each warp loads its candidates 32 at a time (coalesced, one chunk
-  // ahead) and hands the leaves among them to whichever lanes are idle, so
-  // a lane that keeps delivering last (and so carries chain after chain)
-  // does not hold up the warp's other leaves.  A step loads the parent's
-  // child count and the grandparent before its atomic, so all three are in
-  // flight together.
+  // Warps take candidates in chunks of 32 (coalesced, one chunk ahead)
+  // from a shared counter, eight chunks per grab, and hand the leaves among
+  // them to whichever lanes are idle.  The last deliverer of a node carries
+  // on with it, so chains pile up on some lanes; warps so held up take fewer
+  // chunks, and the rest of their lanes keep taking leaves.  A step loads the
+  // parent's child count and the grandparent before its atomic, so all three
+  // are in flight together.
   {
     const unsigned lt = (1u << lane) - 1u;
     const int64_t nchunks = (N1 + 31) / 32;
-    const int64_t nmine = gwarp < nchunks ? (nchunks - gwarp + nwarps - 1) / nwarps : 0;
+    int64_t sc = 0;  // current grab (warp-uniform)
+    int kc = 8;      // next chunk within it
+    bool dry = false;
+    auto next_chunk = [&]() -> int64_t {
+      if (dry) return -1;
+      if (kc == 8) {
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(&p.ctr[7], 1u);
+        sc = __shfl_sync(0xffffffffu, g, 0);
+        kc = 0;
+      }
+      const int64_t c = sc * 8 + kc++;
+      if (c >= nchunks) dry = true;
+      return dry ? -1 : c;
+    };
     int32_t nt = 0, nv = n, np = 0;  // prefetched chunk: this lane's node
     uint32_t nc = 1u;
-    auto load = [&](int64_t j) {
-      const int64_t i = (gwarp + j * nwarps) * 32 + lane;
+    bool pre = false;  // a prefetched chunk is waiting (warp-uniform)
+    auto load = [&]() {
+      const int64_t c = next_chunk();
+      pre = c >= 0;
       nt = 0;
       nv = n;
       nc = 1u;
       np = 0;
-      if (j < nmine && i < N1) {
+      const int64_t i = c * 32 + lane;
+      if (pre && i < N1) {
         nt = (int32_t)(i / n1);
         nv = (int32_t)(i - (int64_t)nt * n1);
         if (nv != n) {
@@ -214,23 +232,21 @@ __global__ void __launch_bounds__(RB_T) k_rb(RBParams p) {
         }
       }
     };
-    load(0);
-    int64_t jn = 1;      // chunks loaded so far (warp-uniform)
+    load();
     unsigned lmask = 0;  // leaves of the current chunk not yet taken (warp-uniform)
     int32_t ct = 0, cv = 0, cpar = 0;  // this lane's node of the current chunk
     int32_t t = -1, v = 0, par = 0;
     uint32_t s = 0;
     for (;;) {
-      if (lmask == 0u && jn <= nmine) {  // the prefetched chunk becomes current
+      if (lmask == 0u && pre) {  // the prefetched chunk becomes current
         ct = nt;
         cv = nv;
         cpar = np;
         lmask = __ballot_sync(0xffffffffu, nv != n && nc == 0u);
-        load(jn);
-        ++jn;
+        load();
       }
       const unsigned need = __ballot_sync(0xffffffffu, t < 0);
-      if (need == 0xffffffffu && lmask == 0u && jn > nmine) break;  // uniform
+      if (need == 0xffffffffu && lmask == 0u && !pre) break;  // uniform
       const int avail = __popc(lmask);
       const int ntake = min(__popc(need), avail);
       const int r = __popc(need & lt);
@@ -340,13 +356,15 @@ __global__ void __launch_bounds__(RB_T) k_rb(RBParams p) {
   // ---- neighbours outside the subtree: a warp per row segment, a lane per
   // tree (each lane sums its tree's weights in row order; unweighted counts
   // of the segments of a long row add up exactly) ----
+  // The next segment's record is loaded while the current one is scanned.
   const int64_t nseg = *p.nseg;
+  int4 nxt = gwarp < nseg ? p.segs[gwarp] : make_int4(0, 0, 0, 0);
   for (int64_t sg = gwarp; sg < nseg; sg += nwarps) {
-    const int2 sv = p.segs[sg];
+    const int4 sv = nxt;
+    if (sg + nwarps < nseg) nxt = p.segs[sg + nwarps];
     const int32_t v = sv.x;
-    const int64_t r1 = p.rowptr[v + 1];
-    const int64_t e0 = p.rowptr[v] + (int64_t)sv.y * RB_SEG;
-    const int64_t e1 = p.w ? r1 : std::min<int64_t>(r1, e0 + RB_SEG);
+    const int64_t e0 = (int64_t)(((uint64_t)(uint32_t)sv.w << 32) | (uint32_t)sv.z);
+    const int64_t e1 = e0 + sv.y;
     const bool on = lane < Tc;
     int32_t lo = 0, hi = 0;
     if (on) {
@@ -432,10 +450,15 @@ __global__ void k_seg_count(int32_t n, const int64_t* __restrict__ rowptr, bool 
 }
 
 __global__ void k_seg_fill(int32_t n, const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off,
-                           int2* __restrict__ segs) {
+                           const int64_t* __restrict__ rowptr, bool weighted, int4* __restrict__ segs) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t o = off[v];
-    for (uint32_t k = 0; k < cnt[v]; ++k) segs[o + k] = make_int2((int32_t)v, (int32_t)k);
+    const int64_t r0 = rowptr[v], r1 = rowptr[v + 1];
+    for (uint32_t k = 0; k < cnt[v]; ++k) {
+      const int64_t e0 = r0 + (int64_t)k * RB_SEG;
+      const int32_t m = (int32_t)(weighted ? r1 - r0 : std::min<int64_t>(RB_SEG, r1 - e0));
+      segs[o + k] = make_int4((int32_t)v, m, (int32_t)(uint32_t)e0, (int32_t)(uint32_t)((uint64_t)e0 >> 32));
+    }
   }
 }
 
@@ -476,7 +499,7 @@ extern "C" fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int3
   const int64_t seg_max = (int64_t)n + g->nnz / RB_SEG + 1;  // bound on the number of segments
   char* ws = nullptr;
   const size_t bytes = N1 * 4 * 2 + (size_t)grid * 4 + (N1 + 16 * (size_t)Tc_max) * 8 * 2 + N * 4 * 2 + N * 8 + 32 +
-                       ((size_t)n + 1) * 8 + (size_t)seg_max * 8 + 256 * 12;
+                       ((size_t)n + 1) * 8 + (size_t)seg_max * 16 + 256 * 12;
   FC_CK(cudaMallocAsync((void**)&ws, bytes, st));
   auto carve = [&](size_t b) {
     char* r = ws;
@@ -505,7 +528,7 @@ extern "C" fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int3
   p.ctr = (uint32_t*)carve(32);
   uint32_t* scnt = (uint32_t*)carve(((size_t)n + 1) * 4);
   uint32_t* soff = (uint32_t*)carve(((size_t)n + 1) * 4);
-  int2* segs = (int2*)carve((size_t)seg_max * 8);
+  int4* segs = (int4*)carve((size_t)seg_max * 16);
   ws = base;
   p.segs = segs;
   p.nseg = soff + n;
@@ -518,7 +541,7 @@ extern "C" fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int3
       FC_CK(cudaFreeAsync(base, st));
       return r;
     }
-    k_seg_fill<<<b, 256, 0, st>>>(n, scnt, soff, segs);
+    k_seg_fill<<<b, 256, 0, st>>>(n, scnt, soff, g->rowptr, g->w != nullptr, segs);
     FC_LAUNCHED();
   }
   fc_status status = FC_OK;
