@@ -89,6 +89,22 @@ def profiled_traffic(kname, launched):
         return None
 
 
+def nvtx_push(name):
+    try:
+        import torch
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def nvtx_pop():
+    try:
+        import torch
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -550,6 +566,7 @@ def main():
     clocks.start()
     step_ms, samp_ms, stats = [], [], []
     launches0 = fc.launch_count()
+    nvtx_push("timed")  # profilers can restrict a capture to this range
     for i in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
@@ -563,6 +580,7 @@ def main():
         barrier()
         step_ms.append(a.elapsed_time(b))
         samp_ms.append(sa.elapsed_time(sb))
+    nvtx_pop()
     launches = fc.launch_count() - launches0
     clk = clocks.stop()
     R_sum = int(R.sum().item())
