@@ -61,8 +61,8 @@ struct RBParams {
   // scratch.  Per tree node flat index i = t (n + 1) + v, where v = n is the
   // tree's u*; vertex-major index v Tc + t.
   uint32_t* cnt;              // [Tc (n + 1)] children counts (zeroed by the host)
-  unsigned long long* word;   // [Tc][16 wb] {summed sizes of finished children, finished children} (zeroed)
-  int64_t wb;                 // ceil((n + 1) / 16): the words of vertices v and v + 1 lie wb apart
+  unsigned long long* word;   // [Tc (n + 1)] {summed sizes of finished children, finished children} (zeroed)
+  uint32_t* rsz;              // [Tc (n + 1)] subtree size of each root, 0 elsewhere
   unsigned long long* jw;     // [Tc (n + 1)] pointer-jumping words {ancestor, partial preorder number}
   int32_t* size;              // [n][Tc] subtree sizes (vertex-major)
   int32_t* tin;               // [n][Tc] preorder numbers (vertex-major)
@@ -71,6 +71,8 @@ struct RBParams {
   uint32_t* rsum;             // [Tc (n + 1)] exclusive scan of the roots' subtree sizes
   uint32_t* bsum;             // [gridDim.x] block totals of the scan
   uint32_t* ctr;              // [2] error, [4..6] active counts of the jumping rounds, [7] chunk grabs (zeroed)
+  const uint64_t* qtab;       // unweighted, one alpha: fixed-point value for each count of outside neighbours, or null
+
 };
 
 __device__ __forceinline__ uint32_t block_exscan_u32(uint32_t x, uint32_t* total, uint32_t* wsum) {
@@ -147,7 +149,7 @@ __device__ __forceinline__ unsigned long long jw_pack(int32_t anc, int32_t sum) 
 
 constexpr int RB_TILE = 256;  // vertices per tile of the vertex-major transpose
 
-__global__ void __launch_bounds__(RB_T) k_rb(RBParams p) {
+__global__ void __launch_bounds__(RB_T, 5) k_rb(RBParams p) {
   cg::grid_group grid = cg::this_grid();
   __shared__ int32_t tile[RB_TMAX][RB_TILE + 1];
   __shared__ uint32_t wsum[32];
@@ -161,13 +163,11 @@ __global__ void __launch_bounds__(RB_T) k_rb(RBParams p) {
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = gtid >> 5, nwarps = gstride >> 5;
 #define VT(t, v) ((int64_t)(v) * Tc + (t))
-  // Low vertex ids are often the hubs (the parents of many nodes); spreading
-  // consecutive ids over 16 columns keeps their atomics off one cache line.
-#define WI(t, v) ((int64_t)(t) * 16 * p.wb + (int64_t)((v) & 15) * p.wb + ((v) >> 4))
 
   // ---- child counts; parents must lie in [0, n] and differ from the vertex ----
   for (int64_t i = gtid; i < N1; i += gstride) {
     const int32_t t = (int32_t)(i / n1), v = (int32_t)(i - (int64_t)t * n1);
+    p.rsz[i] = 0u;
     if (v == n) {
       p.jw[i] = jw_pack(-1, -1);
       continue;
@@ -265,14 +265,15 @@ __global__ void __launch_bounds__(RB_T) k_rb(RBParams p) {
         p.size[VT(t, v)] = 1;
       }
       if (t < 0) continue;
-      if (par == n) {  // a root: offsets from the scan below
+      if (par == n) {  // a root: its offset comes from the scan below
+        p.rsz[(int64_t)t * n1 + v] = s;
         t = -1;
         continue;
       }
       const int64_t pi = (int64_t)t * n1 + par;
       const uint32_t cp = p.cnt[pi];
       const int32_t gp = p.parents[(int64_t)t * n + par];
-      const unsigned long long old = atomicAdd(&p.word[WI(t, par)], (1ull << 32) | s);
+      const unsigned long long old = atomicAdd(&p.word[pi], (1ull << 32) | s);
       p.jw[(int64_t)t * n1 + v] = jw_pack((int32_t)pi, (int32_t)(1u + (uint32_t)old));
       if ((uint32_t)(old >> 32) + 1u != cp) {
         t = -1;
@@ -286,13 +287,7 @@ __global__ void __launch_bounds__(RB_T) k_rb(RBParams p) {
   }
   grid.sync();
   // roots in vertex order: preorder number = sizes of the tree's earlier roots
-  grid_exscan(
-      grid,
-      [&](int64_t i) {
-        const int32_t t = (int32_t)(i / n1), v = (int32_t)(i - (int64_t)t * n1);
-        return (v < n && p.parents[(int64_t)t * n + v] == n) ? 1u + (uint32_t)p.word[WI(t, v)] : 0u;
-      },
-      p.rsum, N1, p.bsum, wsum, &carry);
+  grid_exscan(grid, [&](int64_t i) { return p.rsz[i]; }, p.rsum, N1, p.bsum, wsum, &carry);
   grid.sync();
   for (int64_t i = gtid; i < N1; i += gstride) {
     const int32_t t = (int32_t)(i / n1), v = (int32_t)(i - (int64_t)t * n1);
@@ -300,7 +295,7 @@ __global__ void __launch_bounds__(RB_T) k_rb(RBParams p) {
     if (v == n) {
       // a parent cycle leaves its vertices and their subtrees outside u*'s tree
       if (p.rsum[i] - base != (uint32_t)n) atomicOr(&p.ctr[2], ERR_INVAL);
-    } else if (p.parents[(int64_t)t * n + v] == n) {
+    } else if (p.rsz[i] != 0u) {
       p.jw[i] = jw_pack(-1, (int32_t)(p.rsum[i] - base));
     }
   }
@@ -374,34 +369,26 @@ __global__ void __launch_bounds__(RB_T) k_rb(RBParams p) {
     double s = 0.0;
     uint32_t c = 0;
     // 32 entries at a time: lane j loads entry j, the warp broadcasts them
-    // and each lane tests its own tree, in row order
+    // and each lane tests its own tree, in row order; the preorder numbers of
+    // eight neighbours are loaded before any is tested, so eight loads are in
+    // flight (a neighbour past the row's end reads as inside the subtree)
     for (int64_t eb = e0; eb < e1; eb += 32) {
       const int32_t m = (int32_t)std::min<int64_t>(32, e1 - eb);
       const int32_t uj = lane < m ? __ldg(p.colidx + eb + lane) : 0;
       const float wj = (p.w && lane < m) ? __ldg(p.w + eb + lane) : 0.f;
-      if (m == 32) {
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) {
-          const int32_t u = __shfl_sync(0xffffffffu, uj, k);
-          const float wk = __shfl_sync(0xffffffffu, wj, k);
-          if (on) {
-            const int32_t tu = p.tin[VT(lane, u)];
-            if (tu < lo || tu >= hi) {
-              if (p.w) s = __dadd_rn(s, (double)wk);
-              else ++c;
-            }
-          }
+      for (int k0 = 0; k0 < m; k0 += 8) {
+        int32_t tu[8];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const int32_t u = __shfl_sync(0xffffffffu, uj, (k0 + kk) & 31);
+          tu[kk] = (on && k0 + kk < m) ? p.tin[VT(lane, u)] : lo;
         }
-      } else {
-        for (int k = 0; k < m; ++k) {
-          const int32_t u = __shfl_sync(0xffffffffu, uj, k);
-          const float wk = __shfl_sync(0xffffffffu, wj, k);
-          if (on) {
-            const int32_t tu = p.tin[VT(lane, u)];
-            if (tu < lo || tu >= hi) {
-              if (p.w) s = __dadd_rn(s, (double)wk);
-              else ++c;
-            }
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const float wk = __shfl_sync(0xffffffffu, wj, (k0 + kk) & 31);
+          if (tu[kk] < lo || tu[kk] >= hi) {
+            if (p.w) s = __dadd_rn(s, (double)wk);
+            else ++c;
           }
         }
       }
@@ -416,7 +403,9 @@ __global__ void __launch_bounds__(RB_T) k_rb(RBParams p) {
   // ---- the conditional probabilities, summed over the chunk's trees ----
   for (int64_t v = gwarp; v < n; v += nwarps) {
     uint64_t q = 0;
-    if (lane < Tc) {
+    if (lane < Tc && p.qtab) {
+      q = p.qtab[p.outc[VT(lane, v)]];  // the same FP64 steps, done once per count
+    } else if (lane < Tc) {
       const double s = p.w ? p.sout[VT(lane, v)] : (double)p.outc[VT(lane, v)];
       const double a = p.alpha_v ? p.alpha_v[v] : p.alpha;
       const double val = __ddiv_rn(1.0, __dadd_rn(1.0, __dmul_rn(a, s)));
@@ -427,7 +416,16 @@ __global__ void __launch_bounds__(RB_T) k_rb(RBParams p) {
     if (lane == 0) atomicAdd((unsigned long long*)&p.acc[v], (unsigned long long)q);
   }
 #undef VT
-#undef WI
+}
+
+// Fixed-point value of 1 / (1 + alpha c) for every count c = 0..cmax of
+// outside neighbours (unweighted graphs, one alpha), with the FP64 steps of
+// the per-tree formula, so a table lookup gives the same bits.
+__global__ void k_rb_table(double alpha, int32_t cmax, uint64_t* __restrict__ qtab) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= cmax; c += (int64_t)gridDim.x * blockDim.x) {
+    const double val = __ddiv_rn(1.0, __dadd_rn(1.0, __dmul_rn(alpha, (double)c)));
+    qtab[c] = (uint64_t)__dadd_rn(__dmul_rn(val, (double)(1ull << RB_FRAC)), 0.5);
+  }
 }
 
 __global__ void k_rb_diag(int32_t n, const uint64_t* __restrict__ acc, double denom, double* __restrict__ diag) {
@@ -489,17 +487,17 @@ extern "C" fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int3
   const int grid = std::max(1, per_sm) * nsm;  // every CTA resident: required by the grid barriers
   // trees per chunk: one per lane, 32 bytes of scratch per (tree, vertex), at
   // most 4 GB and flat ids below 2^31
-  // trees per chunk: one per lane, 40 bytes of scratch per (tree, vertex)
+  // trees per chunk: one per lane, 44 bytes of scratch per (tree, vertex)
   // within a sixteenth of the device (1 to 16 GB), flat ids below 2^31
   const int64_t budget = std::max<int64_t>(1ll << 30, std::min<int64_t>(16ll << 30, (int64_t)(g->device_bytes / 16)));
-  const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(budget / (40ll * (n + 1)),
+  const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(budget / (44ll * (n + 1)),
                                                              ((int64_t)1 << 31) / ((int64_t)n + 1) - 1));
   const int64_t Tc_max = std::min<int64_t>(std::min<int64_t>(T, RB_TMAX), cap);
   const size_t N1 = (size_t)Tc_max * (n + 1), N = (size_t)Tc_max * n;
   const int64_t seg_max = (int64_t)n + g->nnz / RB_SEG + 1;  // bound on the number of segments
   char* ws = nullptr;
-  const size_t bytes = N1 * 4 * 2 + (size_t)grid * 4 + (N1 + 16 * (size_t)Tc_max) * 8 * 2 + N * 4 * 2 + N * 8 + 32 +
-                       ((size_t)n + 1) * 8 + (size_t)seg_max * 16 + 256 * 12;
+  const size_t bytes = N1 * 4 * 3 + (size_t)grid * 4 + N1 * 8 * 2 + N * 4 * 2 + N * 8 + 32 +
+                       ((size_t)n + 1) * 8 + (size_t)seg_max * 16 + ((size_t)g->max_deg + 1) * 8 + 256 * 16;
   FC_CK(cudaMallocAsync((void**)&ws, bytes, st));
   auto carve = [&](size_t b) {
     char* r = ws;
@@ -516,8 +514,8 @@ extern "C" fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int3
   p.alpha_v = g->num_graphs > 0 ? g->alpha_v : nullptr;
   p.acc = acc;
   p.cnt = (uint32_t*)carve(N1 * 4);
-  p.wb = ((int64_t)n + 1 + 15) / 16;
-  p.word = (unsigned long long*)carve((size_t)Tc_max * 16 * p.wb * 8);
+  p.word = (unsigned long long*)carve(N1 * 8);
+  p.rsz = (uint32_t*)carve(N1 * 4);
   p.jw = (unsigned long long*)carve(N1 * 8);
   p.size = (int32_t*)carve(N * 4);
   p.tin = (int32_t*)carve(N * 4);
@@ -526,6 +524,9 @@ extern "C" fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int3
   p.rsum = (uint32_t*)carve(N1 * 4);
   p.bsum = (uint32_t*)carve((size_t)grid * 4);
   p.ctr = (uint32_t*)carve(32);
+  const bool table = g->w == nullptr && g->num_graphs == 0;
+  uint64_t* qtab = table ? (uint64_t*)carve(((size_t)g->max_deg + 1) * 8) : nullptr;
+  p.qtab = qtab;
   uint32_t* scnt = (uint32_t*)carve(((size_t)n + 1) * 4);
   uint32_t* soff = (uint32_t*)carve(((size_t)n + 1) * 4);
   int4* segs = (int4*)carve((size_t)seg_max * 16);
@@ -543,6 +544,11 @@ extern "C" fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int3
     }
     k_seg_fill<<<b, 256, 0, st>>>(n, scnt, soff, g->rowptr, g->w != nullptr, segs);
     FC_LAUNCHED();
+    if (table) {
+      const unsigned bt = (unsigned)std::min<int64_t>(((int64_t)g->max_deg + 256) / 256, (int64_t)nsm * 4);
+      k_rb_table<<<bt, 256, 0, st>>>(p.alpha, g->max_deg, qtab);
+      FC_LAUNCHED();
+    }
   }
   fc_status status = FC_OK;
   for (int64_t t0 = 0; t0 < T && status == FC_OK; t0 += Tc_max) {
@@ -550,7 +556,7 @@ extern "C" fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int3
     p.Tc = Tc;
     p.parents = parents + (size_t)t0 * n;
     FC_CK(cudaMemsetAsync(p.cnt, 0, (size_t)Tc * (n + 1) * 4, st));
-    FC_CK(cudaMemsetAsync(p.word, 0, (size_t)Tc * 16 * p.wb * 8, st));
+    FC_CK(cudaMemsetAsync(p.word, 0, (size_t)Tc * (n + 1) * 8, st));
     FC_CK(cudaMemsetAsync(p.ctr, 0, 32, st));
     void* args[] = {&p};
     FC_CK(cudaLaunchCooperativeKernel((void*)k_rb, dim3(grid), dim3(RB_T), args, 0, st));
