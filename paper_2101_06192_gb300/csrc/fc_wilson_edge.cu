@@ -148,6 +148,10 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
 #define BITW(v) ((BITS == 1 && CL) ? REMOTE(&sh_bits[((uint32_t)((v) - base) >> 5) >> clog],          \
                                           ((uint32_t)((v) - base) >> 5) & (C - 1))                   \
                                    : &sh_bits[(uint32_t)((v) - base) >> 5])
+  // the step just taken lands on a vertex already in the tree (bitmap modes):
+  // the path is finished in this iteration instead of at the next claim (the
+  // bitmap only gains bits, so the answer is final)
+#define EARLY_HIT(v) (BITS != 0 && ((*BITW(v) >> ((v) & 31)) & 1u))
   // current generation of walker w of this tree
 #define GEN_OF(w) (CL ? *REMOTE(&sh_gen[(w) % (uint32_t)W], (w) / (uint32_t)W) : sh_gen[(w)])
   // stop every CTA working on this tree
@@ -433,6 +437,10 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
               xth = er.w;
               cur ^= 1u;
               mode = E_CLAIM;
+              if (EARLY_HIT(x)) {
+                CNT(CNT_TREE_HIT);
+                finished = true;
+              }
               break;
             }
             if (mode == E_CLAIM2) {
@@ -562,6 +570,10 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             xth = er.w;
             cur ^= 1u;
             mode = E_CLAIM;
+            if (EARLY_HIT(x)) {
+              CNT(CNT_TREE_HIT);
+              finished = true;
+            }
             break;
           }
           case E_POP: {
@@ -741,6 +753,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
 #undef SV
 #undef REMOTE
 #undef BITW
+#undef EARLY_HIT
 #undef GEN_OF
 #undef ABORT_TREE
 #undef ADD_ST
