@@ -109,8 +109,8 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
   // start window of this warp: row info and state record of each slot (copied
   // asynchronously) and its vertex
   uint4* sh_wri = (uint4*)(smem_raw + (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15));
-  uint4* sh_wst = sh_wri + W;
-  uint32_t* sh_wv = (uint32_t*)(sh_wst + W);
+  uint4* sh_wst = sh_wri + W;  // BITS = 0 only
+  uint32_t* sh_wv = (uint32_t*)(sh_wri + (BITS == 0 ? 2 : 1) * W);
   // [2][W][12] slot-threshold high words of each walker's current / next vertex (WGT)
   uint32_t* sh_thr = (uint32_t*)(((uintptr_t)(sh_wv + W) + 15) & ~(uintptr_t)15);
   // in-tree bitmap [ceil(n / 32)] (BITS = 1: shared memory, 2: this CTA's global region)
@@ -784,11 +784,12 @@ WilsonFn wilson_edge_fn(int bits, bool wgt, bool ring, bool cl, int regs) {
   return edge_fn_wgt<0, false>(wgt, ring, regs);
 }
 
-size_t wilson_edge_smem(int W, int32_t n, bool sbits, bool wgt, int C) {  // sbits: bitmap in shared memory
-  const size_t base = (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15) + (size_t)W * (16 + 16 + 4);
+size_t wilson_edge_smem(int W, int32_t n, int bits, bool wgt, int C) {
+  // the start window keeps state records only when membership is a state flag
+  const size_t base = (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15) + (size_t)W * (16 + (bits == 0 ? 16 : 0) + 4);
   const size_t words = ((size_t)n + 31) / 32;
   return ((base + 15) & ~(size_t)15) + (wgt ? (size_t)W * 2 * 12 * 4 : 0) +
-         (sbits ? ((words + (size_t)C - 1) / (size_t)C) * 4 : 0);
+         (bits == 1 ? ((words + (size_t)C - 1) / (size_t)C) * 4 : 0);
 }
 
 }  // namespace fcx
