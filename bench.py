@@ -47,10 +47,11 @@ def parse():
     ap.add_argument("--n-log2", type=int, default=N_LOG2,
                     help="BA size 2^k (profiling cases only; the benchmark is 2^20)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["ba", "cv", "grid", "batch"], default="ba",
+    ap.add_argument("--workload", choices=["ba", "cv", "grid", "batch", "rb"], default="ba",
                     help="ba: the benchmark line; cv: time to eps = 0.1, learned control variate vs "
                          "plain (R-MAT scale 22); grid: 2048^2 road-like grid, three alphas in one launch; "
-                         "batch: 4096 uneven graphs in one launch")
+                         "batch: 4096 uneven graphs in one launch; rb: Rao-Blackwellised accumulation of "
+                         "32 sampled trees of R-MAT (--rmat-scale)")
     ap.add_argument("--graphs", type=int, default=4096)
     ap.add_argument("--rmat-scale", type=int, default=22)
     ap.add_argument("--seeds", type=int, default=5)
@@ -473,9 +474,68 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_rb(args):
+    """Rao-Blackwellised accumulation (fc_rb_accumulate) of 32 trees sampled
+    with their parents on R-MAT(scale, 16), alpha = 1: (tree, vertex) pairs per
+    second of the accumulation alone, inputs resident, L2 flushed before each
+    timed call."""
+    import torch
+    import synth
+    from paper_2101_06192_gb300 import fc
+    torch.cuda.set_device(0)
+    g = synth.rmat(args.rmat_scale, 16, 4)
+    G = fc.Graph.from_csr(g, [1.0])
+    T = 32
+    par = G.sample(6, T, want_parents=True)["parents"][0]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        G.rb_accumulate(par)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms = []
+    nvtx_push("timed")
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        G.rb_accumulate(par)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    nvtx_pop()
+    clk = clocks.stop()
+    t = statistics.mean(ms) / 1000.0
+    n, nnz = g.n, int(g.rowptr[-1])
+    # algorithmic bytes per call: parents read, CSR rows read once, one
+    # neighbour test per (tree, CSR entry) reading a 4-byte preorder number,
+    # one u64 total per vertex
+    alg = 4 * T * n + (4 * nnz + 8 * (n + 1)) + 4 * T * nnz + 8 * n
+    peaks, peak_kind = load_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    line = {"metric": "tree-vertices/s (Rao-Blackwellised accumulation)", "value": T * n / t,
+            "unit": "tree-vertices/s", "ms_per_call": statistics.mean(ms), "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "u64 fixed point / f64",
+            "data": "synthetic", "config": {"workload": f"R-MAT scale {args.rmat_scale} ef 16, alpha=1, 32 trees "
+                                                        "with parents, one chunk", "n": n, "nnz": nnz,
+                                            "l2": "flushed before every timed call (512 MB write)"},
+            "roofline": {"bound": "hbm", "achieved": alg / t / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / t / 1e9 / peak, "traffic": None, "kernel": "k_rb",
+                         "algorithmic_bytes": alg, "peak_source": peak_kind},
+            "clocks": clk}
+    G.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.workload == "rb":
+        if rank == 0:
+            run_rb(args)
+        return
     if args.workload == "batch":
         if rank == 0:
             run_batch(args)
