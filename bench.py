@@ -47,11 +47,14 @@ def parse():
     ap.add_argument("--n-log2", type=int, default=N_LOG2,
                     help="BA size 2^k (profiling cases only; the benchmark is 2^20)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["ba", "cv", "grid", "batch", "rb"], default="ba",
+    ap.add_argument("--workload", choices=["ba", "cv", "grid", "batch", "rb", "group"], default="ba",
                     help="ba: the benchmark line; cv: time to eps = 0.1, learned control variate vs "
                          "plain (R-MAT scale 22); grid: 2048^2 road-like grid, three alphas in one launch; "
                          "batch: 4096 uneven graphs in one launch; rb: Rao-Blackwellised accumulation of "
-                         "32 sampled trees of R-MAT (--rmat-scale)")
+                         "32 sampled trees of R-MAT (--rmat-scale); group: greedy group forest closeness "
+                         "(Algorithm 3) on a weighted BA graph of --group-n vertices, --group-k members")
+    ap.add_argument("--group-n", type=int, default=16384)
+    ap.add_argument("--group-k", type=int, default=64)
     ap.add_argument("--graphs", type=int, default=4096)
     ap.add_argument("--rmat-scale", type=int, default=22)
     ap.add_argument("--seeds", type=int, default=5)
@@ -529,9 +532,83 @@ def run_rb(args):
     print(json.dumps(line), flush=True)
 
 
+def run_group(args):
+    """Greedy group forest closeness (fc_group_closeness, Algorithm 3) on a
+    weighted BA graph (m = 4, weights U[0.5, 3]), alpha = 1: the whole call
+    (forest matrix by CG, the grounded inverse, k - 1 greedy passes) and the
+    greedy part alone (a k = 1 call subtracted)."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2101_06192_gb300 import fc
+    torch.cuda.set_device(0)
+    n, k = args.group_n, args.group_k
+    base = synth.barabasi_albert(n, 4, 7)
+    u, v, _ = base.edges()
+    rng = np.random.default_rng(8)
+    g = synth.from_edges(n, u, v, rng.uniform(0.5, 3.0, u.size).astype(np.float32))
+    G = fc.Graph.from_csr(g, [1.0])
+    stream = torch.cuda.current_stream()
+
+    def timed(kk):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        S, far = G.group_closeness(kk)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), S, far
+
+    for _ in range(max(1, args.warmup)):
+        timed(k)
+    clocks = ClockSampler(0)
+    clocks.start()
+    nvtx_push("timed")
+    full = [timed(k) for _ in range(args.steps)]
+    one = [timed(1)[0] for _ in range(args.steps)]
+    nvtx_pop()
+    clk = clocks.stop()
+    t_full = statistics.median(x[0] for x in full)
+    t_one = statistics.median(one)
+    per_step = (t_full - t_one) / max(1, k - 1)
+    S, far = full[-1][1].cpu().numpy(), full[-1][2].cpu().numpy()
+    n1 = n + 1
+    pass_bytes = 16.0 * n1 * n1  # M read and written once per greedy step
+    peaks, peak_kind = load_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    line = {"metric": "group forest closeness, greedy steps/s (Algorithm 3)", "value": 1000.0 / per_step,
+            "unit": "steps/s", "ms_total": t_full, "ms_setup_k1": t_one, "ms_per_greedy_step": per_step,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"weighted BA n={n} m=4 w~U[0.5,3], alpha=1, k={k}", "n": n, "k": k,
+                       "nnz": int(g.rowptr[-1])},
+            "roofline": {"bound": "hbm", "achieved": pass_bytes / (per_step / 1000.0) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": pass_bytes / (per_step / 1000.0) / 1e9 / peak, "traffic": None,
+                         "kernel": "k_grp_pass (with k_grp_pick, k_grp_trace)", "bytes_per_step": pass_bytes,
+                         "fp64_fma_per_step": 2.0 * n1 * n1, "peak_source": peak_kind},
+            "group_head": S[:8].tolist(), "farness_first_last": [float(far[0]), float(far[-1])],
+            "clocks": clk}
+    if not args.no_cpu_baseline:
+        from oracle import group as ogroup
+        ns = 2048
+        us, vs, _ = synth.barabasi_albert(ns, 4, 7).edges()
+        gs = synth.from_edges(ns, us, vs, np.random.default_rng(9).uniform(0.5, 3.0, us.size).astype(np.float32))
+        t0 = time.perf_counter()
+        ogroup.greedy(gs, 1.0, 32)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 31.0 / dt, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"Algorithm 3 on weighted BA n={ns}, k=32 (numpy FP64, {dt:.2f} s "
+                                          "including the dense pseudo-inverse and inverse)"}
+    G.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.workload == "group":
+        if rank == 0:
+            run_group(args)
+        return
     if args.workload == "rb":
         if rank == 0:
             run_rb(args)

@@ -278,6 +278,25 @@ fc_status fc_farness_from_diag(fc_graph* g, const double* diag, double* farness_
                                void* stream);
 
 /*
+ * Group forest closeness (Sec. 5, Algorithm 3): the greedy group S of k
+ * vertices for group forest farness rho(S) = tr((L*_{-S})^{-1}) (L* the
+ * Laplacian of G*, rows and columns of S removed, u* kept).  The first vertex
+ * minimises Omega_vv (highest individual forest closeness); each further
+ * vertex maximises ||M e_v||^2 / M_vv over V \ S with M = (L*_{-S})^{-1},
+ * followed by the rank-one downdate of M.  Ties go to the smallest id.
+ * Omega = (I + alpha_a L)^{-1} is solved with fc_solve at rel_tol (FP64
+ * residual), then M is kept as a dense FP64 (n+1) x (n+1) matrix on the
+ * device: about 16 (n+1)^2 bytes plus the solver's scratch; FC_ENOMEM when
+ * that exceeds 90% of the free device memory.
+ * Single graphs only (FC_EINVAL for batches); 1 <= k <= n.
+ * S_out: device int32 [k], the chosen vertices in order.  farness_out:
+ * device double [k] (may be NULL), farness_out[i] = rho(S[0..i]).
+ * Synchronises `stream`.
+ */
+fc_status fc_group_closeness(fc_graph* g, int32_t alpha_idx, int32_t k, double rel_tol, int32_t* S_out,
+                             double* farness_out, void* stream);
+
+/*
  * Solve (I + alpha_a L) x_j = b_j for n_rhs right-hand sides by Jacobi-
  * preconditioned CG with FP32 inner iterations and FP64 residual / iterative
  * refinement (the paper's ground truth uses CG at tolerance 1e-9, Sec. 6.1;

@@ -31,9 +31,10 @@ def group_farness(g, alpha: float, S) -> float:
     return float(np.trace(np.linalg.inv(Ls[np.ix_(keep, keep)])))
 
 
-def greedy(g, alpha: float, k: int):
+def greedy(g, alpha: float, k: int, with_gains: bool = False):
     """Algorithm 3.  Returns (S, farness) with S the chosen vertices in order
-    and farness[i] = rho(S[:i+1]) read off the maintained inverse."""
+    and farness[i] = rho(S[:i+1]) read off the maintained inverse; with
+    with_gains, also the gain of every candidate at every step (dicts)."""
     n = g.n
     if not 1 <= k <= n:
         raise ValueError("need 1 <= k <= n")
@@ -45,21 +46,27 @@ def greedy(g, alpha: float, k: int):
     M = np.linalg.inv(Ls[np.ix_(idx, idx)])
     S = [v]
     far = [float(np.trace(M))]
+    all_gains = []
     while len(S) < k:
         best, bj = -np.inf, -1
+        step = {}
         for j, vert in enumerate(idx):
             if vert == n:  # u* is never chosen
                 continue
             col = M[:, j]
             gain = float(col @ col) / float(M[j, j])
+            step[vert] = gain
             if gain > best:
                 best, bj = gain, j
+        all_gains.append(step)
         col = M[:, bj].copy()
         M = M - np.outer(col, col) / col[bj]
         M = np.delete(np.delete(M, bj, axis=0), bj, axis=1)
         S.append(idx[bj])
         del idx[bj]
         far.append(float(np.trace(M)))
+    if with_gains:
+        return S, np.array(far), all_gains
     return S, np.array(far)
 
 

@@ -65,6 +65,7 @@ def lib():
             "fc_rb_accumulate": ([P, I32, P, I64, P, P], ctypes.c_int),
             "fc_rb_diag": ([P, I32, I64, P, P], ctypes.c_int),
             "fc_farness_from_diag": ([P, P, P, P, P], ctypes.c_int),
+            "fc_group_closeness": ([P, I32, I32, D, P, P, P], ctypes.c_int),
             "fc_root_counts": ([P, I32, I64, P, I32, P, P], ctypes.c_int),
             "fc_mlp_param_count": ([], I32),
             "fc_vertex_features": ([P, I32, P, P], ctypes.c_int),
@@ -358,6 +359,17 @@ class Graph:
         _check(lib().fc_farness_from_diag(self._h, _ptr(diag), _ptr(far), _ptr(clo), _stream(stream)),
                "fc_farness_from_diag")
         return far, clo
+
+    def group_closeness(self, k: int, alpha_idx: int = 0, rel_tol: float = 1e-12, stream=None):
+        """fc_group_closeness (Algorithm 3): (S, farness) with S the k chosen
+        vertices in order (int32 CUDA) and farness[i] = rho(S[:i+1]) (FP64
+        CUDA)."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        S = torch.empty(int(k), dtype=torch.int32, device=dev)
+        far = torch.empty(int(k), dtype=torch.float64, device=dev)
+        _check(lib().fc_group_closeness(self._h, int(alpha_idx), int(k), float(rel_tol), _ptr(S), _ptr(far),
+                                        _stream(stream)), "fc_group_closeness")
+        return S, far
 
     # ---- learned control variate ----
     def features(self, alpha_idx: int = 0, stream=None):
