@@ -28,6 +28,30 @@ __device__ __forceinline__ double group_sum(double v) {
   for (int o = RG / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// Block-wide sum of two doubles (warp shuffles, then one warp); the result
+// is valid in thread 0.
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double wa[SV_T / 32], wb[SV_T / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    wa[threadIdx.x >> 5] = a;
+    wb[threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = 0.0;
+    b = 0.0;
+    for (int w = 0; w < SV_T / 32; ++w) {
+      a += wa[w];
+      b += wb[w];
+    }
+  }
+}
+
 __device__ __forceinline__ float group_sumf(float v) {
 #pragma unroll
   for (int o = RG / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -39,44 +63,36 @@ __global__ void k_resid64(int32_t n, const int64_t* __restrict__ rowptr, const i
                           const float* __restrict__ w, const double* __restrict__ dw, double alpha,
                           const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ r,
                           double* __restrict__ prr, double* __restrict__ pbb, int nb) {
-  __shared__ double s1[SV_T], s2[SV_T];
+  // blocks stride over the chunks of ROWS_PER_BLOCK rows; nb = gridDim.x partials per column
   const int j = blockIdx.y;
   const int gl = threadIdx.x % RG;
-  const int64_t v = (int64_t)blockIdx.x * ROWS_PER_BLOCK + threadIdx.x / RG;
   const size_t off = (size_t)j * n;
   double rr = 0.0, bb = 0.0;
-  double acc = 0.0;
-  if (v < n) {
-    for (int64_t e = rowptr[v] + gl; e < rowptr[v + 1]; e += RG) {
-      const double we = w ? (double)w[e] : 1.0;
-      acc += we * x[off + colidx[e]];
+  for (int64_t c = blockIdx.x; c * ROWS_PER_BLOCK < n; c += gridDim.x) {
+    const int64_t v = c * ROWS_PER_BLOCK + threadIdx.x / RG;
+    double acc = 0.0;
+    if (v < n) {
+      for (int64_t e = rowptr[v] + gl; e < rowptr[v + 1]; e += RG) {
+        const double we = w ? (double)w[e] : 1.0;
+        acc += we * x[off + colidx[e]];
+      }
+    }
+    acc = group_sum(acc);
+    if (v < n && gl == 0) {
+      const double ax = x[off + v] * (1.0 + alpha * dw[v]) - alpha * acc;
+      const double rv = b[off + v] - ax;
+      r[off + v] = rv;
+      rr += rv * rv;
+      bb += b[off + v] * b[off + v];
     }
   }
-  acc = group_sum(acc);
-  if (v < n && gl == 0) {
-    const double ax = x[off + v] * (1.0 + alpha * dw[v]) - alpha * acc;
-    const double rv = b[off + v] - ax;
-    r[off + v] = rv;
-    rr = rv * rv;
-    bb = b[off + v] * b[off + v];
-  }
-  s1[threadIdx.x] = rr;
-  s2[threadIdx.x] = bb;
-  __syncthreads();
-  for (int s = SV_T / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      s1[threadIdx.x] += s1[threadIdx.x + s];
-      s2[threadIdx.x] += s2[threadIdx.x + s];
-    }
-    __syncthreads();
-  }
+  block_sum2(rr, bb);
   if (threadIdx.x == 0) {
-    prr[(size_t)j * nb + blockIdx.x] = s1[0];
-    pbb[(size_t)j * nb + blockIdx.x] = s2[0];
+    prr[(size_t)j * nb + blockIdx.x] = rr;
+    pbb[(size_t)j * nb + blockIdx.x] = bb;
   }
 }
 
-// per-column fixed-order sum of nb partials: out[j] = sum_i part[j][i]
 __global__ void k_colsum(const double* __restrict__ part, int nb, double* __restrict__ out) {
   __shared__ double red[SV_T];
   const int j = blockIdx.x;
@@ -104,34 +120,23 @@ struct Inner {
 __global__ void k_inner_init(int32_t n, const double* __restrict__ r64, const float* __restrict__ prec,
                              const double* __restrict__ scal, Inner in, double* __restrict__ prz,
                              double* __restrict__ prr, int nb) {
-  __shared__ double s1[SV_T], s2[SV_T];
   const int j = blockIdx.y;
-  const int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x;
   const size_t off = (size_t)j * n;
+  const double sc = scal[j * 8 + 4];
   double rz = 0.0, rr = 0.0;
-  if (v < n) {
-    const double sc = scal[j * 8 + 4];
+  for (int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x; v < n; v += (int64_t)gridDim.x * SV_T) {
     const float rv = (float)(r64[off + v] * sc);
     const float z = prec ? rv / prec[v] : rv;
     in.r[off + v] = rv;
     in.p[off + v] = z;
     in.d[off + v] = 0.0f;
-    rz = (double)rv * (double)z;
-    rr = (double)rv * (double)rv;
+    rz += (double)rv * (double)z;
+    rr += (double)rv * (double)rv;
   }
-  s1[threadIdx.x] = rz;
-  s2[threadIdx.x] = rr;
-  __syncthreads();
-  for (int s = SV_T / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      s1[threadIdx.x] += s1[threadIdx.x + s];
-      s2[threadIdx.x] += s2[threadIdx.x + s];
-    }
-    __syncthreads();
-  }
+  block_sum2(rz, rr);
   if (threadIdx.x == 0) {
-    prz[(size_t)j * nb + blockIdx.x] = s1[0];
-    prr[(size_t)j * nb + blockIdx.x] = s2[0];
+    prz[(size_t)j * nb + blockIdx.x] = rz;
+    prr[(size_t)j * nb + blockIdx.x] = rr;
   }
 }
 
@@ -139,81 +144,75 @@ __global__ void k_inner_init(int32_t n, const double* __restrict__ r64, const fl
 __global__ void k_spmv_pq(int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                           const float* __restrict__ w, const float* __restrict__ diag32, float alpha, Inner in,
                           double* __restrict__ ppq, int nb) {
-  __shared__ double s1[SV_T];
   const int j = blockIdx.y;
   const int gl = threadIdx.x % RG;
-  const int64_t v = (int64_t)blockIdx.x * ROWS_PER_BLOCK + threadIdx.x / RG;
   const size_t off = (size_t)j * n;
   const float* pj = in.p + off;
-  double pq = 0.0;
-  float acc = 0.0f;
-  if (v < n) {
-    for (int64_t e = rowptr[v] + gl; e < rowptr[v + 1]; e += RG) acc += (w ? w[e] : 1.0f) * pj[colidx[e]];
+  double pq = 0.0, unused = 0.0;
+  for (int64_t c = blockIdx.x; c * ROWS_PER_BLOCK < n; c += gridDim.x) {
+    const int64_t v = c * ROWS_PER_BLOCK + threadIdx.x / RG;
+    float acc = 0.0f;
+    if (v < n) {
+      for (int64_t e = rowptr[v] + gl; e < rowptr[v + 1]; e += RG) acc += (w ? w[e] : 1.0f) * pj[colidx[e]];
+    }
+    acc = group_sumf(acc);
+    if (v < n && gl == 0) {
+      const float pv = pj[v];
+      const float qv = pv * diag32[v] - alpha * acc;
+      in.q[off + v] = qv;
+      pq += (double)pv * (double)qv;
+    }
   }
-  acc = group_sumf(acc);
-  if (v < n && gl == 0) {
-    const float pv = pj[v];
-    const float qv = pv * diag32[v] - alpha * acc;
-    in.q[off + v] = qv;
-    pq = (double)pv * (double)qv;
-  }
-  s1[threadIdx.x] = pq;
-  __syncthreads();
-  for (int s = SV_T / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) s1[threadIdx.x] += s1[threadIdx.x + s];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) ppq[(size_t)j * nb + blockIdx.x] = s1[0];
+  block_sum2(pq, unused);
+  if (threadIdx.x == 0) ppq[(size_t)j * nb + blockIdx.x] = pq;
 }
 
 // d += a p; r -= a q; partial r.z, r.r with z = r / diag
 __global__ void k_inner_update(int32_t n, const float* __restrict__ prec, const double* __restrict__ scal,
                                Inner in, double* __restrict__ prz, double* __restrict__ prr, int nb) {
-  __shared__ double s1[SV_T], s2[SV_T];
   const int j = blockIdx.y;
-  const int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x;
   const size_t off = (size_t)j * n;
+  const double* sc = scal + j * 8;
+  const float a = (sc[5] != 0.0 && sc[1] != 0.0) ? (float)(sc[0] / sc[1]) : 0.0f;
   double rz = 0.0, rr = 0.0;
-  if (v < n) {
-    const double* sc = scal + j * 8;
-    const float a = (sc[5] != 0.0 && sc[1] != 0.0) ? (float)(sc[0] / sc[1]) : 0.0f;
+  for (int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x; v < n; v += (int64_t)gridDim.x * SV_T) {
     in.d[off + v] += a * in.p[off + v];
     const float rv = in.r[off + v] - a * in.q[off + v];
     in.r[off + v] = rv;
     const float z = prec ? rv / prec[v] : rv;
-    rz = (double)rv * (double)z;
-    rr = (double)rv * (double)rv;
+    rz += (double)rv * (double)z;
+    rr += (double)rv * (double)rv;
   }
-  s1[threadIdx.x] = rz;
-  s2[threadIdx.x] = rr;
-  __syncthreads();
-  for (int s = SV_T / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      s1[threadIdx.x] += s1[threadIdx.x + s];
-      s2[threadIdx.x] += s2[threadIdx.x + s];
-    }
-    __syncthreads();
-  }
+  block_sum2(rz, rr);
   if (threadIdx.x == 0) {
-    prz[(size_t)j * nb + blockIdx.x] = s1[0];
-    prr[(size_t)j * nb + blockIdx.x] = s2[0];
+    prz[(size_t)j * nb + blockIdx.x] = rz;
+    prr[(size_t)j * nb + blockIdx.x] = rr;
   }
 }
 
 // p = z + beta p with beta = rz_new / rz
 __global__ void k_inner_p(int32_t n, const float* __restrict__ prec, const double* __restrict__ scal, Inner in) {
   const int j = blockIdx.y;
-  const int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x;
-  if (v >= n) return;
   const size_t off = (size_t)j * n;
   const double* sc = scal + j * 8;
   const float beta = sc[0] != 0.0 ? (float)(sc[2] / sc[0]) : 0.0f;
-  const float z = prec ? in.r[off + v] / prec[v] : in.r[off + v];
-  in.p[off + v] = z + beta * in.p[off + v];
+  for (int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x; v < n; v += (int64_t)gridDim.x * SV_T) {
+    const float z = prec ? in.r[off + v] / prec[v] : in.r[off + v];
+    in.p[off + v] = z + beta * in.p[off + v];
+  }
 }
 
 // scalar bookkeeping after k_inner_update: rz <- rz_new (done after k_inner_p
 // has used both), rr stored
+// scal[j][f + i] = sums[i m + j] for i < cnt: the per-column scalars from
+// the column sums (one launch instead of a strided copy of m 8-byte rows,
+// which costs about a microsecond per row)
+__global__ void k_put_scal(int m, const double* __restrict__ sums, int f, int cnt, double* __restrict__ scal) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < m)
+    for (int i = 0; i < cnt; ++i) scal[j * 8 + f + i] = sums[(size_t)i * m + j];
+}
+
 __global__ void k_scal_shift(int m, double* scal) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < m) scal[j * 8 + 0] = scal[j * 8 + 2];
@@ -223,12 +222,11 @@ __global__ void k_scal_shift(int m, double* scal) {
 __global__ void k_correct(int32_t n, const double* __restrict__ scal, const float* __restrict__ d,
                           double* __restrict__ x) {
   const int j = blockIdx.y;
-  const int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x;
-  if (v >= n) return;
   const double* sc = scal + j * 8;
   if (sc[5] == 0.0) return;
   const size_t off = (size_t)j * n;
-  x[off + v] += (double)d[off + v] / sc[4];
+  for (int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x; v < n; v += (int64_t)gridDim.x * SV_T)
+    x[off + v] += (double)d[off + v] / sc[4];
 }
 
 __global__ void k_diag32(int32_t n, const double* __restrict__ dw, double alpha, float* __restrict__ diag32) {
@@ -299,19 +297,25 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
   const float* prec = jacobi ? diag32 : nullptr;
   k_diag32<<<(n + 255) / 256, 256, 0, st>>>(n, g->dw, alpha, diag32);
   FC_LAUNCHED();
-  const dim3 grid(nb, m);
-  const dim3 gridr(nbr, m);
+  // blocks per column: a few thousand blocks in all, each striding over its
+  // column's chunks (many right-hand sides would otherwise launch millions of
+  // one-chunk blocks); nbx / nbrx partial sums per column
+  const int target = 2048;
+  const int nbx = std::max(1, std::min(nb, target / m));
+  const int nbrx = std::max(1, std::min(nbr, target / m));
+  const dim3 grid(nbx, m);
+  const dim3 gridr(nbrx, m);
   const double inner_tol = 1e-4;
   const int check_every = 8;
   std::vector<double> h_rr(m), h_bb(m), h_scal((size_t)8 * m, 0.0), h_in(m);
   int used = 0;
   fc_status result = FC_ENOCONV;
   for (int outer = 0; outer < 64; ++outer) {
-    k_resid64<<<gridr, SV_T, 0, st>>>(n, g->rowptr, g->colidx, g->w, g->dw, alpha, b, x, r64, pA, pB, nbr);
+    k_resid64<<<gridr, SV_T, 0, st>>>(n, g->rowptr, g->colidx, g->w, g->dw, alpha, b, x, r64, pA, pB, nbrx);
     FC_LAUNCHED();
-    k_colsum<<<m, SV_T, 0, st>>>(pA, nbr, sums);
+    k_colsum<<<m, SV_T, 0, st>>>(pA, nbrx, sums);
     fcx::note_launch();
-    k_colsum<<<m, SV_T, 0, st>>>(pB, nbr, sums + m);
+    k_colsum<<<m, SV_T, 0, st>>>(pB, nbrx, sums + m);
     fcx::note_launch();
     FC_CK(cudaMemcpyAsync(h_rr.data(), sums, m * sizeof(double), cudaMemcpyDeviceToHost, st));
     FC_CK(cudaMemcpyAsync(h_bb.data(), sums + m, m * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -330,11 +334,11 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
     }
     if (used >= max_iter) break;
     FC_CK(cudaMemcpyAsync(scal, h_scal.data(), (size_t)8 * m * sizeof(double), cudaMemcpyHostToDevice, st));
-    k_inner_init<<<grid, SV_T, 0, st>>>(n, r64, prec, scal, in, pA, pB, nb);
+    k_inner_init<<<grid, SV_T, 0, st>>>(n, r64, prec, scal, in, pA, pB, nbx);
     FC_LAUNCHED();
-    k_colsum<<<m, SV_T, 0, st>>>(pA, nb, sums);
+    k_colsum<<<m, SV_T, 0, st>>>(pA, nbx, sums);
     fcx::note_launch();
-    k_colsum<<<m, SV_T, 0, st>>>(pB, nb, sums + m);
+    k_colsum<<<m, SV_T, 0, st>>>(pB, nbx, sums + m);
     fcx::note_launch();
     FC_CK(cudaMemcpyAsync(h_in.data(), sums, m * sizeof(double), cudaMemcpyDeviceToHost, st));
     FC_CK(cudaMemcpyAsync(h_rr.data(), sums + m, m * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -344,23 +348,21 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
     FC_CK(cudaMemcpyAsync(scal, h_scal.data(), (size_t)8 * m * sizeof(double), cudaMemcpyHostToDevice, st));
     int it = 0;
     while (used < max_iter) {
-      k_spmv_pq<<<gridr, SV_T, 0, st>>>(n, g->rowptr, g->colidx, g->w, diag32, (float)alpha, in, pA, nbr);
+      k_spmv_pq<<<gridr, SV_T, 0, st>>>(n, g->rowptr, g->colidx, g->w, diag32, (float)alpha, in, pA, nbrx);
       FC_LAUNCHED();
       // pq -> scal[j*8+1]
-      k_colsum<<<m, SV_T, 0, st>>>(pA, nbr, sums);
+      k_colsum<<<m, SV_T, 0, st>>>(pA, nbrx, sums);
       fcx::note_launch();
-      FC_CK(cudaMemcpy2DAsync(scal + 1, 8 * sizeof(double), sums, sizeof(double), sizeof(double), m,
-                              cudaMemcpyDeviceToDevice, st));
-      k_inner_update<<<grid, SV_T, 0, st>>>(n, prec, scal, in, pA, pB, nb);
+      k_put_scal<<<(m + 127) / 128, 128, 0, st>>>(m, sums, 1, 1, scal);
       FC_LAUNCHED();
-      k_colsum<<<m, SV_T, 0, st>>>(pA, nb, sums);
+      k_inner_update<<<grid, SV_T, 0, st>>>(n, prec, scal, in, pA, pB, nbx);
+      FC_LAUNCHED();
+      k_colsum<<<m, SV_T, 0, st>>>(pA, nbx, sums);
       fcx::note_launch();
-      k_colsum<<<m, SV_T, 0, st>>>(pB, nb, sums + m);
+      k_colsum<<<m, SV_T, 0, st>>>(pB, nbx, sums + m);
       fcx::note_launch();
-      FC_CK(cudaMemcpy2DAsync(scal + 2, 8 * sizeof(double), sums, sizeof(double), sizeof(double), m,
-                              cudaMemcpyDeviceToDevice, st));
-      FC_CK(cudaMemcpy2DAsync(scal + 3, 8 * sizeof(double), sums + m, sizeof(double), sizeof(double), m,
-                              cudaMemcpyDeviceToDevice, st));
+      k_put_scal<<<(m + 127) / 128, 128, 0, st>>>(m, sums, 2, 2, scal);  // scal[2] <- sums[0..m), scal[3] <- sums[m..2m)
+      FC_LAUNCHED();
       k_inner_p<<<grid, SV_T, 0, st>>>(n, prec, scal, in);
       FC_LAUNCHED();
       k_scal_shift<<<(m + 127) / 128, 128, 0, st>>>(m, scal);
