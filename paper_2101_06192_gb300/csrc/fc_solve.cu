@@ -257,6 +257,181 @@ __global__ void k_partial_sum(int64_t len, const double* __restrict__ a, double*
   if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
+
+// ---------------------------------------------------------------------------
+// Many right-hand sides (m >= 32): the solver's vectors interleaved by
+// column, element (v, j) at v m + j.  A warp takes 32 columns of one row, so
+// each neighbour gather of the SpMV loads 32 columns' values from one
+// contiguous segment (128 bytes in FP32) instead of 32 separate sectors.
+// Blocks are 32 x 8 threads (column in the group x row); blockIdx.y is the
+// column group and blocks stride over row chunks of 8; per-column partial
+// sums go to part[j nb + blockIdx.x] as for the column-major kernels.
+// ---------------------------------------------------------------------------
+constexpr int IL_R = 8;
+
+__device__ __forceinline__ void il_sum2(double a, double b, int j, bool on, double* __restrict__ pa,
+                                        double* __restrict__ pb, int nb) {
+  __shared__ double sa[IL_R][33], sb[IL_R][33];
+  sa[threadIdx.y][threadIdx.x] = a;
+  sb[threadIdx.y][threadIdx.x] = b;
+  __syncthreads();
+  if (threadIdx.y == 0 && on) {
+    double ta = 0.0, tb = 0.0;
+    for (int r = 0; r < IL_R; ++r) {
+      ta += sa[r][threadIdx.x];
+      tb += sb[r][threadIdx.x];
+    }
+    pa[(size_t)j * nb + blockIdx.x] = ta;
+    if (pb) pb[(size_t)j * nb + blockIdx.x] = tb;
+  }
+}
+
+// [m][n] (column-major) <-> [n][m] (interleaved) through 32 x 32 tiles
+__global__ void k_il_transpose(int64_t rows, int64_t cols, const double* __restrict__ src, double* __restrict__ dst) {
+  __shared__ double t[32][33];
+  for (int64_t br = blockIdx.y; br * 32 < rows; br += gridDim.y)
+    for (int64_t bc = blockIdx.x; bc * 32 < cols; bc += gridDim.x) {
+      for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t i = br * 32 + r, c = bc * 32 + threadIdx.x;
+        if (i < rows && c < cols) t[r][threadIdx.x] = src[i * cols + c];
+      }
+      __syncthreads();
+      for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t c = bc * 32 + r, i = br * 32 + threadIdx.x;
+        if (i < rows && c < cols) dst[c * rows + i] = t[threadIdx.x][r];
+      }
+      __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_resid64_il(int32_t n, int m, const int64_t* __restrict__ rowptr,
+                                                    const int32_t* __restrict__ colidx, const float* __restrict__ w,
+                                                    const double* __restrict__ dw, double alpha,
+                                                    const double* __restrict__ b, const double* __restrict__ x,
+                                                    double* __restrict__ r, double* __restrict__ prr,
+                                                    double* __restrict__ pbb, int nb) {
+  const int j = blockIdx.y * 32 + threadIdx.x;
+  const bool on = j < m;
+  double rr = 0.0, bb = 0.0;
+  for (int64_t c = blockIdx.x; c * IL_R < n; c += gridDim.x) {
+    const int64_t v = c * IL_R + threadIdx.y;
+    if (v < n && on) {
+      double acc = 0.0;
+      for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e)
+        acc += (w ? (double)w[e] : 1.0) * x[(size_t)colidx[e] * m + j];
+      const size_t i = (size_t)v * m + j;
+      const double rv = b[i] - (x[i] * (1.0 + alpha * dw[v]) - alpha * acc);
+      r[i] = rv;
+      rr += rv * rv;
+      bb += b[i] * b[i];
+    }
+  }
+  il_sum2(rr, bb, j, on, prr, pbb, nb);
+}
+
+__global__ void __launch_bounds__(256) k_inner_init_il(int32_t n, int m, const double* __restrict__ r64,
+                                                       const float* __restrict__ prec, const double* __restrict__ scal,
+                                                       Inner in, double* __restrict__ prz, double* __restrict__ prr,
+                                                       int nb) {
+  const int j = blockIdx.y * 32 + threadIdx.x;
+  const bool on = j < m;
+  const double sc = on ? scal[j * 8 + 4] : 0.0;
+  double rz = 0.0, rr = 0.0;
+  for (int64_t c = blockIdx.x; c * IL_R < n; c += gridDim.x) {
+    const int64_t v = c * IL_R + threadIdx.y;
+    if (v < n && on) {
+      const size_t i = (size_t)v * m + j;
+      const float rv = (float)(r64[i] * sc);
+      const float z = prec ? rv / prec[v] : rv;
+      in.r[i] = rv;
+      in.p[i] = z;
+      in.d[i] = 0.0f;
+      rz += (double)rv * (double)z;
+      rr += (double)rv * (double)rv;
+    }
+  }
+  il_sum2(rz, rr, j, on, prz, prr, nb);
+}
+
+__global__ void __launch_bounds__(256) k_spmv_pq_il(int32_t n, int m, const int64_t* __restrict__ rowptr,
+                                                    const int32_t* __restrict__ colidx, const float* __restrict__ w,
+                                                    const float* __restrict__ diag32, float alpha, Inner in,
+                                                    double* __restrict__ ppq, int nb) {
+  const int j = blockIdx.y * 32 + threadIdx.x;
+  const bool on = j < m;
+  double pq = 0.0;
+  for (int64_t c = blockIdx.x; c * IL_R < n; c += gridDim.x) {
+    const int64_t v = c * IL_R + threadIdx.y;
+    if (v < n && on) {
+      float acc = 0.0f;
+      for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) acc += (w ? w[e] : 1.0f) * in.p[(size_t)colidx[e] * m + j];
+      const size_t i = (size_t)v * m + j;
+      const float pv = in.p[i];
+      const float qv = pv * diag32[v] - alpha * acc;
+      in.q[i] = qv;
+      pq += (double)pv * (double)qv;
+    }
+  }
+  il_sum2(pq, 0.0, j, on, ppq, nullptr, nb);
+}
+
+__global__ void __launch_bounds__(256) k_inner_update_il(int32_t n, int m, const float* __restrict__ prec,
+                                                         const double* __restrict__ scal, Inner in,
+                                                         double* __restrict__ prz, double* __restrict__ prr, int nb) {
+  const int j = blockIdx.y * 32 + threadIdx.x;
+  const bool on = j < m;
+  float a = 0.0f;
+  if (on) {
+    const double* sc = scal + j * 8;
+    a = (sc[5] != 0.0 && sc[1] != 0.0) ? (float)(sc[0] / sc[1]) : 0.0f;
+  }
+  double rz = 0.0, rr = 0.0;
+  for (int64_t c = blockIdx.x; c * IL_R < n; c += gridDim.x) {
+    const int64_t v = c * IL_R + threadIdx.y;
+    if (v < n && on) {
+      const size_t i = (size_t)v * m + j;
+      in.d[i] += a * in.p[i];
+      const float rv = in.r[i] - a * in.q[i];
+      in.r[i] = rv;
+      const float z = prec ? rv / prec[v] : rv;
+      rz += (double)rv * (double)z;
+      rr += (double)rv * (double)rv;
+    }
+  }
+  il_sum2(rz, rr, j, on, prz, prr, nb);
+}
+
+__global__ void __launch_bounds__(256) k_inner_p_il(int32_t n, int m, const float* __restrict__ prec,
+                                                    const double* __restrict__ scal, Inner in) {
+  const int j = blockIdx.y * 32 + threadIdx.x;
+  if (j >= m) return;
+  const double* sc = scal + j * 8;
+  const float beta = sc[0] != 0.0 ? (float)(sc[2] / sc[0]) : 0.0f;
+  for (int64_t c = blockIdx.x; c * IL_R < n; c += gridDim.x) {
+    const int64_t v = c * IL_R + threadIdx.y;
+    if (v < n) {
+      const size_t i = (size_t)v * m + j;
+      const float z = prec ? in.r[i] / prec[v] : in.r[i];
+      in.p[i] = z + beta * in.p[i];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_correct_il(int32_t n, int m, const double* __restrict__ scal,
+                                                    const float* __restrict__ d, double* __restrict__ x) {
+  const int j = blockIdx.y * 32 + threadIdx.x;
+  if (j >= m) return;
+  const double* sc = scal + j * 8;
+  if (sc[5] == 0.0) return;
+  for (int64_t c = blockIdx.x; c * IL_R < n; c += gridDim.x) {
+    const int64_t v = c * IL_R + threadIdx.y;
+    if (v < n) {
+      const size_t i = (size_t)v * m + j;
+      x[i] += (double)d[i] / sc[4];
+    }
+  }
+}
+
 }  // namespace fcx
 
 using namespace fcx;
@@ -274,6 +449,10 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
   const int nb = (n + SV_T - 1) / SV_T;              // blocks of the element-wise kernels
   const int nbr = (n + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK;  // blocks of the row kernels
   const size_t nm = (size_t)n * m;
+  // many right-hand sides: vectors interleaved by column (see k_spmv_pq_il)
+  const bool il = m >= 32;
+  const int gy = (m + 31) / 32;
+  const int gxi = std::max(1, std::min((n + IL_R - 1) / IL_R, 2048 / gy));
   // scratch: FP64 r64, FP32 r/p/q/d, diag32, partials, scalars
   double* r64 = nullptr;
   float* f32 = nullptr;
@@ -281,7 +460,21 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
   double* scal = nullptr;
   FC_CK(cudaMallocAsync((void**)&r64, nm * sizeof(double), st));
   FC_CK(cudaMallocAsync((void**)&f32, (4 * nm + n) * sizeof(float), st));
-  const int npart = std::max(nb, nbr);
+  const int npart = std::max(std::max(nb, nbr), il ? gxi : 1);
+  double* bi = nullptr;  // interleaved copies of b and x
+  double* xi = nullptr;
+  if (il) {
+    FC_CK(cudaMallocAsync((void**)&bi, nm * sizeof(double), st));
+    FC_CK(cudaMallocAsync((void**)&xi, nm * sizeof(double), st));
+    const dim3 tg((unsigned)std::min<int64_t>((n + 31) / 32, 1024), (unsigned)std::min<int64_t>(gy, 1024));
+    k_il_transpose<<<tg, dim3(32, 8), 0, st>>>(m, n, b, bi);
+    FC_LAUNCHED();
+    k_il_transpose<<<tg, dim3(32, 8), 0, st>>>(m, n, x, xi);
+    FC_LAUNCHED();
+  }
+  const double* bv = il ? bi : b;
+  double* xv = il ? xi : x;
+  const dim3 gridi(gxi, gy), blki(32, IL_R);
   FC_CK(cudaMallocAsync((void**)&part, (size_t)2 * m * npart * sizeof(double) + 4 * m * sizeof(double), st));
   FC_CK(cudaMallocAsync((void**)&scal, (size_t)8 * m * sizeof(double), st));
   Inner in;
@@ -311,11 +504,14 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
   int used = 0;
   fc_status result = FC_ENOCONV;
   for (int outer = 0; outer < 64; ++outer) {
-    k_resid64<<<gridr, SV_T, 0, st>>>(n, g->rowptr, g->colidx, g->w, g->dw, alpha, b, x, r64, pA, pB, nbrx);
+    if (il)
+      k_resid64_il<<<gridi, blki, 0, st>>>(n, m, g->rowptr, g->colidx, g->w, g->dw, alpha, bv, xv, r64, pA, pB, gxi);
+    else
+      k_resid64<<<gridr, SV_T, 0, st>>>(n, g->rowptr, g->colidx, g->w, g->dw, alpha, b, x, r64, pA, pB, nbrx);
     FC_LAUNCHED();
-    k_colsum<<<m, SV_T, 0, st>>>(pA, nbrx, sums);
+    k_colsum<<<m, SV_T, 0, st>>>(pA, il ? gxi : nbrx, sums);
     fcx::note_launch();
-    k_colsum<<<m, SV_T, 0, st>>>(pB, nbrx, sums + m);
+    k_colsum<<<m, SV_T, 0, st>>>(pB, il ? gxi : nbrx, sums + m);
     fcx::note_launch();
     FC_CK(cudaMemcpyAsync(h_rr.data(), sums, m * sizeof(double), cudaMemcpyDeviceToHost, st));
     FC_CK(cudaMemcpyAsync(h_bb.data(), sums + m, m * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -334,11 +530,14 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
     }
     if (used >= max_iter) break;
     FC_CK(cudaMemcpyAsync(scal, h_scal.data(), (size_t)8 * m * sizeof(double), cudaMemcpyHostToDevice, st));
-    k_inner_init<<<grid, SV_T, 0, st>>>(n, r64, prec, scal, in, pA, pB, nbx);
+    if (il)
+      k_inner_init_il<<<gridi, blki, 0, st>>>(n, m, r64, prec, scal, in, pA, pB, gxi);
+    else
+      k_inner_init<<<grid, SV_T, 0, st>>>(n, r64, prec, scal, in, pA, pB, nbx);
     FC_LAUNCHED();
-    k_colsum<<<m, SV_T, 0, st>>>(pA, nbx, sums);
+    k_colsum<<<m, SV_T, 0, st>>>(pA, il ? gxi : nbx, sums);
     fcx::note_launch();
-    k_colsum<<<m, SV_T, 0, st>>>(pB, nbx, sums + m);
+    k_colsum<<<m, SV_T, 0, st>>>(pB, il ? gxi : nbx, sums + m);
     fcx::note_launch();
     FC_CK(cudaMemcpyAsync(h_in.data(), sums, m * sizeof(double), cudaMemcpyDeviceToHost, st));
     FC_CK(cudaMemcpyAsync(h_rr.data(), sums + m, m * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -348,22 +547,31 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
     FC_CK(cudaMemcpyAsync(scal, h_scal.data(), (size_t)8 * m * sizeof(double), cudaMemcpyHostToDevice, st));
     int it = 0;
     while (used < max_iter) {
-      k_spmv_pq<<<gridr, SV_T, 0, st>>>(n, g->rowptr, g->colidx, g->w, diag32, (float)alpha, in, pA, nbrx);
+      if (il)
+        k_spmv_pq_il<<<gridi, blki, 0, st>>>(n, m, g->rowptr, g->colidx, g->w, diag32, (float)alpha, in, pA, gxi);
+      else
+        k_spmv_pq<<<gridr, SV_T, 0, st>>>(n, g->rowptr, g->colidx, g->w, diag32, (float)alpha, in, pA, nbrx);
       FC_LAUNCHED();
       // pq -> scal[j*8+1]
-      k_colsum<<<m, SV_T, 0, st>>>(pA, nbrx, sums);
+      k_colsum<<<m, SV_T, 0, st>>>(pA, il ? gxi : nbrx, sums);
       fcx::note_launch();
       k_put_scal<<<(m + 127) / 128, 128, 0, st>>>(m, sums, 1, 1, scal);
       FC_LAUNCHED();
-      k_inner_update<<<grid, SV_T, 0, st>>>(n, prec, scal, in, pA, pB, nbx);
+      if (il)
+        k_inner_update_il<<<gridi, blki, 0, st>>>(n, m, prec, scal, in, pA, pB, gxi);
+      else
+        k_inner_update<<<grid, SV_T, 0, st>>>(n, prec, scal, in, pA, pB, nbx);
       FC_LAUNCHED();
-      k_colsum<<<m, SV_T, 0, st>>>(pA, nbx, sums);
+      k_colsum<<<m, SV_T, 0, st>>>(pA, il ? gxi : nbx, sums);
       fcx::note_launch();
-      k_colsum<<<m, SV_T, 0, st>>>(pB, nbx, sums + m);
+      k_colsum<<<m, SV_T, 0, st>>>(pB, il ? gxi : nbx, sums + m);
       fcx::note_launch();
       k_put_scal<<<(m + 127) / 128, 128, 0, st>>>(m, sums, 2, 2, scal);  // scal[2] <- sums[0..m), scal[3] <- sums[m..2m)
       FC_LAUNCHED();
-      k_inner_p<<<grid, SV_T, 0, st>>>(n, prec, scal, in);
+      if (il)
+        k_inner_p_il<<<gridi, blki, 0, st>>>(n, m, prec, scal, in);
+      else
+        k_inner_p<<<grid, SV_T, 0, st>>>(n, prec, scal, in);
       FC_LAUNCHED();
       k_scal_shift<<<(m + 127) / 128, 128, 0, st>>>(m, scal);
       fcx::note_launch();
@@ -378,8 +586,18 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
         if (conv) break;
       }
     }
-    k_correct<<<grid, SV_T, 0, st>>>(n, scal, in.d, x);
+    if (il)
+      k_correct_il<<<gridi, blki, 0, st>>>(n, m, scal, in.d, xv);
+    else
+      k_correct<<<grid, SV_T, 0, st>>>(n, scal, in.d, x);
     FC_LAUNCHED();
+  }
+  if (il) {
+    const dim3 tg((unsigned)std::min<int64_t>(gy, 1024), (unsigned)std::min<int64_t>((n + 31) / 32, 1024));
+    k_il_transpose<<<tg, dim3(32, 8), 0, st>>>(n, m, xi, x);
+    FC_LAUNCHED();
+    FC_CK(cudaFreeAsync(bi, st));
+    FC_CK(cudaFreeAsync(xi, st));
   }
   FC_CK(cudaFreeAsync(r64, st));
   FC_CK(cudaFreeAsync(f32, st));
