@@ -288,6 +288,7 @@ def run_cv(args):
         return r, a.elapsed_time(b)
 
     results = {}
+    infer_ms = []  # features + MLP forward (fc_vertex_features, fc_mlp_forward)
     for form in ("plain", "cv", "rb"):
         per_seed = []
         for sd in range(args.seeds):
@@ -298,6 +299,7 @@ def run_cv(args):
             gp = None
             if form == "cv":
                 gp, dt = timed(lambda: cvnet.predict(G, params))
+                infer_ms.append(dt)
                 ms += dt
             done = 0
             hit = None
@@ -340,6 +342,12 @@ def run_cv(args):
                                   if results["cv"]["median_ms"] and results["plain"]["median_ms"] else None),
         "trees_plain": results["plain"]["median_trees"], "trees_cv": results["cv"]["median_trees"],
         "rao_blackwell_ms": results["rb"]["median_ms"], "trees_rao_blackwell": results["rb"]["median_trees"],
+        # features + forward pass per vertex: about 1.55 kFLOP FP32 (128 hidden
+        # units x (4 FMAs + bias + relu) + 128 FMAs + the sigmoid); CUDA-core
+        # FP32 peak 152 SMs x 128 lanes x 2 x 2.07 GHz = 80.5 TFLOP/s
+        "cv_inference": {"ms": statistics.median(infer_ms) if infer_ms else None,
+                         "tflops": (1.55e3 * g.n / (statistics.median(infer_ms) / 1000.0) / 1e12) if infer_ms else None,
+                         "fp32_peak_tflops": 80.5, "bytes_per_vertex": 16 + 4},
         "seeds": args.seeds, "judge": {"vertices": int(J.size), "plain_trees": TJ,
                                        "judge_vs_cg_max_abs": judge_vs_cg},
         "train": {"graphs": "R-MAT scale 16-18 x2, plain targets tau=4096", "steps": 500,

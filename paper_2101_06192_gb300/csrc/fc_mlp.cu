@@ -36,22 +36,46 @@ __device__ __forceinline__ double p_of(const uint4& ri) {
   return (double)T * 0x1.0p-53;
 }
 
-// sum over neighbours of their degree, RG lanes per row
-constexpr int FG = 8;
+// Sum over neighbours of their degree.  Each thread takes a run of FT_RUN
+// CSR entries (finding its first row by binary search) and adds the
+// neighbours' degrees into its current row's total, flushing with an integer
+// atomic whenever the row changes: a hub row is shared by many threads
+// instead of being walked by one group (R-MAT hubs have 10^5 entries).  The
+// totals are integers, so the order of the additions does not matter.
+constexpr int FT_RUN = 64;
+__global__ void k_nbr_deg_sum(int32_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
+                              const int32_t* __restrict__ colidx, const int32_t* __restrict__ deg,
+                              unsigned long long* __restrict__ s2) {
+  const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * FT_RUN;
+  if (e0 >= nnz) return;
+  const int64_t e1 = e0 + FT_RUN < nnz ? e0 + FT_RUN : nnz;
+  int32_t lo = 0, hi = n - 1;  // the row v with rowptr[v] <= e0 < rowptr[v + 1]
+  while (lo < hi) {
+    const int32_t mid = lo + (hi - lo + 1) / 2;
+    if (rowptr[mid] <= e0) lo = mid;
+    else hi = mid - 1;
+  }
+  int32_t v = lo;
+  int64_t end = rowptr[v + 1];
+  unsigned long long acc = 0;
+  for (int64_t e = e0; e < e1; ++e) {
+    while (e >= end) {
+      if (acc) atomicAdd(&s2[v], acc);
+      acc = 0;
+      ++v;
+      end = rowptr[v + 1];
+    }
+    acc += (unsigned long long)deg[colidx[e]];
+  }
+  if (acc) atomicAdd(&s2[v], acc);
+}
+
 __global__ void k_features(int32_t n, double alpha_s, const double* __restrict__ alpha_v,
-                           const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                            const int32_t* __restrict__ deg, const double* __restrict__ dw,
-                           float4* __restrict__ X) {
-  const int gl = threadIdx.x % FG;
-  const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / FG;
-  double s2 = 0.0;
-  if (v < n)
-    for (int64_t e = rowptr[v] + gl; e < rowptr[v + 1]; e += FG) s2 += (double)deg[colidx[e]];
-#pragma unroll
-  for (int o = FG / 2; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-  if (v < n && gl == 0) {
+                           const unsigned long long* __restrict__ s2, float4* __restrict__ X) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const double alpha = alpha_v ? alpha_v[v] : alpha_s;
-    X[v] = make_float4((float)log1p((double)deg[v]), (float)log1p(alpha * dw[v]), (float)log1p(s2),
+    X[v] = make_float4((float)log1p((double)deg[v]), (float)log1p(alpha * dw[v]), (float)log1p((double)s2[v]),
                        (float)log(alpha));
   }
 }
@@ -208,11 +232,18 @@ extern "C" fc_status fc_vertex_features(fc_graph* g, int32_t alpha_idx, float* X
     return FC_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  const int64_t threads = (int64_t)g->n * FG;
-  k_features<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g->n, g->alphas[alpha_idx], g->alpha_v,
-                                                                g->rowptr, g->colidx, g->deg, g->dw,
-                                                                (float4*)X);
+  unsigned long long* s2 = nullptr;
+  FC_CK(cudaMallocAsync((void**)&s2, (size_t)g->n * sizeof(unsigned long long), st));
+  FC_CK(cudaMemsetAsync(s2, 0, (size_t)g->n * sizeof(unsigned long long), st));
+  const int64_t runs = (g->nnz + FT_RUN - 1) / FT_RUN;
+  if (runs > 0) {
+    k_nbr_deg_sum<<<(unsigned)((runs + 255) / 256), 256, 0, st>>>(g->n, g->nnz, g->rowptr, g->colidx, g->deg, s2);
+    FC_LAUNCHED();
+  }
+  const unsigned fb = (unsigned)std::min<int64_t>(((int64_t)g->n + 255) / 256, 152 * 16);
+  k_features<<<fb, 256, 0, st>>>(g->n, g->alphas[alpha_idx], g->alpha_v, g->deg, g->dw, s2, (float4*)X);
   FC_LAUNCHED();
+  FC_CK(cudaFreeAsync(s2, st));
   return FC_OK;
 }
 
