@@ -90,12 +90,12 @@ __device__ __forceinline__ float mlp_z(const float* sw, const float4& x) {
   float z = sw[OFF_B2];
 #pragma unroll 8
   for (int j = 0; j < HID; ++j) {
-    const float* w = sw + OFF_W1 + j * NF;
+    const float4 w = *reinterpret_cast<const float4*>(sw + OFF_W1 + j * NF);  // one 16-byte load
     float pre = sw[OFF_B1 + j];
-    pre = fmaf(w[0], x.x, pre);
-    pre = fmaf(w[1], x.y, pre);
-    pre = fmaf(w[2], x.z, pre);
-    pre = fmaf(w[3], x.w, pre);
+    pre = fmaf(w.x, x.x, pre);
+    pre = fmaf(w.y, x.y, pre);
+    pre = fmaf(w.z, x.z, pre);
+    pre = fmaf(w.w, x.w, pre);
     z = fmaf(sw[OFF_W2 + j], fmaxf(pre, 0.0f), z);
   }
   return z;
@@ -104,7 +104,7 @@ __device__ __forceinline__ float mlp_z(const float* sw, const float4& x) {
 __global__ void __launch_bounds__(MLP_T) k_mlp_forward(int32_t n, const float4* __restrict__ X,
                                                        const uint4* __restrict__ rinfo,
                                                        const float* __restrict__ params, float* __restrict__ gout) {
-  __shared__ float sw[NPARAM];
+  __shared__ __align__(16) float sw[NPARAM];
   load_params(params, sw);
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const float z = mlp_z(sw, X[v]);
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(MLP_T) k_mlp_grad(int32_t n, const float4* __r
                                                     const uint4* __restrict__ rinfo, const float* __restrict__ y,
                                                     const float* __restrict__ params, float inv_n,
                                                     float* __restrict__ gpart, double* __restrict__ lpart) {
-  __shared__ float sw[NPARAM];
+  __shared__ __align__(16) float sw[NPARAM];
   __shared__ float4 sx[MLP_T];
   __shared__ float sdz[MLP_T];
   __shared__ double sl[MLP_T];
