@@ -217,7 +217,7 @@ def run_reference(args, g):
     print(json.dumps(line), flush=True)
 
 
-def judge_vertices(g, count: int, seed: int):
+def reference_vertices(g, count: int, seed: int):
     """Judge set: stratified by degree decile among non-isolated vertices, plus
     the 256 lowest-degree non-isolated vertices (largest variance)."""
     import numpy as np
@@ -234,7 +234,7 @@ def judge_vertices(g, count: int, seed: int):
 
 
 def run_cv(args):
-    """Time to max-abs diag(Omega) error <= 0.1 on a judge set, learned control
+    """Time to max-abs diag(Omega) error <= 0.1 on a reference set, learned control
     variate vs plain estimator, R-MAT(scale, 16, a=0.57, b=c=0.19), alpha = 1."""
     import numpy as np
     import torch
@@ -250,19 +250,19 @@ def run_cv(args):
     # automatic because the checkpoint launches range from 16 to 1024 trees
     shape = tune.autotune(G, 64)
     G.set_shape(0, 0, 0, shape.get("regs", 0))
-    J = judge_vertices(g, 4096, 5)
+    J = reference_vertices(g, 4096, 5)
     Jt = torch.from_numpy(J).cuda()
     TJ = 16384
     ref = G.sample(777_000, TJ, tree_offset=10**6, with_C=False)
     dj, _, _ = G.farness(ref["R"], TJ)
     dj = dj[Jt]
-    # spot check of the judge against CG columns (fc_solve) on 16 judge vertices
+    # spot check of the reference against CG columns (fc_solve) on 16 reference vertices
     sub = J[np.linspace(0, J.size - 1, 4).astype(int)]
     B = torch.zeros((sub.size, g.n), dtype=torch.float64, device="cuda")
     B[torch.arange(sub.size), torch.from_numpy(sub).cuda()] = 1.0
     X, _ = G.solve(B, rel_tol=1e-8)
     om_sub = X[torch.arange(sub.size), torch.from_numpy(sub).cuda()]
-    judge_vs_cg = float((dj[torch.from_numpy(np.searchsorted(J, sub)).cuda()] - om_sub).abs().max())
+    ref_vs_cg = float((dj[torch.from_numpy(np.searchsorted(J, sub)).cuda()] - om_sub).abs().max())
     # training on smaller R-MAT graphs, targets from the plain estimator
     tt = time.perf_counter()
     train = []
@@ -348,8 +348,8 @@ def run_cv(args):
         "cv_inference": {"ms": statistics.median(infer_ms) if infer_ms else None,
                          "tflops": (1.55e3 * g.n / (statistics.median(infer_ms) / 1000.0) / 1e12) if infer_ms else None,
                          "fp32_peak_tflops": 80.5, "bytes_per_vertex": 16 + 4},
-        "seeds": args.seeds, "judge": {"vertices": int(J.size), "plain_trees": TJ,
-                                       "judge_vs_cg_max_abs": judge_vs_cg},
+        "seeds": args.seeds, "reference_set": {"vertices": int(J.size), "plain_trees": TJ,
+                                       "reference_vs_cg_max_abs": ref_vs_cg},
         "train": {"graphs": "R-MAT scale 16-18 x2, plain targets tau=4096", "steps": 500,
                   "loss_first_last": [hist[0][1], hist[-1][1]], "seconds": train_s},
         "config": {"workload": f"R-MAT scale {args.rmat_scale} ef 16 (0.57,0.19,0.19), alpha=1",
@@ -455,7 +455,7 @@ def run_batch(args):
         times.append(a.elapsed_time(b))
     lat = G.batch_latency_ms()
     d_plain, _, _ = G.farness(R, tau)
-    # accuracy on the small graphs; judge: diag(Omega) from the library's CG
+    # accuracy on the small graphs; reference: diag(Omega) from the library's CG
     # solve of (I + alpha L) X = I on each graph (independent of the sampler)
     dp, dc = d_plain.cpu().numpy(), d_cv.cpu().numpy()
     small = [i for i, g in enumerate(graphs) if g.n <= 1500][:40]
@@ -781,20 +781,20 @@ def main():
                 "departures_per_launch": deps, "pops_per_launch": pops}
 
     # accuracy of the last step's estimate (untimed): diag(Omega) against CG
-    # columns of the library's solver on degree-stratified judge vertices
+    # columns of the library's solver on degree-stratified reference vertices
     accuracy = None
     if rank == 0 and args.n_log2 == N_LOG2 and not args.no_e2e:
         import math
-        J = judge_vertices(g, 256, 5)
+        J = reference_vertices(g, 256, 5)
         Gj = fc.Graph(rowptr_d, colidx_d, None, [ALPHA])
         B = torch.zeros(J.size, n, dtype=torch.float64, device=dev)
         Jt = torch.from_numpy(J).to(dev)
         B[torch.arange(J.size, device=dev), Jt] = 1.0
         X, _ = Gj.solve(B, rel_tol=1e-10)
-        judge = X[torch.arange(J.size, device=dev), Jt]
+        ref = X[torch.arange(J.size, device=dev), Jt]
         Gj.close()
-        err = (last_diag[0][Jt] - judge).abs()
-        accuracy = {"judge_vertices": int(J.size), "max_abs_err": float(err.max()),
+        err = (last_diag[0][Jt] - ref).abs()
+        accuracy = {"reference_vertices": int(J.size), "max_abs_err": float(err.max()),
                     "mean_abs_err": float(err.mean()),
                     "hoeffding_bound_delta_1e-6": math.sqrt(math.log(2e6) / (2 * tau))}
         del B, X
