@@ -778,7 +778,10 @@ def main():
                 "traffic_over_algorithmic": (traffic / alg_bytes) if traffic else None,
                 "kernel": kname, "launch": launched,
                 "peak_source": peak_kind, "kernel_ms": 1000.0 * samp_s,
-                "departures_per_launch": deps, "pops_per_launch": pops}
+                "departures_per_launch": deps, "pops_per_launch": pops,
+                "steps_per_s": deps / samp_s,
+                # DRAM bytes per walk step, from the committed capture's traffic
+                "dram_bytes_per_departure": (traffic / deps) if traffic else None}
 
     # accuracy of the last step's estimate (untimed): diag(Omega) against CG
     # columns of the library's solver on degree-stratified reference vertices
