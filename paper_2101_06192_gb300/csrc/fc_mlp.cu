@@ -74,9 +74,11 @@ __global__ void k_features(int32_t n, double alpha_s, const double* __restrict__
                            const int32_t* __restrict__ deg, const double* __restrict__ dw,
                            const unsigned long long* __restrict__ s2, float4* __restrict__ X) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    // FP32 logarithms (GB300's FP64 rate made the FP64 ones the cost of the
+    // feature pass); the inputs are rounded to FP32 first
     const double alpha = alpha_v ? alpha_v[v] : alpha_s;
-    X[v] = make_float4((float)log1p((double)deg[v]), (float)log1p(alpha * dw[v]), (float)log1p((double)s2[v]),
-                       (float)log(alpha));
+    X[v] = make_float4(log1pf((float)deg[v]), log1pf((float)(alpha * dw[v])), log1pf((float)s2[v]),
+                       logf((float)alpha));
   }
 }
 
