@@ -331,14 +331,28 @@ static int grid_for(int64_t items, int threads) {
 
 // Locality of the vertex numbering: CSR entries whose endpoints are at most 32
 // ids apart (high for meshes and road networks numbered along their geometry).
-__global__ void k_id_locality(int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                              unsigned long long* count) {
+// Each thread takes a run of 64 entries (its first row by binary search), so
+// the entries are read in order whatever the degrees.
+constexpr int LOC_RUN = 64;
+__global__ void k_id_locality(int32_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
+                              const int32_t* __restrict__ colidx, unsigned long long* count) {
   unsigned long long local = 0;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+  const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * LOC_RUN;
+  if (e0 < nnz) {
+    const int64_t e1 = e0 + LOC_RUN < nnz ? e0 + LOC_RUN : nnz;
+    int32_t lo = 0, hi = n - 1;  // the row v with rowptr[v] <= e0 < rowptr[v + 1]
+    while (lo < hi) {
+      const int32_t mid = lo + (hi - lo + 1) / 2;
+      if (rowptr[mid] <= e0) lo = mid;
+      else hi = mid - 1;
+    }
+    int64_t v = lo, end = rowptr[v + 1];
+    for (int64_t e = e0; e < e1; ++e) {
+      while (e >= end) end = rowptr[++v + 1];
       const int64_t d = (int64_t)colidx[e] - v;
       local += (d >= -32 && d <= 32) ? 1ull : 0ull;
     }
+  }
   for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
   if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
 }
@@ -610,7 +624,8 @@ static fc_status build_impl(int32_t n, int64_t nnz, const int64_t* rowptr, const
   if (nnz > 0) {
     BUILD_CK(cudaMallocAsync((void**)&d_local, sizeof(unsigned long long), st));
     BUILD_CK(cudaMemsetAsync(d_local, 0, sizeof(unsigned long long), st));
-    k_id_locality<<<grid_for(n, 256), 256, 0, st>>>(n, g->rowptr, g->colidx, d_local);
+    k_id_locality<<<(unsigned)(((nnz + LOC_RUN - 1) / LOC_RUN + 255) / 256), 256, 0, st>>>(n, nnz, g->rowptr,
+                                                                                       g->colidx, d_local);
     BUILD_CK((fcx::note_launch(), cudaGetLastError()));
     BUILD_CK(cudaMemcpyAsync(&h_local, d_local, sizeof(h_local), cudaMemcpyDeviceToHost, st));
     BUILD_CK(cudaFreeAsync(d_local, st));
