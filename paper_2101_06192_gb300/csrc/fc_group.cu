@@ -222,9 +222,10 @@ extern "C" fc_status fc_group_closeness(fc_graph* g, int32_t alpha_idx, int32_t 
   int nsm = 0;
   FC_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device));
   // Omega (n^2), M (n1 x ld), the identity block and the solver's scratch
-  // (about 24 bytes per right-hand side and vertex)
+  // (FP64 residual, four FP32 vectors and, for 32 or more right-hand sides,
+  // interleaved copies of b and x: about 40 bytes per right-hand side and vertex)
   const int32_t nb = std::min<int32_t>(n, 4096);
-  const size_t need = (size_t)n * n * 8 + (size_t)n1 * ld * 8 + (size_t)nb * n * (8 + 24);
+  const size_t need = (size_t)n * n * 8 + (size_t)n1 * ld * 8 + (size_t)nb * n * (8 + 40);
   size_t freeb = 0, totb = 0;
   FC_CK(cudaMemGetInfo(&freeb, &totb));
   if (need > freeb / 10 * 9) {
