@@ -101,3 +101,16 @@ def test_grounded_inverse_from_forest_matrix():
         M = np.linalg.inv(Ls[np.ix_(idx, idx)])
         Mi = Om[np.ix_(idx, idx)] - Om[idx, v][:, None] - Om[v, idx][None, :] + Om[v, v]
         np.testing.assert_allclose(Mi, M, rtol=1e-10, atol=1e-12)
+
+
+def test_greedy_guarantee_of_the_corollary():
+    # Sec. 5, Corollary: rho({v0}) - rho(S) >= (1 - k / (e (k - 1))) (rho({v0}) - rho(S~))
+    # for the greedy S of size k and the best S~ of size k (brute force)
+    g = _weighted_er(9, 3, 17)
+    for alpha, k in ((0.6, 3), (2.5, 4)):
+        S, far = group.greedy(g, alpha, k)
+        r0 = group.group_farness(g, alpha, [S[0]])
+        best = min(group.group_farness(g, alpha, T) for T in itertools.combinations(range(9), k))
+        bound = 1.0 - k / (np.e * (k - 1))
+        assert r0 - far[-1] >= bound * (r0 - best) - 1e-12
+        assert far[-1] >= best - 1e-12  # the greedy group is never better than the optimum
