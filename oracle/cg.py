@@ -1,7 +1,7 @@
 """FP64 conjugate-gradient ground truth on I + alpha L (test infrastructure only).
 
 The paper takes its ground truth Omega[v, v] from a CG solver at tolerance 1e-9
-(Sec. 6.1, "Accuracy and Running Time") and checks it against NumPy's pinv.
+(Sec. 6.1, the accuracy measurement) and checks it against NumPy's pinv.
 This module is the same idea written out plainly: textbook CG (Hestenes-Stiefel)
 on the SPD matrix A = I + alpha L with scipy's sparse product as the only
 library step; column e_v of the solution gives Omega[:, v] and its v-th entry
