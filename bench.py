@@ -208,7 +208,10 @@ def run_reference(args, g):
         "metric": "USTs/s", "value": value, "unit": "trees/s", "impl": "reference", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * TAU / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "n": g.n, "m_edges": g.m, "tau": TAU},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if (args.n_log2 == N_LOG2 and args.tau == TAU) else
+                   f"BA n=2^{args.n_log2} m={BA_M} (seed {BA_SEED}) unweighted, alpha={ALPHA:g}, tau={args.tau} trees/step",
+                   "n": g.n, "m_edges": g.m, "tau": args.tau},
         "cpu_baseline": {"value": value, "unit": "trees/s", "cores": cores, "kind": "oracle",
                          "sample": f"{trees_per_core * cores} trees of the workload per step, "
                                    f"{trees_per_core} per core, sequential Wilson per thread"},
