@@ -47,12 +47,14 @@ def parse():
     ap.add_argument("--n-log2", type=int, default=N_LOG2,
                     help="BA size 2^k (profiling cases only; the benchmark is 2^20)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["ba", "cv", "grid", "batch", "rb", "group"], default="ba",
+    ap.add_argument("--workload", choices=["ba", "cv", "grid", "batch", "rb", "group", "roots"], default="ba",
                     help="ba: the benchmark line; cv: time to eps = 0.1, learned control variate vs "
                          "plain (R-MAT scale 22); grid: 2048^2 road-like grid, three alphas in one launch; "
                          "batch: 4096 uneven graphs in one launch; rb: Rao-Blackwellised accumulation of "
                          "32 sampled trees of R-MAT (--rmat-scale); group: greedy group forest closeness "
-                         "(Algorithm 3) on a weighted BA graph of --group-n vertices, --group-k members")
+                         "(Algorithm 3) on a weighted BA graph of --group-n vertices, --group-k members; "
+                         "roots: forest roots and depths of 152 sampled trees of BA 2^20 plus root counts "
+                         "for 64 query vertices (Omega columns)")
     ap.add_argument("--group-n", type=int, default=16384)
     ap.add_argument("--group-k", type=int, default=64)
     ap.add_argument("--graphs", type=int, default=4096)
@@ -621,9 +623,70 @@ def run_group(args):
     print(json.dumps(line), flush=True)
 
 
+def run_roots(args):
+    """Forest roots and depths of sampled trees (fc_tree_roots) and root
+    counts of 64 query vertices (fc_root_counts): columns of Omega from the
+    same trees, on the benchmark graph (BA n = 2^20, m = 8), 152 trees with
+    parents, inputs resident, L2 flushed before each timed call."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2101_06192_gb300 import fc
+    torch.cuda.set_device(0)
+    g = synth.barabasi_albert(1 << N_LOG2, BA_M, BA_SEED)
+    G = fc.Graph.from_csr(g, [ALPHA])
+    T = 152
+    par = G.sample(11, T, want_parents=True)["parents"][0].contiguous()
+    queries = torch.from_numpy(np.linspace(0, g.n - 1, 64).astype(np.int64)).cuda()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        roots, depth = fc.tree_roots(par)
+        fc.root_counts(roots, queries)
+    torch.cuda.synchronize()
+    ms_roots, ms_counts = [], []
+    nvtx_push("timed")
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        roots, depth = fc.tree_roots(par)
+        b.record(stream)
+        fc.root_counts(roots, queries)
+        c.record(stream)
+        torch.cuda.synchronize()
+        ms_roots.append(a.elapsed_time(b))
+        ms_counts.append(b.elapsed_time(c))
+    nvtx_pop()
+    n = g.n
+    t_r = statistics.median(ms_roots) / 1000.0
+    # algorithmic bytes of fc_tree_roots: parents read, roots and depths
+    # written (4 B each per tree and vertex)
+    alg = 12.0 * T * n
+    peaks, peak_kind = load_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    line = {"metric": "tree-vertices/s (forest roots and depths)", "value": T * n / t_r,
+            "unit": "tree-vertices/s", "ms_tree_roots": 1000.0 * t_r, "ms_root_counts_64": statistics.median(ms_counts),
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "i32",
+            "data": "synthetic",
+            "config": {"workload": f"BA n=2^{N_LOG2} m={BA_M}, alpha={ALPHA:g}, {T} trees with parents, 64 queries",
+                       "l2": "flushed before every timed call (512 MB write)"},
+            "roofline": {"bound": "hbm", "achieved": alg / t_r / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / t_r / 1e9 / peak, "traffic": None, "kernel": "k_tree_roots",
+                         "algorithmic_bytes": alg, "peak_source": peak_kind},
+            "max_depth": int(depth.max().item())}
+    G.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.workload == "roots":
+        if rank == 0:
+            run_roots(args)
+        return
     if args.workload == "group":
         if rank == 0:
             run_group(args)
