@@ -624,7 +624,8 @@ def run_group(args):
 
 
 def run_roots(args):
-    """Forest roots and depths of sampled trees (fc_tree_roots) and root
+    """Forest roots and depths of sampled trees (fc_tree_roots: pointer
+    jumping) and root
     counts of 64 query vertices (fc_root_counts): columns of Omega from the
     same trees, on the benchmark graph (BA n = 2^20, m = 8), 152 trees with
     parents, inputs resident, L2 flushed before each timed call."""
@@ -673,7 +674,7 @@ def run_roots(args):
             "config": {"workload": f"BA n=2^{N_LOG2} m={BA_M}, alpha={ALPHA:g}, {T} trees with parents, 64 queries",
                        "l2": "flushed before every timed call (512 MB write)"},
             "roofline": {"bound": "hbm", "achieved": alg / t_r / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": alg / t_r / 1e9 / peak, "traffic": None, "kernel": "k_tree_roots",
+                         "frac": alg / t_r / 1e9 / peak, "traffic": None, "kernel": "k_roots_jump",
                          "algorithmic_bytes": alg, "peak_source": peak_kind},
             "max_depth": int(depth.max().item())}
     G.close()

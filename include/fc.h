@@ -411,10 +411,9 @@ fc_status fc_mlp_adam(float* params, const float* grad, float* m, float* v, int3
  * Tree-path aggregation.  For T sampled trees given as parent arrays
  * (int32 device [T][n], u* = n, as written by fc_sample_usts), computes for
  * every vertex its forest root -- the vertex on its path whose parent is u* --
- * and its depth below that root (0 for roots), by BFS levels from u*: children
- * lists by counting sort, one level at a time, output positions from
- * block-wide warp scans.  roots, depth: int32 device [T][n] (depth may be
- * NULL).  FC_EINVAL if some parent array is not a spanning tree rooted at u*.
+ * and its depth below that root (0 for roots), by pointer jumping over all
+ * trees at once (O(log depth) rounds).  roots, depth: int32 device [T][n]
+ * (depth may be NULL).  FC_EINVAL if some parent array is not a spanning tree rooted at u*.
  * By the matrix-forest theorem (Sec. 2), P(root(v) = u) = Omega[u, v].
  * Allocates temporary device memory.  Synchronises `stream`.
  */

@@ -1,5 +1,5 @@
-// Tree-path aggregation over sampled trees: forest roots and depths by BFS
-// levels from u*, and root-frequency counts.
+// Tree-path aggregation over sampled trees: forest roots and depths, and
+// root-frequency counts.
 //
 // In a spanning tree of G* rooted at u*, removing u* leaves a rooted spanning
 // forest of G whose roots are the children of u*.  By the matrix-forest
@@ -9,143 +9,68 @@
 // pairwise forest distances rho(u, v) = Omega_uu + Omega_vv - 2 Omega_uv
 // (Def. 1).
 //
-// fc_tree_roots: one CTA per tree.  Children lists are built by counting
-// (atomic child counts, a block-wide exclusive scan made of warp scans, a
-// scatter); the BFS then expands one level at a time, each level's output
-// positions again from a block-wide scan of the frontier's child counts.
+// fc_tree_roots: pointer jumping over all trees at once.  Every node holds a
+// 64-bit word {ancestor, distance to it}: a root (parent u*) points at itself
+// at distance 0, any other node at its parent at distance 1.  A round
+// replaces each word {a, d} by {ancestor of a, d + a's distance}; a node
+// pointing at a root no longer changes, so O(log depth) rounds end with every
+// node at its root and depth.  Words are read and written whole, so a node
+// may read a word of this round or the last one.  A parent cycle never
+// reaches a root and is caught by the round limit and the final check.
+// (A first version took one CTA per tree with children lists and BFS levels;
+// its per-tree scratch, touched at random, moved 60x the algorithmic bytes.)
 #include "fc_internal.cuh"
 
 namespace fcx {
 
-constexpr int AG_T = 1024;
+constexpr int AG_T = 256;
 
-// Block-wide exclusive scan of one value per thread (warp shuffles, then a
-// scan of the warp totals).  Returns the exclusive prefix; *total gets the sum.
-__device__ __forceinline__ int32_t block_exscan(int32_t x, int32_t* total, int32_t* wsum) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int32_t s = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int32_t y = __shfl_up_sync(0xffffffffu, s, o);
-    if (lane >= o) s += y;
-  }
-  if (lane == 31) wsum[wid] = s;
-  __syncthreads();
-  if (wid == 0) {
-    int32_t t = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int32_t y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
-    }
-    wsum[lane] = t;
-  }
-  __syncthreads();
-  const int32_t excl = s - x + (wid > 0 ? wsum[wid - 1] : 0);
-  *total = wsum[(blockDim.x >> 5) - 1];
-  __syncthreads();
-  return excl;
+__device__ __forceinline__ unsigned long long rw_pack(int32_t a, int32_t d) {
+  return (unsigned long long)(uint32_t)a | ((unsigned long long)(uint32_t)d << 32);
 }
 
-// scratch per CTA slot: cnt/off [n+1], fill [n], child [n], front [2][n]
-__global__ void __launch_bounds__(AG_T) k_tree_roots(const int32_t* __restrict__ parents, int32_t n, int64_t T,
-                                                     int32_t* __restrict__ roots, int32_t* __restrict__ depth,
-                                                     int32_t* __restrict__ scratch, uint32_t* err) {
-  __shared__ int32_t wsum[32];
-  __shared__ int32_t sh_carry, sh_len;
-  const size_t sn = (size_t)n;
-  int32_t* off = scratch + (size_t)blockIdx.x * (5 * sn + 1);
-  int32_t* fill = off + sn + 1;
-  int32_t* child = fill + sn;
-  int32_t* front0 = child + sn;
-  int32_t* front1 = front0 + sn;
-  for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
-    const int32_t* par = parents + (size_t)t * sn;
-    int32_t* rt = roots + (size_t)t * sn;
-    int32_t* dp = depth ? depth + (size_t)t * sn : nullptr;
-    // child counts
-    for (int32_t v = threadIdx.x; v <= n; v += AG_T) off[v] = 0;
-    for (int32_t v = threadIdx.x; v < n; v += AG_T) fill[v] = 0;
-    __syncthreads();
-    for (int32_t v = threadIdx.x; v < n; v += AG_T) {
-      const int32_t p = par[v];
-      if (p < 0 || p > n || p == v) atomicOr(err, ERR_INVAL);
-      else if (p < n) atomicAdd(&off[p], 1);
+__global__ void k_roots_init(const int32_t* __restrict__ parents, int32_t n, int64_t N,
+                             unsigned long long* __restrict__ jw, uint32_t* err) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = (int32_t)(i % n);
+    const int32_t p = parents[i];
+    if (p < 0 || p > n || p == v) {
+      atomicOr(err, ERR_INVAL);
+      jw[i] = rw_pack(v, 0);
+    } else {
+      jw[i] = p == n ? rw_pack(v, 0) : rw_pack(p, 1);
     }
-    __syncthreads();
-    // exclusive scan of the counts, chunk by chunk with a running carry
-    if (threadIdx.x == 0) sh_carry = 0;
-    __syncthreads();
-    for (int32_t b0 = 0; b0 <= n; b0 += AG_T) {
-      const int32_t v = b0 + threadIdx.x;
-      const int32_t x = v <= n ? off[v] : 0;
-      int32_t tot = 0;
-      const int32_t ex = block_exscan(x, &tot, wsum);
-      if (v <= n) off[v] = sh_carry + ex;
-      __syncthreads();
-      if (threadIdx.x == 0) sh_carry += tot;
-      __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(AG_T) k_roots_jump(int32_t n, int64_t N, unsigned long long* jw,
+                                                     uint32_t* changed) {
+  volatile unsigned long long* jv = jw;
+  bool any = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long w = jv[i];
+    const int32_t a = (int32_t)(uint32_t)w;
+    const int64_t base = i - i % n;
+    const unsigned long long wa = jv[base + a];
+    const int32_t aa = (int32_t)(uint32_t)wa;
+    if (aa != a) {
+      jv[i] = rw_pack(aa, (int32_t)((uint32_t)(w >> 32) + (uint32_t)(wa >> 32)));
+      any = true;
     }
-    // scatter children
-    for (int32_t v = threadIdx.x; v < n; v += AG_T) {
-      const int32_t p = par[v];
-      if (p >= 0 && p < n && p != v) child[off[p] + atomicAdd(&fill[p], 1)] = v;
-    }
-    // level 0: the children of u* are their own roots
-    if (threadIdx.x == 0) sh_len = 0;
-    __syncthreads();
-    for (int32_t b0 = 0; b0 < n; b0 += AG_T) {
-      const int32_t v = b0 + threadIdx.x;
-      const int32_t is_root = (v < n && par[v] == n) ? 1 : 0;
-      int32_t tot = 0;
-      const int32_t ex = block_exscan(is_root, &tot, wsum);
-      if (is_root) {
-        front0[sh_len + ex] = v;
-        rt[v] = v;
-        if (dp) dp[v] = 0;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) sh_len += tot;
-      __syncthreads();
-    }
-    int32_t len = sh_len;
-    int32_t* cur = front0;
-    int32_t* nxt = front1;
-    int32_t level = 0, seen = len;
-    while (len > 0) {
-      ++level;
-      if (threadIdx.x == 0) sh_len = 0;
-      __syncthreads();
-      for (int32_t b0 = 0; b0 < len; b0 += AG_T) {
-        const int32_t i = b0 + threadIdx.x;
-        int32_t f = -1, cnt = 0, c0 = 0;
-        if (i < len) {
-          f = cur[i];
-          c0 = off[f];
-          cnt = off[f + 1] - c0;
-        }
-        int32_t tot = 0;
-        const int32_t ex = block_exscan(cnt, &tot, wsum);
-        const int32_t base = sh_len;
-        for (int32_t j = 0; j < cnt; ++j) {
-          const int32_t c = child[c0 + j];
-          nxt[base + ex + j] = c;
-          rt[c] = rt[f];
-          if (dp) dp[c] = level;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) sh_len += tot;
-        __syncthreads();
-      }
-      len = sh_len;
-      seen += len;
-      int32_t* tmp = cur;
-      cur = nxt;
-      nxt = tmp;
-      if (level > n) break;
-    }
-    if (threadIdx.x == 0 && seen != n) atomicOr(err, ERR_INVAL);  // not a tree rooted at u*
-    __syncthreads();
+  }
+  if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(changed, 1u);
+}
+
+__global__ void k_roots_out(const int32_t* __restrict__ parents, int32_t n, int64_t N,
+                            const unsigned long long* __restrict__ jw, int32_t* __restrict__ roots,
+                            int32_t* __restrict__ depth, uint32_t* err) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long w = jw[i];
+    const int32_t r = (int32_t)(uint32_t)w;
+    const int64_t base = i - i % n;
+    if (r < 0 || r >= n || parents[base + r] != n) atomicOr(err, ERR_INVAL);  // not a tree rooted at u*
+    roots[i] = r;
+    if (depth) depth[i] = (int32_t)(w >> 32);
   }
 }
 
@@ -186,20 +111,34 @@ extern "C" fc_status fc_tree_roots(const int32_t* parents, int32_t n, int64_t T,
   int nsm = 0, dev = 0;
   FC_CK(cudaGetDevice(&dev));
   FC_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const int64_t grid = std::min<int64_t>(T, (int64_t)nsm * 2);
-  int32_t* scratch = nullptr;
-  uint32_t* err = nullptr;
-  FC_CK(cudaMallocAsync((void**)&scratch, (size_t)grid * (5 * (size_t)n + 1) * sizeof(int32_t), st));
-  FC_CK(cudaMallocAsync((void**)&err, sizeof(uint32_t), st));
-  FC_CK(cudaMemsetAsync(err, 0, sizeof(uint32_t), st));
-  k_tree_roots<<<(unsigned)grid, AG_T, 0, st>>>(parents, n, T, roots, depth, scratch, err);
+  const int64_t N = T * (int64_t)n;
+  const unsigned blocks = (unsigned)std::min<int64_t>((N + AG_T - 1) / AG_T, (int64_t)nsm * 16);
+  unsigned long long* jw = nullptr;
+  uint32_t* flags = nullptr;  // [0] error, [1] changed in this round
+  FC_CK(cudaMallocAsync((void**)&jw, (size_t)N * sizeof(unsigned long long), st));
+  FC_CK(cudaMallocAsync((void**)&flags, 2 * sizeof(uint32_t), st));
+  FC_CK(cudaMemsetAsync(flags, 0, 2 * sizeof(uint32_t), st));
+  k_roots_init<<<blocks, AG_T, 0, st>>>(parents, n, N, jw, flags);
   FC_LAUNCHED();
-  uint32_t herr = 0;
-  FC_CK(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-  FC_CK(cudaFreeAsync(scratch, st));
-  FC_CK(cudaFreeAsync(err, st));
+  uint32_t h[2] = {0u, 1u};
+  int round = 0;
+  // depth < n < 2^31 needs at most 32 rounds; more means a parent cycle
+  for (; round < 40 && h[0] == 0u && h[1] != 0u; ++round) {
+    FC_CK(cudaMemsetAsync(flags + 1, 0, sizeof(uint32_t), st));
+    k_roots_jump<<<blocks, AG_T, 0, st>>>(n, N, jw, flags + 1);
+    FC_LAUNCHED();
+    FC_CK(cudaMemcpyAsync(h, flags, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    FC_CK(cudaStreamSynchronize(st));
+  }
+  if (h[0] == 0u) {
+    k_roots_out<<<blocks, AG_T, 0, st>>>(parents, n, N, jw, roots, depth, flags);
+    FC_LAUNCHED();
+    FC_CK(cudaMemcpyAsync(h, flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  }
+  FC_CK(cudaFreeAsync(jw, st));
+  FC_CK(cudaFreeAsync(flags, st));
   FC_CK(cudaStreamSynchronize(st));
-  if (herr) {
+  if (h[0] != 0u || h[1] != 0u) {
     set_error("fc_tree_roots: parents do not form spanning trees rooted at u* = n");
     return FC_EINVAL;
   }
