@@ -44,3 +44,15 @@ def test_null_graph_arguments_rejected_without_gpu():
     assert L.fc_sample_usts(None, 1, 1, 0, None, None, None, 0, None, None) == fc.FC_EINVAL
     assert L.fc_set_sampler_shape(None, 32, 0, 0, 0) == fc.FC_EINVAL
     L.fc_destroy(None)
+
+
+def test_null_arguments_of_the_next_rows_rejected_without_gpu():
+    # Rao-Blackwellised accumulation, tree roots, root counts and group
+    # closeness check their arguments before touching the device
+    L = fc.lib()
+    assert L.fc_rb_accumulate(None, 0, None, 1, None, None) == fc.FC_EINVAL
+    assert L.fc_rb_diag(None, 10, 1, None, None) == fc.FC_EINVAL
+    assert L.fc_tree_roots(None, 10, 1, None, None, None) == fc.FC_EINVAL
+    assert L.fc_root_counts(None, 10, 1, None, 1, None, None) == fc.FC_EINVAL
+    assert L.fc_group_closeness(None, 0, 1, 1e-12, None, None, None) == fc.FC_EINVAL
+    assert L.fc_farness_from_diag(None, None, None, None, None) == fc.FC_EINVAL
