@@ -192,6 +192,17 @@ def cpu_trees_per_s(g, trees_per_core: int = 4):
     return total / dt, cores, total, dt
 
 
+def cpu_single_thread(g, trees: int = 2):
+    """The oracle's sequential sampler on one host thread: (trees/s, walk
+    steps/s) from its own step counters."""
+    from oracle import native
+    native.build()
+    t0 = time.perf_counter()
+    out = native.wilson(g, ALPHA, 7, trees, 10**7, 0, None, False, False, True)
+    dt = time.perf_counter() - t0
+    return trees / dt, float(out["steps"].sum()) / dt
+
+
 def run_reference(args, g):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -206,9 +217,11 @@ def run_reference(args, g):
         if i >= args.warmup:
             vals.append(rate)
     value = statistics.median(vals)
+    st_trees, st_steps = cpu_single_thread(g)
+    single = {"trees_per_s": st_trees, "walk_steps_per_s": st_steps, "trees": 2}
     line = {
         "metric": "USTs/s", "value": value, "unit": "trees/s", "impl": "reference", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * TAU / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * args.tau / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD if (args.n_log2 == N_LOG2 and args.tau == TAU) else
@@ -216,14 +229,15 @@ def run_reference(args, g):
                    "n": g.n, "m_edges": g.m, "tau": args.tau},
         "cpu_baseline": {"value": value, "unit": "trees/s", "cores": cores, "kind": "oracle",
                          "sample": f"{trees_per_core * cores} trees of the workload per step, "
-                                   f"{trees_per_core} per core, sequential Wilson per thread"},
+                                   f"{trees_per_core} per core, sequential Wilson per thread",
+                         "single_thread": single},
         "e2e": {"value": value, "unit": "trees/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def reference_vertices(g, count: int, seed: int):
-    """Judge set: stratified by degree decile among non-isolated vertices, plus
+    """Reference set: stratified by degree decile among non-isolated vertices, plus
     the 256 lowest-degree non-isolated vertices (largest variance)."""
     import numpy as np
     rng = np.random.default_rng(seed)
@@ -872,9 +886,11 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, total, dt = cpu_trees_per_s(g, trees_per_core=4)
+        st_trees, st_steps = cpu_single_thread(g)
         cpu = {"value": rate, "unit": "trees/s", "cores": cores, "kind": "oracle",
                "sample": f"{total} trees of the workload ({dt:.1f} s wall), 4 per host core, "
-                         f"sequential Wilson (Algorithm 2) per thread"}
+                         f"sequential Wilson (Algorithm 2) per thread",
+               "single_thread": {"trees_per_s": st_trees, "walk_steps_per_s": st_steps, "trees": 2}}
 
     if rank == 0:
         line = {
