@@ -81,3 +81,39 @@ def omega_forests(n: int, edges, alpha: Fraction):
                 x = par[x]
             num[x][v] += wt
     return [[x / total for x in row] for row in num], total
+
+
+def _inverse(M):
+    """Exact inverse of a nonsingular Fraction matrix by Gauss-Jordan."""
+    k = len(M)
+    A = [row[:] + [Fraction(int(i == j)) for j in range(k)] for i, row in enumerate(M)]
+    for col in range(k):
+        piv = next(r for r in range(col, k) if A[r][col] != 0)
+        A[col], A[piv] = A[piv], A[col]
+        pv = A[col][col]
+        A[col] = [x / pv for x in A[col]]
+        for r in range(k):
+            if r != col and A[r][col] != 0:
+                f = A[r][col]
+                A[r] = [a - f * b for a, b in zip(A[r], A[col])]
+    return [row[k:] for row in A]
+
+
+def group_farness(n: int, edges, alpha: Fraction, S):
+    """rho(S) = tr((L*_{-S})^{-1}) (Sec. 5) exactly: L* is the Laplacian of
+    G* (edges of G scaled by alpha, every vertex joined to u* = n by weight 1)
+    with the rows and columns of S removed."""
+    L = [[Fraction(0)] * (n + 1) for _ in range(n + 1)]
+    for u, v, w in edges:
+        L[u][u] += alpha * w
+        L[v][v] += alpha * w
+        L[u][v] -= alpha * w
+        L[v][u] -= alpha * w
+    for v in range(n):
+        L[v][v] += 1
+        L[n][n] += 1
+        L[v][n] -= 1
+        L[n][v] -= 1
+    keep = [i for i in range(n + 1) if i not in set(S)]
+    inv = _inverse([[L[i][j] for j in keep] for i in keep])
+    return sum(inv[i][i] for i in range(len(keep)))

@@ -114,3 +114,27 @@ def test_greedy_guarantee_of_the_corollary():
         bound = 1.0 - k / (np.e * (k - 1))
         assert r0 - far[-1] >= bound * (r0 - best) - 1e-12
         assert far[-1] >= best - 1e-12  # the greedy group is never better than the optimum
+
+
+def test_against_exact_rationals():
+    # tests/golden/group_exact.json: rho(S) for all S of size 1 and 2 and the
+    # greedy sequence, in exact rational arithmetic (weights exact in FP32)
+    import json
+    import os
+    from fractions import Fraction
+    path = os.path.join(os.path.dirname(__file__), "golden", "group_exact.json")
+    with open(path) as f:
+        cases = json.load(f)
+    for c in cases:
+        n = c["n"]
+        u = np.array([e[0] for e in c["edges"]])
+        v = np.array([e[1] for e in c["edges"]])
+        w = np.array([float(Fraction(e[2])) for e in c["edges"]], dtype=np.float32)
+        g = synth.from_edges(n, u, v, w)
+        alpha = float(Fraction(c["alpha"]))
+        for key, val in c["rho"].items():
+            S = [int(x) for x in key.split(",")]
+            assert group.group_farness(g, alpha, S) == pytest.approx(float(Fraction(val)), rel=1e-12)
+        S, far = group.greedy(g, alpha, c["k"])
+        assert S == c["greedy"]
+        np.testing.assert_allclose(far, [float(Fraction(x)) for x in c["greedy_farness"]], rtol=1e-12)
