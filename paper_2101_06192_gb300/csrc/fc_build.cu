@@ -12,6 +12,12 @@
 
 namespace fcx {
 
+// Record msg as the last error and return FC_EINVAL.
+static inline fc_status invalid(const char* msg) {
+  set_error(msg);
+  return FC_EINVAL;
+}
+
 static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -447,7 +453,7 @@ extern "C" fc_status fc_release_scratch(void) {
 static fc_status build_impl(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
                             const float* w, const double* alphas, int32_t n_alpha, uint32_t flags, void* stream,
                             fc_graph** out, int32_t G, const int64_t* voff_h, const double* galpha_h) {
-  if (out == nullptr) return FC_EINVAL;
+  if (out == nullptr) return fcx::invalid("fc_build_augmented / fc_build_batch: null output pointer");
   *out = nullptr;
   if (n < 1 || n >= (1 << 30) || nnz < 0 || nnz >= (int64_t(1) << 32) || n_alpha < 1 || n_alpha > 64 ||
       rowptr == nullptr || (nnz > 0 && colidx == nullptr) || alphas == nullptr ||
@@ -656,7 +662,7 @@ extern "C" fc_status fc_build_augmented(int32_t n, int64_t nnz, const int64_t* r
 extern "C" fc_status fc_build_batch(int32_t num_graphs, const int64_t* vertex_offsets, int64_t nnz,
                                     const int64_t* rowptr, const int32_t* colidx, const float* w,
                                     const double* graph_alphas, uint32_t flags, void* stream, fc_graph** out) {
-  if (out == nullptr) return FC_EINVAL;
+  if (out == nullptr) return fcx::invalid("fc_build_batch: bad argument");
   *out = nullptr;
   if (num_graphs < 1 || vertex_offsets == nullptr || graph_alphas == nullptr || vertex_offsets[0] != 0) {
     set_error("fc_build_batch: bad argument");
@@ -680,7 +686,7 @@ extern "C" fc_status fc_build_batch(int32_t num_graphs, const int64_t* vertex_of
 
 extern "C" fc_status fc_graph_info(const fc_graph* g, int32_t* n, int64_t* nnz, int32_t* n_alpha,
                                    int32_t* weighted) {
-  if (g == nullptr) return FC_EINVAL;
+  if (g == nullptr) return fcx::invalid("fc_graph_info: bad argument");
   if (n) *n = g->n;
   if (nnz) *nnz = g->nnz;
   if (n_alpha) *n_alpha = g->n_alpha;
@@ -693,7 +699,7 @@ extern "C" fc_status fc_set_sampler_shape(fc_graph* g, int32_t walkers_per_tree,
   if (g == nullptr || walkers_per_tree < 0 || walkers_per_tree > 1024 || (walkers_per_tree % 32) != 0 ||
       max_trees_resident < 0 || smem < 0 || smem > 2 ||
       !(regs == 0 || regs == 32 || regs == 40 || regs == 48 || regs == 64))
-    return FC_EINVAL;
+    return fcx::invalid("fc_set_sampler_shape: bad argument");
   g->walkers = walkers_per_tree;
   g->max_trees = max_trees_resident;
   g->smem_mode = smem;
@@ -702,7 +708,7 @@ extern "C" fc_status fc_set_sampler_shape(fc_graph* g, int32_t walkers_per_tree,
 }
 
 extern "C" fc_status fc_set_start_order(fc_graph* g, int32_t order) {
-  if (g == nullptr || order < 0 || order > 4) return FC_EINVAL;
+  if (g == nullptr || order < 0 || order > 4) return fcx::invalid("fc_set_start_order: bad argument");
   g->order_auto = order == 4;
   g->order_desc = order == 4 ? 0 : (order & 1);
   g->order_id = order == 4 ? 0 : (order >> 1);
@@ -710,7 +716,7 @@ extern "C" fc_status fc_set_start_order(fc_graph* g, int32_t order) {
 }
 
 extern "C" fc_status fc_set_sampler_kernel(fc_graph* g, int32_t kernel) {
-  if (g == nullptr || kernel < 0 || kernel > 2) return FC_EINVAL;
+  if (g == nullptr || kernel < 0 || kernel > 2) return fcx::invalid("fc_set_sampler_kernel: bad argument");
   if (kernel == 2 && g->edges == nullptr) {
     set_error("fc_set_sampler_kernel: edge records exist only for graphs with edges");
     return FC_EINVAL;
@@ -724,7 +730,7 @@ extern "C" int32_t fc_sampler_last_kernel(const fc_graph* g) { return g ? g->las
 extern "C" fc_status fc_set_sampler_cluster(fc_graph* g, int32_t ctas_per_tree) {
   if (g == nullptr || !(ctas_per_tree == 0 || ctas_per_tree == 1 || ctas_per_tree == 2 || ctas_per_tree == 4 ||
                         ctas_per_tree == 8))
-    return FC_EINVAL;
+    return fcx::invalid("fc_set_sampler_cluster: bad argument");
   g->cluster = ctas_per_tree;
   return FC_OK;
 }
@@ -732,20 +738,20 @@ extern "C" fc_status fc_set_sampler_cluster(fc_graph* g, int32_t ctas_per_tree) 
 extern "C" int32_t fc_sampler_last_cluster(const fc_graph* g) { return g ? g->last_cluster : -1; }
 
 extern "C" fc_status fc_set_sampler_bitmap(fc_graph* g, int32_t mode) {
-  if (g == nullptr || mode < 0 || mode > 3) return FC_EINVAL;
+  if (g == nullptr || mode < 0 || mode > 3) return fcx::invalid("fc_set_sampler_bitmap: bad argument");
   g->bitmap_mode = mode;
   return FC_OK;
 }
 
 extern "C" fc_status fc_set_sampler_pops(fc_graph* g, int32_t mode) {
-  if (g == nullptr || mode < 0 || mode > 2) return FC_EINVAL;
+  if (g == nullptr || mode < 0 || mode > 2) return fcx::invalid("fc_set_sampler_pops: bad argument");
   g->pops_mode = mode;
   return FC_OK;
 }
 
 extern "C" fc_status fc_sampler_last_shape(const fc_graph* g, int32_t* walkers_per_tree, int32_t* regs,
                                            int32_t* ctas) {
-  if (g == nullptr) return FC_EINVAL;
+  if (g == nullptr) return fcx::invalid("fc_sampler_last_shape: bad argument");
   if (walkers_per_tree) *walkers_per_tree = g->last_W;
   if (regs) *regs = g->last_regs;
   if (ctas) *ctas = g->last_grid;

@@ -9,6 +9,12 @@
 
 namespace fcx {
 
+// Record msg as the last error and return FC_EINVAL.
+static inline fc_status invalid(const char* msg) {
+  set_error(msg);
+  return FC_EINVAL;
+}
+
 constexpr int RED_THREADS = 256;
 
 // p_v = T_v / 2^53 (exact: T_v <= 2^53)
@@ -274,7 +280,8 @@ extern "C" fc_status fc_farness_from_diag(fc_graph* g, const double* diag, doubl
 }
 
 extern "C" fc_status fc_p_root(fc_graph* g, int32_t alpha_idx, double* p_out, void* stream) {
-  if (g == nullptr || p_out == nullptr || alpha_idx < 0 || alpha_idx >= g->n_alpha) return FC_EINVAL;
+  if (g == nullptr || p_out == nullptr || alpha_idx < 0 || alpha_idx >= g->n_alpha)
+    return fcx::invalid("fc_p_root: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
   k_p_root<<<(unsigned)((g->n + 255) / 256), 256, 0, st>>>(g->n, g->rowinfo + (size_t)alpha_idx * g->n, p_out);
   FC_LAUNCHED();

@@ -34,6 +34,12 @@
 
 namespace fcx {
 
+// Record msg as the last error and return FC_EINVAL.
+static inline fc_status invalid(const char* msg) {
+  set_error(msg);
+  return FC_EINVAL;
+}
+
 enum { P_IDLE = 0, P_CHECK, P_CLAIM, P_CLAIM2, P_EDGE, P_NEXT, P_POP, P_RETRACE, P_RELEASE, P_WAIT,
        P_DONE };
 constexpr uint32_t NO_START = 0xffffffffu;
@@ -591,7 +597,7 @@ extern "C" fc_status fc_sample_usts_async(fc_graph* g, uint64_t seed, int64_t ta
 }
 
 extern "C" fc_status fc_sampler_check(fc_graph* g, void* stream) {
-  if (g == nullptr) return FC_EINVAL;
+  if (g == nullptr) return fcx::invalid("fc_sampler_check: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
   uint32_t herr = 0;
   FC_CK(cudaMemcpyAsync(&herr, g->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -825,7 +831,7 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
 // trees) and departures (walk steps actually executed, including steps redone
 // after a released path).  Host pointers; either may be NULL.  Synchronous.
 extern "C" fc_status fc_sampler_stats(fc_graph* g, uint64_t* pops, uint64_t* departures) {
-  if (g == nullptr) return FC_EINVAL;
+  if (g == nullptr) return fcx::invalid("fc_sampler_stats: bad argument");
   unsigned long long h[2] = {0, 0};
   FC_CK(cudaMemcpy(h, g->d_stats, sizeof(h), cudaMemcpyDeviceToHost));
   if (pops) *pops = h[0];
@@ -834,7 +840,7 @@ extern "C" fc_status fc_sampler_stats(fc_graph* g, uint64_t* pops, uint64_t* dep
 }
 
 extern "C" fc_status fc_sampler_counters(fc_graph* g, uint64_t* out, int32_t count) {
-  if (g == nullptr || out == nullptr || count < 0) return FC_EINVAL;
+  if (g == nullptr || out == nullptr || count < 0) return fcx::invalid("fc_sampler_counters: bad argument");
   unsigned long long h[N_CNT] = {};
   FC_CK(cudaMemcpy(h, g->d_stats + 2, sizeof(h), cudaMemcpyDeviceToHost));
   for (int i = 0; i < count && i < N_CNT; ++i) out[i] = h[i];
