@@ -54,3 +54,31 @@ def test_two_rank_tree_sharding_matches_single_run(tmp_path):
     np.testing.assert_array_equal(got["R"], ref["R"].astype(np.int64))
     np.testing.assert_array_equal(got["C"], ref["C"].astype(np.int64))
     assert got["tmax"][0] == 2.0
+
+
+def _rb_worker(rank, world, port, out_path):
+    # Rao-Blackwellised totals are integers (fixed point), so ranks holding
+    # disjoint tree ranges sum them exactly, in any order
+    from oracle import rb
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    g = synth.barabasi_albert(300, 3, 9)
+    share = 12 // world
+    o = native.wilson(g, 0.7, seed=33, tau=share, tree_offset=rank * share, want_parents=True)
+    acc = torch.from_numpy(rb.accumulate(g, 0.7, o["parents"]).astype(np.int64))
+    dist.all_reduce(acc, op=dist.ReduceOp.SUM)
+    if rank == 0:
+        np.save(out_path, acc.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_rao_blackwell_totals_match_single_run(tmp_path):
+    from oracle import rb
+    out = str(tmp_path / "acc.npy")
+    mp.start_processes(_rb_worker, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+    g = synth.barabasi_albert(300, 3, 9)
+    o = native.wilson(g, 0.7, seed=33, tau=12, want_parents=True)
+    ref = rb.accumulate(g, 0.7, o["parents"]).astype(np.int64)
+    np.testing.assert_array_equal(np.load(out), ref)
