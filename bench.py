@@ -10,12 +10,17 @@ Def. 2) and the top-100 ranking.
 
 Workload: Barabasi-Albert n = 2^20, m = 8 (seed clique K_9, seed 2),
 unweighted, alpha = 1, tau = 1024 trees per step (synthetic stand-in for the
-paper's complex networks).  Metric: USTs/s (trees per second, whole job).
+paper's complex networks).  Metric: USTs/s (trees per second, whole job).  The
+default line also carries "time_to_eps": time to max-abs diag(Omega) error 0.1
+on R-MAT scale 22 (edge factor 16, a = 0.57, b = c = 0.19), learned control
+variate vs the plain estimator and the ablations (untrained network, g = p_v)
+and the Rao-Blackwellised estimator, medians over 5 seeds.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun (N > 1) each rank samples its own 1024 trees (tree_offset =
-rank * 1024; no data-path collective, weak scaling); rank 0 prints one JSON line.
+Under torchrun (N > 1) each rank samples its own 1024 trees of a N * 1024-tree
+run (tree_offset = rank * 1024, weak scaling) and the ranks sum R and C with one
+all-reduce before the combination; rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -47,6 +52,9 @@ def parse():
     ap.add_argument("--n-log2", type=int, default=N_LOG2,
                     help="BA size 2^k (profiling cases only; the benchmark is 2^20)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tte", action="store_true",
+                    help="leave out the time-to-eps study (R-MAT 22, learned control variate vs plain) that the "
+                         "default run appends to its line")
     ap.add_argument("--workload", choices=["ba", "cv", "grid", "batch", "rb", "group", "roots"], default="ba",
                     help="ba: the benchmark line; cv: time to eps = 0.1, learned control variate vs "
                          "plain (R-MAT scale 22); grid: 2048^2 road-like grid, three alphas in one launch; "
@@ -117,6 +125,26 @@ def load_peaks():
             return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# Algorithmic bytes of the sampler: per walk step (departure) the row info 8 B,
+# the selected CSR entry 4 B and the state word read and written 8 B (20 B),
+# weighted rows one FP64 slot threshold more (28 B); per vertex and tree one
+# retrace read and write of the state word (8 B).
+ALG_BYTES_PER_STEP, ALG_BYTES_PER_STEP_WEIGHTED, ALG_BYTES_PER_VERTEX_TREE = 20.0, 28.0, 8.0
+
+
+def algorithmic_bytes(departures, n, trees, weighted=False):
+    per_step = ALG_BYTES_PER_STEP_WEIGHTED if weighted else ALG_BYTES_PER_STEP
+    return departures * per_step + ALG_BYTES_PER_VERTEX_TREE * n * trees
+
+
+def layout_bytes(departures, pops, n, trees, u_edges):
+    """Bytes the edge-record kernel's own layout touches: 40 B per departure
+    (row info 16, CSR target 4, state read and write 16, next pointer 4), 20 B
+    per pop, 20 B per vertex and tree (state clear 16, start order 4), 8 B per
+    u*-edge count."""
+    return departures * 40 + pops * 20 + trees * n * (16 + 4) + u_edges * 8
 
 
 class ClockSampler:
@@ -203,33 +231,46 @@ def cpu_single_thread(g, trees: int = 2):
     return trees / dt, float(out["steps"].sum()) / dt
 
 
+def bench_config(args, g, world: int) -> dict:
+    """The workload description both arms print (identical dicts)."""
+    full = args.n_log2 == N_LOG2 and args.tau == TAU
+    return {"workload": WORKLOAD if full else
+            f"BA n=2^{args.n_log2} m={BA_M} (seed {BA_SEED}) unweighted, alpha={ALPHA:g}, tau={args.tau} "
+            "trees/step (profiling case)",
+            "n": g.n, "m_edges": g.m, "nnz": g.nnz, "tau": args.tau,
+            "l2": "GPU arm: flushed before every timed step (512 MB write)",
+            "parallelism": ("one GPU" if world == 1 else
+                            f"{world} tree shards: each rank samples its own tau trees, R and C summed by one "
+                            "all-reduce")}
+
+
 def run_reference(args, g):
+    """The oracle (sequential Wilson per host thread) on the same workload: each
+    step samples a bounded share of the step's trees, 2 per host core, and is
+    timed as it stands; value = trees per second over the timed steps."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np
-    from oracle import dense
     trees_per_core = 2
-    vals = []
+    times, trees = [], 0
     cores = os.cpu_count() or 1
+    total = 0
     for i in range(args.warmup + args.steps):
         rate, cores, total, dt = cpu_trees_per_s(g, trees_per_core)
         if i >= args.warmup:
-            vals.append(rate)
-    value = statistics.median(vals)
+            times.append(dt)
+            trees += total
+    value = trees / sum(times)
     st_trees, st_steps = cpu_single_thread(g)
     single = {"trees_per_s": st_trees, "walk_steps_per_s": st_steps, "trees": 2}
+    sample = (f"{total} of the step's {args.tau} trees per step ({trees_per_core} per host core, sequential "
+              f"Wilson per thread); ms_per_step is the time of that sample")
     line = {
         "metric": "USTs/s", "value": value, "unit": "trees/s", "impl": "reference", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * args.tau / value,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD if (args.n_log2 == N_LOG2 and args.tau == TAU) else
-                   f"BA n=2^{args.n_log2} m={BA_M} (seed {BA_SEED}) unweighted, alpha={ALPHA:g}, tau={args.tau} trees/step",
-                   "n": g.n, "m_edges": g.m, "tau": args.tau},
-        "cpu_baseline": {"value": value, "unit": "trees/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{trees_per_core * cores} trees of the workload per step, "
-                                   f"{trees_per_core} per core, sequential Wilson per thread",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(times),
+        "trees_per_step": total, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32/f64", "data": "synthetic", "config": bench_config(args, g, args.gpus),
+        "cpu_baseline": {"value": value, "unit": "trees/s", "cores": cores, "kind": "oracle", "sample": sample,
                          "single_thread": single},
         "e2e": {"value": value, "unit": "trees/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -252,17 +293,44 @@ def reference_vertices(g, count: int, seed: int):
     return np.unique(np.concatenate(picks))
 
 
-def run_cv(args):
-    """Time to max-abs diag(Omega) error <= 0.1 on a reference set, learned control
-    variate vs plain estimator, R-MAT(scale, 16, a=0.57, b=c=0.19), alpha = 1."""
+def gen_graph(spec):
+    """Seeded generator call (runs in a spawned worker process)."""
+    import synth
+    kind, a = spec
+    return {"rmat": synth.rmat, "ba": synth.barabasi_albert}[kind](*a)
+
+
+def start_generation(specs):
+    """Generate graphs in spawned host processes while the GPU works."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    ex = cf.ProcessPoolExecutor(max_workers=max(1, min(len(specs), os.cpu_count() or 1)),
+                                mp_context=mp.get_context("spawn"))
+    return ex, [ex.submit(gen_graph, sp) for sp in specs]
+
+
+TTE_EPS = 0.1
+TRAIN_SCALES = (16, 17, 18)
+TRAIN_PER_SCALE = 8
+
+
+def cv_graph_specs(rmat_scale: int):
+    """R-MAT(scale, 16, a = 0.57, b = c = 0.19), seed 4, and the training graphs
+    R-MAT 16-18, eight per scale (seeds 100 + i + scale)."""
+    return [("rmat", (rmat_scale, 16, 4))] + [("rmat", (sc, 16, 100 + i + sc)) for sc in TRAIN_SCALES
+                                             for i in range(TRAIN_PER_SCALE)]
+
+
+def cv_study(g, train_graphs, seeds: int, rmat_scale: int):
+    """Time to max-abs diag(Omega) error <= 0.1 on a 4096-vertex reference set,
+    for the plain estimator (Prop. 1), the learned control variate (trained
+    network), the same control variate with the untrained network and with the
+    feature-free prediction g = p_v (beta = 1), and the Rao-Blackwellised
+    estimator; median GPU time over seeds (CUDA events: sampling, features and
+    inference, combination).  Training time is reported separately."""
     import numpy as np
     import torch
-    import synth
     from paper_2101_06192_gb300 import cvnet, fc, tune
-    torch.cuda.set_device(0)
-    t0 = time.perf_counter()
-    g = synth.rmat(args.rmat_scale, 16, 4)
-    gen_s = time.perf_counter() - t0
     G = fc.Graph.from_csr(g, [1.0])
     # start order and register variant tuned at the checkpoint scale (tens of
     # trees per launch), untimed; walkers per tree and CTAs per tree stay
@@ -275,26 +343,29 @@ def run_cv(args):
     ref = G.sample(777_000, TJ, tree_offset=10**6, with_C=False)
     dj, _, _ = G.farness(ref["R"], TJ)
     dj = dj[Jt]
-    # spot check of the reference against CG columns (fc_solve) on 16 reference vertices
+    # spot check of the reference against CG columns (fc_solve) on 4 reference vertices
     sub = J[np.linspace(0, J.size - 1, 4).astype(int)]
     B = torch.zeros((sub.size, g.n), dtype=torch.float64, device="cuda")
     B[torch.arange(sub.size), torch.from_numpy(sub).cuda()] = 1.0
     X, _ = G.solve(B, rel_tol=1e-8)
     om_sub = X[torch.arange(sub.size), torch.from_numpy(sub).cuda()]
     ref_vs_cg = float((dj[torch.from_numpy(np.searchsorted(J, sub)).cuda()] - om_sub).abs().max())
-    # training on smaller R-MAT graphs, targets from the plain estimator
+    del B, X
+    # training on the smaller R-MAT graphs, targets from the plain estimator
     tt = time.perf_counter()
     train = []
-    for sc in (16, 17, 18):
-        for sd in (100, 101):
-            gs = synth.rmat(sc, 16, sd + sc)
-            Gs = fc.Graph.from_csr(gs, [1.0])
-            train.append((Gs, Gs.features(), cvnet.plain_targets(Gs, 4096, seed=sd), 0))
+    for i, gs in enumerate(train_graphs):
+        Gs = fc.Graph.from_csr(gs, [1.0])
+        train.append((Gs, Gs.features(), cvnet.plain_targets(Gs, 4096, seed=100 + i), 0))
+    torch.cuda.synchronize()
+    targets_s = time.perf_counter() - tt
+    tt = time.perf_counter()
     params, hist = cvnet.train(train, steps=500, lr=3e-3, seed=1, log_every=100)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - tt
     for (Gs, _, _, _) in train:
         Gs.close()
+    untrained = cvnet.init_params(1)  # the initial parameters of the training run
     checkpoints = [16, 32, 64, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096]
     stream = torch.cuda.current_stream()
 
@@ -306,22 +377,29 @@ def run_cv(args):
         torch.cuda.synchronize()
         return r, a.elapsed_time(b)
 
+    forms = {"plain": None, "cv": params, "cv_untrained": untrained, "cv_p": "p", "rb": None}
     results = {}
     infer_ms = []  # features + MLP forward (fc_vertex_features, fc_mlp_forward)
-    for form in ("plain", "cv", "rb"):
+    for form, prm in forms.items():
         per_seed = []
-        for sd in range(args.seeds):
+        for sd in range(seeds):
             R = torch.zeros(g.n, dtype=torch.int32, device="cuda")
             C = torch.zeros(g.n, dtype=torch.int32, device="cuda")
             acc = torch.zeros(g.n, dtype=torch.int64, device="cuda")
             ms = 0.0
             gp = None
-            if form == "cv":
-                gp, dt = timed(lambda: cvnet.predict(G, params))
-                infer_ms.append(dt)
-                ms += dt
+            if form.startswith("cv"):
+                if prm == "p":
+                    # g = 0 clips to p_v: beta = 1, no features, no network
+                    gp = torch.zeros(g.n, dtype=torch.float32, device="cuda")
+                else:
+                    gp, dt = timed(lambda: cvnet.predict(G, prm))
+                    if form == "cv":
+                        infer_ms.append(dt)
+                    ms += dt
             done = 0
             hit = None
+            err = None
             for cp in checkpoints:
                 if form == "rb":
                     # the same trees, with their parents, summarised by the
@@ -337,42 +415,64 @@ def run_cv(args):
                     _, dt = timed(lambda: G.sample(50_000 + 1000 * sd, cp - done, tree_offset=done, R=R, C=C))
                     ms += dt
                     done = cp
-                    if form == "cv":
+                    if gp is not None:
                         (d, _, _), dt = timed(lambda: G.farness(R, cp, C=C, g_pred=gp))
                     else:
                         (d, _, _), dt = timed(lambda: G.farness(R, cp))
                     ms += dt
                 err = float((d[Jt] - dj).abs().max())
-                if err <= 0.1:
+                if err <= TTE_EPS:
                     hit = {"trees": cp, "ms": ms, "max_err": err}
                     break
             per_seed.append(hit or {"trees": None, "ms": ms, "max_err": err})
         ok = [r for r in per_seed if r["trees"] is not None]
         results[form] = {
-            "median_ms": statistics.median(r["ms"] for r in ok) if ok else None,
-            "median_trees": statistics.median(r["trees"] for r in ok) if ok else None,
+            "median_ms": statistics.median(r["ms"] for r in ok) if len(ok) == len(per_seed) else None,
+            "median_trees": statistics.median(r["trees"] for r in ok) if len(ok) == len(per_seed) else None,
             "runs": per_seed,
         }
     G.close()
-    line = {
-        "metric": "time to eps=0.1 max-abs diag(Omega) error", "unit": "ms", "higher_is_better": False,
-        "value": results["cv"]["median_ms"], "plain_ms": results["plain"]["median_ms"],
-        "speedup_cv_over_plain": (results["plain"]["median_ms"] / results["cv"]["median_ms"]
-                                  if results["cv"]["median_ms"] and results["plain"]["median_ms"] else None),
-        "trees_plain": results["plain"]["median_trees"], "trees_cv": results["cv"]["median_trees"],
-        "rao_blackwell_ms": results["rb"]["median_ms"], "trees_rao_blackwell": results["rb"]["median_trees"],
+    med = {f: results[f]["median_ms"] for f in forms}
+    summary = {
+        "eps": TTE_EPS, "unit": "ms", "seeds": seeds,
+        "workload": f"R-MAT scale {rmat_scale} ef 16 (0.57,0.19,0.19) seed 4, alpha=1",
+        "plain_ms": med["plain"], "cv_ms": med["cv"], "cv_untrained_ms": med["cv_untrained"],
+        "cv_p_ms": med["cv_p"], "rb_ms": med["rb"],
+        "trees": {f: results[f]["median_trees"] for f in forms},
+        "speedup_cv_over_plain": (med["plain"] / med["cv"]) if med["cv"] and med["plain"] else None,
+        "speedup_cv_over_untrained": (med["cv_untrained"] / med["cv"]) if med["cv"] and med["cv_untrained"] else None,
+        "speedup_cv_over_p": (med["cv_p"] / med["cv"]) if med["cv"] and med["cv_p"] else None,
+        "reference_set": {"vertices": int(J.size), "plain_trees": TJ, "reference_vs_cg_max_abs": ref_vs_cg},
+        "train": {"graphs": f"R-MAT scale {TRAIN_SCALES[0]}-{TRAIN_SCALES[-1]} x{TRAIN_PER_SCALE}, plain targets "
+                            "tau=4096", "steps": 500, "loss_first_last": [hist[0][1], hist[-1][1]],
+                  "seconds": train_s, "target_seconds": targets_s},
         # features + forward pass per vertex: about 1.55 kFLOP FP32 (128 hidden
         # units x (4 FMAs + bias + relu) + 128 FMAs + the sigmoid); CUDA-core
         # FP32 peak 152 SMs x 128 lanes x 2 x 2.07 GHz = 80.5 TFLOP/s
         "cv_inference": {"ms": statistics.median(infer_ms) if infer_ms else None,
                          "tflops": (1.55e3 * g.n / (statistics.median(infer_ms) / 1000.0) / 1e12) if infer_ms else None,
                          "fp32_peak_tflops": 80.5, "bytes_per_vertex": 16 + 4},
-        "seeds": args.seeds, "reference_set": {"vertices": int(J.size), "plain_trees": TJ,
-                                       "reference_vs_cg_max_abs": ref_vs_cg},
-        "train": {"graphs": "R-MAT scale 16-18 x2, plain targets tau=4096", "steps": 500,
-                  "loss_first_last": [hist[0][1], hist[-1][1]], "seconds": train_s},
-        "config": {"workload": f"R-MAT scale {args.rmat_scale} ef 16 (0.57,0.19,0.19), alpha=1",
-                   "n": g.n, "m_edges": g.m, "gen_seconds": gen_s, "sampler_shape": shape},
+        "sampler_shape": shape,
+    }
+    return summary, results
+
+
+def run_cv(args):
+    """Time to max-abs diag(Omega) error <= 0.1, learned control variate vs plain
+    estimator and the ablations, R-MAT(scale, 16, a=0.57, b=c=0.19), alpha = 1."""
+    import torch
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    ex, futs = start_generation(cv_graph_specs(args.rmat_scale))
+    graphs = [f.result() for f in futs]
+    ex.shutdown()
+    gen_s = time.perf_counter() - t0
+    g = graphs[0]
+    summary, results = cv_study(g, graphs[1:], args.seeds, args.rmat_scale)
+    line = {
+        "metric": "time to eps=0.1 max-abs diag(Omega) error", "unit": "ms", "higher_is_better": False,
+        "value": summary["cv_ms"], "time_to_eps": summary,
+        "config": {"workload": summary["workload"], "n": g.n, "m_edges": g.m, "gen_seconds": gen_s},
         "dtype": "u32/f64 (MLP bf16/fp32)", "data": "synthetic", "runs": results,
     }
     print(json.dumps(line), flush=True)
@@ -414,7 +514,8 @@ def run_grid(args):
     pops = statistics.mean(s[0] for s in stats)
     deps = statistics.mean(s[1] for s in stats)
     n_trees = len(alphas) * tau
-    alg_bytes = deps * 40 + pops * 20 + n_trees * g.n * (16 + 4)
+    alg_bytes = algorithmic_bytes(deps, g.n, n_trees, weighted=True)
+    layout = layout_bytes(deps, pops, g.n, n_trees, 0)
     peaks, peak_kind = load_peaks()
     achieved = alg_bytes / (ms / 1000.0) / 1e9
     line = {
@@ -424,7 +525,9 @@ def run_grid(args):
                    "n": g.n, "m_edges": g.m, "shape": shape},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": float(peaks.get("hbm_gbs", 6800.0)),
                      "unit": "GB/s", "frac": achieved / float(peaks.get("hbm_gbs", 6800.0)),
-                     "peak_source": peak_kind, "departures_per_step": deps, "pops_per_step": pops},
+                     "peak_source": peak_kind, "departures_per_step": deps, "pops_per_step": pops,
+                     "algorithmic_bytes": alg_bytes, "layout_bytes": layout,
+                     "layout_frac": layout / (ms / 1000.0) / 1e9 / float(peaks.get("hbm_gbs", 6800.0))},
         "clocks": clk,
     }
     G.close()
@@ -722,15 +825,20 @@ def main():
         if rank == 0:
             run_cv(args)
         return
-    import numpy as np
     import synth
+    full = args.n_log2 == N_LOG2 and args.tau == TAU
+    # time to eps (R-MAT 22, learned control variate vs plain): its graphs are
+    # generated by host processes while the GPU runs the timed steps
+    tte_gen = None
+    if args.impl == "ours" and rank == 0 and world == 1 and full and not args.no_tte:
+        tte_gen = start_generation(cv_graph_specs(args.rmat_scale))
     g = synth.barabasi_albert(1 << args.n_log2, BA_M, BA_SEED)
     if args.impl == "reference":
         run_reference(args, g)
         return
 
     import torch
-    from paper_2101_06192_gb300 import fc
+    from paper_2101_06192_gb300 import fc, shard
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -746,7 +854,8 @@ def main():
     C = torch.zeros(n, dtype=torch.int32, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    tree_offset = rank * tau
+    # weak scaling: every rank samples its own tau trees of a world * tau run
+    tree_offset, _ = shard.tree_range(rank, world, world * tau)
     shape = {}
     launched = {}
     last_diag = [None]
@@ -767,9 +876,11 @@ def main():
             samp_ev[1].record(stream)
         if stats is not None:
             stats.append(G.sampler_stats())
-            launched.update(kernel=G.last_kernel(), **G.last_shape())
+            launched.update(kernel=G.last_kernel(), cluster=G.last_cluster(), **G.last_shape())
+        if world > 1:
+            shard.allreduce_counts(R, C)  # the one exchange of the sharded estimator
         x, _ = G.pivot_solve(rel_tol=1e-9)
-        diag, far, clo = G.farness(R, tau, x_pivot=x)
+        diag, far, clo = G.farness(R, world * tau, x_pivot=x)
         top = fc.top_k(diag, TOPK)
         G.close()
         last_diag[0] = diag
@@ -842,21 +953,26 @@ def main():
     value = world * tau * args.steps / (tot_ms / 1000.0)
     e2e_value = world * tau * args.steps / (tot_e2e / 1000.0)
 
-    # roofline of the dominant kernel (the persistent Wilson sampler)
+    # roofline of the dominant kernel (the persistent Wilson sampler):
+    # algorithmic bytes = 20 B per walk step + 8 B per vertex and tree
     peaks, peak_kind = load_peaks()
-    pops = statistics.mean(s[0] for s in stats)
-    deps = statistics.mean(s[1] for s in stats)
-    alg_bytes = deps * 40 + pops * 20 + tau * n * (16 + 4) + R_sum * 8
+    pops = statistics.mean(s_[0] for s_ in stats)
+    deps = statistics.mean(s_[1] for s_ in stats)
+    alg_bytes = algorithmic_bytes(deps, n, tau)
+    lay_bytes = layout_bytes(deps, pops, n, tau, R_sum if world == 1 else R_sum // world)
     samp_s = statistics.mean(samp_ms) / 1000.0
     achieved = alg_bytes / samp_s / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
     kname = {2: "k_wilson_edge<flags, {r}>", 3: "k_wilson_edge<smem bitmap, {r}>",
              4: "k_wilson_edge<global bitmap, {r}>"}.get(
         launched.get("kernel"), "k_wilson<global state, {r}>").format(r=launched.get("regs"))
-    traffic = profiled_traffic(kname, launched) if (args.n_log2 == N_LOG2 and tau == TAU) else None
+    traffic = profiled_traffic(kname, launched) if full else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_over_algorithmic": (traffic / alg_bytes) if traffic else None,
+                "algorithmic_bytes": alg_bytes,
+                "algorithmic_bytes_rule": "20 B per walk step + 8 B per vertex and tree",
+                "layout_bytes": lay_bytes, "layout_frac": lay_bytes / samp_s / 1e9 / peak,
                 "kernel": kname, "launch": launched,
                 "peak_source": peak_kind, "kernel_ms": 1000.0 * samp_s,
                 "departures_per_launch": deps, "pops_per_launch": pops,
@@ -867,8 +983,7 @@ def main():
     # accuracy of the last step's estimate (untimed): diag(Omega) against CG
     # columns of the library's solver on degree-stratified reference vertices
     accuracy = None
-    if rank == 0 and args.n_log2 == N_LOG2 and not args.no_e2e:
-        import math
+    if rank == 0 and full and not args.no_e2e:
         J = reference_vertices(g, 256, 5)
         Gj = fc.Graph(rowptr_d, colidx_d, None, [ALPHA])
         B = torch.zeros(J.size, n, dtype=torch.float64, device=dev)
@@ -880,8 +995,15 @@ def main():
         err = (last_diag[0][Jt] - ref).abs()
         accuracy = {"reference_vertices": int(J.size), "max_abs_err": float(err.max()),
                     "mean_abs_err": float(err.mean()),
-                    "hoeffding_bound_delta_1e-6": math.sqrt(math.log(2e6) / (2 * tau))}
+                    "hoeffding_bound_delta_1e-6": math.sqrt(math.log(2e6) / (2 * world * tau))}
         del B, X
+    del flush
+
+    tte_graphs = None
+    if tte_gen is not None:
+        ex, futs = tte_gen
+        tte_graphs = [f.result() for f in futs]
+        ex.shutdown()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -892,16 +1014,17 @@ def main():
                          f"sequential Wilson (Algorithm 2) per thread",
                "single_thread": {"trees_per_s": st_trees, "walk_steps_per_s": st_steps, "trees": 2}}
 
+    tte = None
+    if tte_graphs is not None:
+        tte, _ = cv_study(tte_graphs[0], tte_graphs[1:], args.seeds, args.rmat_scale)
+
     if rank == 0:
         line = {
             "metric": "USTs/s", "value": value, "unit": "trees/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32/f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.n_log2 == N_LOG2 and tau == TAU else
-                       f"BA n=2^{args.n_log2} m={BA_M}, alpha={ALPHA:g}, tau={tau} (profiling case)", "n": n, "m_edges": g.m, "nnz": nnz, "tau": tau,
-                       "l2": "flushed before every timed step (512 MB write); per-step working set "
-                             f"{tau * n * 16 / 1e9:.1f} GB of tree state > L2",
-                       "parallelism": f"replicas x{world}", "sampler_shape": shape},
+            "config": bench_config(args, g, world),
+            "sampler_shape": shape,
             "e2e": {"value": e2e_value, "unit": "trees/s", "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz,
                     "d2h_bytes_per_step": 8 * n + 4 * TOPK},
             "gpu_launches": int(launches),
@@ -910,6 +1033,7 @@ def main():
             "clocks": clk,
             "sampling_ms_per_step": statistics.mean(samp_ms),
             "accuracy": accuracy,
+            "time_to_eps": tte,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

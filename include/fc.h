@@ -330,6 +330,8 @@ fc_status fc_pivot_solve(fc_graph* g, int32_t alpha_idx, double* x, double rel_t
  *   with C and g_pred (control variate, not in the paper):
  *               d_v -= beta_v (C[v]/tau - p_v),
  *               beta_v = (1 - clip(g_v, p_v, 1)) / (1 - p_v)
+ *               (a g_v that is NaN counts as p_v: every g_pred keeps the
+ *                estimator unbiased)
  *   farness_v = n d_v + sum_w d_w - 2;   closeness_v = n / farness_v.
  * R, C: the alpha-a slices (n entries each).  C, g_pred (float[n]) and x_pivot
  * (double[n+1]) may be NULL; C and g_pred must be both set or both NULL.
@@ -342,8 +344,9 @@ fc_status fc_forest_farness(fc_graph* g, int32_t alpha_idx, const uint32_t* R, c
 
 /*
  * fc_forest_farness for callers that must not allocate device memory -- for
- * example code that runs while a CUDA graph is being captured, or under a
- * memory manager that forbids allocations behind its back.  Same arguments,
+ * example code under a memory manager that forbids allocations it does not
+ * make itself, or a serving loop whose device memory is fixed once at
+ * start-up.  Same arguments,
  * layouts and results as fc_forest_farness; the only difference is where the
  * temporary per-block sums live: fc_forest_farness takes them from the
  * stream-ordered pool, this entry point uses a fixed device array compiled
@@ -354,8 +357,10 @@ fc_status fc_forest_farness(fc_graph* g, int32_t alpha_idx, const uint32_t* R, c
  *   - The graph's device must be the current device; batches of graphs
  *     (fc_build_batch) are rejected with FC_EINVAL.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) and caches it; make that first call before any
- *     stream capture begins.
+ *     (cudaGetSymbolAddress) and caches it for the life of the process; make
+ *     that first call before any stream capture begins.  The cache assumes
+ *     the device's primary context is not reset (cudaDeviceReset) while the
+ *     library is loaded.
  *   - All calls share the one array: calls whose work overlaps on the GPU
  *     (different streams, or several host threads) race and give wrong
  *     results.  Serialise them (one stream, or events).
@@ -399,6 +404,19 @@ fc_status fc_mlp_forward(fc_graph* g, int32_t alpha_idx, const float* X, const f
  */
 fc_status fc_mlp_loss_grad(fc_graph* g, int32_t alpha_idx, const float* X, const float* y, const float* params,
                            float* grad, float* loss, void* stream);
+
+/*
+ * fc_mlp_loss_grad scaled and accumulated, for training on several graphs:
+ *   grad = (accumulate ? grad : 0) + weight * dloss/dparams,
+ *   loss = (accumulate ? loss : 0) + weight * loss   (loss may be NULL).
+ * Calling it once per graph with weight 1/#graphs (accumulate = 0 for the
+ * first) leaves the mean gradient over the graphs in grad, ready for
+ * fc_mlp_adam.  FC_EINVAL for a weight that is not finite.  Deterministic;
+ * allocates temporary device memory.  Async.
+ */
+fc_status fc_mlp_loss_grad_acc(fc_graph* g, int32_t alpha_idx, const float* X, const float* y,
+                               const float* params, float weight, int32_t accumulate, float* grad, float* loss,
+                               void* stream);
 
 /*
  * One Adam step (Kingma & Ba, bias-corrected; step is 1-based) on count

@@ -35,7 +35,10 @@ def p_root(g, alpha: float) -> np.ndarray:
 
 
 def beta_from_prediction(gpred: np.ndarray, p: np.ndarray) -> np.ndarray:
-    gg = np.clip(gpred, p, 1.0)
+    """beta_v = (1 - clip(g_v, p_v, 1)) / (1 - p_v); a prediction that is not a
+    number is read as p_v (beta_v = 1), which keeps the estimator unbiased."""
+    gpred = np.asarray(gpred, dtype=np.float64)
+    gg = np.where(np.isnan(gpred), p, np.clip(gpred, p, 1.0))
     with np.errstate(divide="ignore", invalid="ignore"):
         b = np.where(p < 1.0, (1.0 - gg) / (1.0 - p), 0.0)
     return b

@@ -41,8 +41,10 @@ __global__ void k_combine(int32_t n, const uint32_t* __restrict__ R, const uint3
     if (C != nullptr) {
       const double p = p_from_rowinfo(rinfo[v]);
       if (p < 1.0) {
+        // clip(g, p, 1); a prediction that is not a number counts as p (so
+        // every g_pred, NaN included, leaves the estimator unbiased)
         double gg = (double)gpred[v];
-        gg = gg < p ? p : (gg > 1.0 ? 1.0 : gg);
+        gg = (gg >= p) ? fmin(gg, 1.0) : p;
         const double beta = (1.0 - gg) / (1.0 - p);
         d = d - beta * ((double)C[v] * inv_tau - p);
       }

@@ -172,14 +172,16 @@ __global__ void __launch_bounds__(MLP_T) k_mlp_grad(int32_t n, const float4* __r
     }
     __syncthreads();
   }
-  float* out = gpart + (size_t)blockIdx.x * NPARAM;
-  out[OFF_W1 + j * NF + 0] = gW0;
-  out[OFF_W1 + j * NF + 1] = gW1;
-  out[OFF_W1 + j * NF + 2] = gW2;
-  out[OFF_W1 + j * NF + 3] = gW3;
-  out[OFF_B1 + j] = gb1;
-  out[OFF_W2 + j] = gw2;
-  if (j == 0) out[OFF_B2] = gb2;
+  // parameter-major partials: gpart[i * nb + block] (the reduction reads
+  // each parameter's partials contiguously)
+  const size_t nb = gridDim.x, b = blockIdx.x;
+  gpart[(size_t)(OFF_W1 + j * NF + 0) * nb + b] = gW0;
+  gpart[(size_t)(OFF_W1 + j * NF + 1) * nb + b] = gW1;
+  gpart[(size_t)(OFF_W1 + j * NF + 2) * nb + b] = gW2;
+  gpart[(size_t)(OFF_W1 + j * NF + 3) * nb + b] = gW3;
+  gpart[(size_t)(OFF_B1 + j) * nb + b] = gb1;
+  gpart[(size_t)(OFF_W2 + j) * nb + b] = gw2;
+  if (j == 0) gpart[(size_t)OFF_B2 * nb + b] = gb2;
   sl[j] = lsum;
   __syncthreads();
   for (int s = MLP_T / 2; s > 0; s >>= 1) {
@@ -189,18 +191,35 @@ __global__ void __launch_bounds__(MLP_T) k_mlp_grad(int32_t n, const float4* __r
   if (j == 0) lpart[blockIdx.x] = sl[0];
 }
 
-__global__ void k_mlp_grad_reduce(const float* __restrict__ gpart, const double* __restrict__ lpart, int nb,
-                                  double inv_n, float* __restrict__ grad, float* __restrict__ loss) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// One block per parameter (block NPARAM: the loss): the block's threads sum
+// strided runs of the partials, then a fixed-order tree in shared memory, so
+// the result is deterministic.  out = (accumulate ? out : 0) + weight * sum.
+constexpr int RED_T = 256;
+__global__ void __launch_bounds__(RED_T) k_mlp_grad_reduce(const float* __restrict__ gpart,
+                                                           const double* __restrict__ lpart, int nb, double inv_n,
+                                                           float weight, int accumulate, float* __restrict__ grad,
+                                                           float* __restrict__ loss) {
+  __shared__ double red[RED_T];
+  const int i = blockIdx.x;
+  double s = 0.0;
   if (i < NPARAM) {
-    float s = 0.0f;
-    for (int b = 0; b < nb; ++b) s += gpart[(size_t)b * NPARAM + i];
-    grad[i] = s;
+    for (int b = threadIdx.x; b < nb; b += RED_T) s += (double)gpart[(size_t)i * nb + b];
+  } else {
+    for (int b = threadIdx.x; b < nb; b += RED_T) s += lpart[b];
   }
-  if (i == 0 && loss != nullptr) {
-    double l = 0.0;
-    for (int b = 0; b < nb; ++b) l += lpart[b];
-    *loss = (float)(l * inv_n);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = RED_T / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  if (i < NPARAM) {
+    const float v = weight * (float)red[0];
+    grad[i] = accumulate ? grad[i] + v : v;
+  } else if (loss != nullptr) {
+    const float v = weight * (float)(red[0] * inv_n);
+    *loss = accumulate ? *loss + v : v;
   }
 }
 
@@ -263,10 +282,11 @@ extern "C" fc_status fc_mlp_forward(fc_graph* g, int32_t alpha_idx, const float*
   return FC_OK;
 }
 
-extern "C" fc_status fc_mlp_loss_grad(fc_graph* g, int32_t alpha_idx, const float* X, const float* y,
-                                      const float* params, float* grad, float* loss, void* stream) {
+extern "C" fc_status fc_mlp_loss_grad_acc(fc_graph* g, int32_t alpha_idx, const float* X, const float* y,
+                                          const float* params, float weight, int32_t accumulate, float* grad,
+                                          float* loss, void* stream) {
   if (g == nullptr || X == nullptr || y == nullptr || params == nullptr || grad == nullptr || alpha_idx < 0 ||
-      alpha_idx >= g->n_alpha) {
+      alpha_idx >= g->n_alpha || !std::isfinite(weight)) {
     set_error("fc_mlp_loss_grad: bad argument");
     return FC_EINVAL;
   }
@@ -279,11 +299,17 @@ extern "C" fc_status fc_mlp_loss_grad(fc_graph* g, int32_t alpha_idx, const floa
   k_mlp_grad<<<nb, MLP_T, 0, st>>>(g->n, (const float4*)X, g->rowinfo + (size_t)alpha_idx * g->n, y, params,
                                    1.0f / (float)g->n, gpart, lpart);
   FC_LAUNCHED();
-  k_mlp_grad_reduce<<<(NPARAM + 255) / 256, 256, 0, st>>>(gpart, lpart, nb, 1.0 / (double)g->n, grad, loss);
+  k_mlp_grad_reduce<<<NPARAM + 1, RED_T, 0, st>>>(gpart, lpart, nb, 1.0 / (double)g->n, weight, accumulate ? 1 : 0,
+                                                  grad, loss);
   FC_LAUNCHED();
   FC_CK(cudaFreeAsync(gpart, st));
   FC_CK(cudaFreeAsync(lpart, st));
   return FC_OK;
+}
+
+extern "C" fc_status fc_mlp_loss_grad(fc_graph* g, int32_t alpha_idx, const float* X, const float* y,
+                                      const float* params, float* grad, float* loss, void* stream) {
+  return fc_mlp_loss_grad_acc(g, alpha_idx, X, y, params, 1.0f, 0, grad, loss, stream);
 }
 
 extern "C" fc_status fc_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t count, int32_t step,

@@ -35,25 +35,23 @@ def plain_targets(G: "fc.Graph", tau: int, seed: int, alpha_idx: int = 0) -> tor
 
 
 def train(data, steps: int = 600, lr: float = 3e-3, seed: int = 0, params=None, log_every: int = 0):
-    """Full-batch Adam over a list of (G, X, y, alpha_idx); gradients of the
-    graphs are averaged.  Returns (params, loss history)."""
+    """Full-batch Adam over a list of (G, X, y, alpha_idx); the library averages
+    the graphs' gradients (fc_mlp_loss_grad_acc with weight 1/#graphs).
+    Returns (params, loss history)."""
     if params is None:
         params = init_params(seed)
     m = torch.zeros_like(params)
     v = torch.zeros_like(params)
+    grad = torch.empty_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    w = 1.0 / len(data)
     hist = []
     for step in range(1, steps + 1):
-        gsum = torch.zeros_like(params)
-        lsum = 0.0
-        for (G, X, y, a) in data:
-            loss, grad = G.mlp_loss_grad(X, y, params, alpha_idx=a)
-            gsum += grad
-            if log_every and step % log_every == 0:
-                lsum += float(loss.item())
-        gsum /= len(data)
-        fc.mlp_adam(params, gsum, m, v, step, lr)
+        for i, (G, X, y, a) in enumerate(data):
+            G.mlp_loss_grad_acc(X, y, params, grad, loss, w, i > 0, alpha_idx=a)
+        fc.mlp_adam(params, grad, m, v, step, lr)
         if log_every and step % log_every == 0:
-            hist.append((step, lsum / len(data)))
+            hist.append((step, float(loss.item())))
     return params, hist
 
 

@@ -71,6 +71,7 @@ def lib():
             "fc_vertex_features": ([P, I32, P, P], ctypes.c_int),
             "fc_mlp_forward": ([P, I32, P, P, P, P], ctypes.c_int),
             "fc_mlp_loss_grad": ([P, I32, P, P, P, P, P, P], ctypes.c_int),
+            "fc_mlp_loss_grad_acc": ([P, I32, P, P, P, ctypes.c_float, I32, P, P, P], ctypes.c_int),
             "fc_mlp_adam": ([P, P, P, P, I32, I32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                              ctypes.c_float, P], ctypes.c_int),
             "fc_tau_for": ([D, D, D, I64], I64),
@@ -389,6 +390,13 @@ class Graph:
         _check(lib().fc_mlp_loss_grad(self._h, alpha_idx, _ptr(X.contiguous()), _ptr(y.contiguous()), _ptr(params),
                                       _ptr(grad), _ptr(loss), _stream(stream)), "fc_mlp_loss_grad")
         return loss, grad
+
+    def mlp_loss_grad_acc(self, X, y, params, grad, loss, weight: float, accumulate: bool, alpha_idx: int = 0,
+                          stream=None):
+        """fc_mlp_loss_grad_acc: grad (and loss) = (accumulate ? old : 0) + weight * this graph's."""
+        _check(lib().fc_mlp_loss_grad_acc(self._h, alpha_idx, _ptr(X.contiguous()), _ptr(y.contiguous()),
+                                          _ptr(params), float(weight), int(bool(accumulate)), _ptr(grad),
+                                          _ptr(loss), _stream(stream)), "fc_mlp_loss_grad_acc")
 
     def p_root(self, alpha_idx: int = 0, stream=None):
         p = torch.empty(self.n, dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))

@@ -75,6 +75,21 @@ def from_edges(n: int, u, v, w=None, name: str = "") -> Graph:
     lo = np.minimum(u, v)
     hi = np.maximum(u, v)
     key = lo * n + hi
+    if w is None:
+        # unweighted: the sorted distinct keys give the same CSR as the general
+        # path below (the (src, dst) pairs are distinct, so any sort orders them
+        # the same way), with two plain sorts instead of argsorts
+        ukey = np.sort(key)
+        if ukey.size:
+            ukey = ukey[np.concatenate(([True], ukey[1:] != ukey[:-1]))]
+        lo, hi = ukey // n, ukey % n
+        both = np.concatenate([ukey, hi * n + lo])
+        both.sort()
+        src, dst = both // n, both % n
+        counts = np.bincount(src, minlength=n) if src.size else np.zeros(n, np.int64)
+        rowptr = np.zeros(n + 1, dtype=np.int64)
+        np.cumsum(counts, out=rowptr[1:])
+        return Graph(n=n, rowptr=rowptr, colidx=dst.astype(np.int32), w=None, name=name)
     _, first = np.unique(key, return_index=True)
     lo, hi = lo[first], hi[first]
     if w is not None:
@@ -230,12 +245,15 @@ def rmat(scale: int, edge_factor: int, seed: int, a=0.57, b=0.19, c=0.19,
         k = min(chunk, total - done)
         uu = np.zeros(k, dtype=np.int64)
         vv = np.zeros(k, dtype=np.int64)
+        q = np.empty(k, dtype=np.uint8)
         for lvl in range(scale):
+            # quadrant of this level: 0 (a), 1 (b: v bit), 2 (c: u bit), 3 (d: both)
             r = rng.random(k)
-            ubit = r >= ab
-            vbit = ((r >= a) & (r < ab)) | (r >= abc)
-            uu |= ubit.astype(np.int64) << lvl
-            vv |= vbit.astype(np.int64) << lvl
+            np.greater_equal(r, a, out=q, casting="unsafe")
+            q += r >= ab
+            q += r >= abc
+            uu |= (q >> 1).astype(np.int64) << lvl
+            vv |= (q & 1).astype(np.int64) << lvl
         us.append(uu)
         vs.append(vv)
         done += k

@@ -114,3 +114,73 @@ def test_trained_network_reduces_error_and_stays_unbiased():
     for (G, _, _, _) in train:
         G.close()
     Gt.close()
+
+
+def test_accumulated_gradient_is_the_mean_over_graphs():
+    """fc_mlp_loss_grad_acc with weight 1/k over k graphs equals the mean of the
+    single-graph gradients (the cross-graph average runs in the library)."""
+    params = cvnet.init_params(5)
+    data, grads, losses = [], [], []
+    for sd in (201, 202, 203):
+        g = synth.rmat(9, 8, sd)
+        G = fc.Graph.from_csr(g, [1.0])
+        y = cvnet.plain_targets(G, 256, seed=sd)
+        X = G.features()
+        data.append((G, X, y))
+        loss, grad = G.mlp_loss_grad(X, y, params)
+        grads.append(grad.cpu().numpy().astype(np.float64))
+        losses.append(float(loss.item()))
+    acc = torch.empty_like(params)
+    lacc = torch.empty(1, dtype=torch.float32, device="cuda")
+    for i, (G, X, y) in enumerate(data):
+        G.mlp_loss_grad_acc(X, y, params, acc, lacc, 1.0 / len(data), i > 0)
+    mean = np.mean(grads, axis=0)
+    np.testing.assert_allclose(acc.cpu().numpy(), mean, rtol=1e-5, atol=1e-6 * np.abs(mean).max())
+    assert abs(float(lacc.item()) - np.mean(losses)) <= 1e-6 * np.mean(losses)
+    for (G, _, _) in data:
+        G.close()
+
+
+def _cv_variance(om, p, g):
+    """Exact per-tree variance of X - beta (C - p) for beta from prediction g:
+    Var = Omega(1 - Omega) + beta^2 p(1 - p) - 2 beta p (1 - Omega), using
+    E[X] = Omega, E[C] = p and C = 1 => X = 1."""
+    beta = ocv.beta_from_prediction(g, p)
+    return om * (1 - om) + beta ** 2 * p * (1 - p) - 2 * beta * p * (1 - om)
+
+
+def test_training_gains_over_untrained_and_feature_free_predictions():
+    """Ablation at equal trees on a held-out graph, by the exact per-tree
+    variance of each estimator (dense Omega, no sampling noise): the trained
+    network's control variate against the plain estimator (the method without
+    the network), the same network untrained, and the feature-free prediction
+    g = p_v (beta = 1, the control variate's structure alone).  The trained
+    network must beat the plain estimator by a wide margin and the untrained
+    network clearly; against g = p_v it must not lose, and the gain it has is
+    reported (the feature-free form is already within a few percent of the
+    optimal beta on R-MAT graphs, so that margin is small by construction)."""
+    train = []
+    for seed in (101, 102, 103, 104):
+        g = synth.rmat(10, 8, seed)
+        G = fc.Graph.from_csr(g, [1.0])
+        train.append((G, G.features(), cvnet.plain_targets(G, 4096, seed=seed), 0))
+    params, _ = cvnet.train(train, steps=400, lr=3e-3, seed=1)
+    gt = synth.rmat(11, 8, 999)
+    Gt = fc.Graph.from_csr(gt, [1.0])
+    om = np.diag(dense.forest_matrix(gt, 1.0))
+    p = ocv.p_root(gt, 1.0)
+    v_plain = om * (1 - om)
+    v_tr = _cv_variance(om, p, cvnet.predict(Gt, params).cpu().numpy().astype(np.float64))
+    v_un = _cv_variance(om, p, cvnet.predict(Gt, cvnet.init_params(1)).cpu().numpy().astype(np.float64))
+    v_p = _cv_variance(om, p, np.zeros(gt.n))
+    v_opt = _cv_variance(om, p, om)
+    m = {k: float(np.mean(v)) for k, v in (("plain", v_plain), ("trained", v_tr), ("untrained", v_un),
+                                          ("g=p", v_p), ("optimal", v_opt))}
+    print("mean per-tree variance", m, "max", float(v_tr.max()), float(v_p.max()))
+    assert m["plain"] / m["trained"] > 5.0, m
+    assert m["untrained"] / m["trained"] > 1.2, m
+    assert m["trained"] <= m["g=p"] * 1.0001, m
+    assert m["optimal"] <= m["trained"] + 1e-12, m
+    for (G, _, _, _) in train:
+        G.close()
+    Gt.close()

@@ -139,13 +139,93 @@ def test_tree_offset_split_equals_single_call():
 
 
 def test_ba_full_size_trees_bit_exact():
-    """BA n = 2^20, m = 8, alpha = 1 in the default (benchmark) launch shape:
-    the first trees of the run are the oracle's, bit for bit."""
+    """BA n = 2^20, m = 8, alpha = 1, few trees (the automatic shape spreads a
+    tree over a thread-block cluster here): the first trees of the run are the
+    oracle's, bit for bit."""
     g = synth.barabasi_albert(1 << 20, 8, 2)
     G = fc.Graph.from_csr(g, [1.0])
     _check_trees(G, g, [1.0], seed=12345, tau=3)
     # trees deep into the run (offset) as well
     _check_trees(G, g, [1.0], seed=12345, tau=1, tree_offset=1000)
+    G.close()
+
+
+def _oracle_threaded(g, alpha, seed, tau, tree_offset=0, alpha_idx=0, threads=16):
+    """native.wilson over tree ranges in parallel host threads (the C sampler
+    releases the GIL): parents, R, C and step counts of trees
+    [tree_offset, tree_offset + tau), identical to one sequential call."""
+    import concurrent.futures as cf
+    threads = max(1, min(threads, tau))
+    cuts = np.linspace(0, tau, threads + 1).astype(int)
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        futs = [ex.submit(native.wilson, g, alpha, seed, int(b - a), tree_offset + int(a), alpha_idx, None, True)
+                for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+        parts = [f.result() for f in futs]
+    return {"parents": np.concatenate([o["parents"] for o in parts]),
+            "R": np.sum([o["R"] for o in parts], axis=0, dtype=np.uint32),
+            "C": np.sum([o["C"] for o in parts], axis=0, dtype=np.uint32),
+            "steps": np.concatenate([o["steps"] for o in parts])}
+
+
+def _check_full_wave(G, g, alphas, seed, tau, tree_offset, expect_kernel, walkers, regs):
+    out = G.sample(seed, tau, tree_offset=tree_offset, want_parents=True, want_steps=True)
+    torch.cuda.synchronize()
+    shape = G.last_shape()
+    assert G.last_kernel() == expect_kernel and G.last_cluster() == 1, (G.last_kernel(), G.last_cluster())
+    assert shape["walkers_per_tree"] == walkers and shape["regs"] == regs, shape
+    # a full wave: one 1024-walker CTA per SM, every SM on its own tree at once
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    assert shape["ctas"] == min(nsm, len(alphas) * tau), (shape, nsm)
+    n = g.n
+    R = _np32(out["R"]).reshape(len(alphas), n)
+    C = _np32(out["C"]).reshape(len(alphas), n)
+    steps = out["steps"].cpu().numpy()
+    for a, al in enumerate(alphas):
+        ref = _oracle_threaded(g, al, seed, tau, tree_offset, a)
+        par = out["parents"][a].cpu().numpy()
+        for t in range(tau):
+            np.testing.assert_array_equal(par[t], ref["parents"][t], err_msg=f"alpha {a} tree {t}")
+        np.testing.assert_array_equal(R[a], ref["R"], err_msg=f"R alpha {a}")
+        np.testing.assert_array_equal(C[a], ref["C"], err_msg=f"C alpha {a}")
+        np.testing.assert_array_equal(steps[a].astype(np.uint64), ref["steps"], err_msg=f"steps alpha {a}")
+
+
+def test_ba_full_size_benchmark_shape_full_wave_bit_exact():
+    """The benchmark's own sampler launch: BA n = 2^20, m = 8 (seed 2), alpha = 1,
+    the shipped tuning-table shape (1024 walkers per tree, 64-register variant,
+    vertex-id start order), in-tree bitmap in shared memory, one CTA per tree,
+    152 trees = one full wave of the persistent grid with every CTA on its own
+    tree at once.  Parents, R, C and step counts of all 152 trees equal the
+    oracle's, for the first wave of a step and for its last wave (trees
+    872..1023 of a 1024-tree step)."""
+    from paper_2101_06192_gb300 import tune
+    g = synth.barabasi_albert(1 << 20, 8, 2)
+    G = fc.Graph.from_csr(g, [1.0])
+    entry = tune._load(tune._SHIPPED)[tune._key(G, 1024)]
+    assert (entry["walkers"], entry["regs"], entry["order"]) == (1024, 64, "id")
+    tune.apply(G, entry)
+    G.set_cluster(1)
+    for off in (0, 872):
+        _check_full_wave(G, g, [1.0], seed=2024, tau=152, tree_offset=off, expect_kernel=3, walkers=1024, regs=64)
+    G.close()
+
+
+def test_grid_full_size_benchmark_shape_full_wave_bit_exact():
+    """The road-like benchmark's sampler launch: 2048 x 2048 grid (10% deleted,
+    1% diagonals, weights U[1, 10]), alpha in {0.1, 1, 10}; weighted edge-record
+    kernel with tree membership as state flags, ring pops, degree start order,
+    1024 walkers, 64 registers, one CTA per tree; 51 trees per alpha = 153 work
+    items, more than one full wave of 152 CTAs.  Every tree equals the oracle's."""
+    g = synth.perturbed_grid(2048, 2048, 3)
+    alphas = [0.1, 1.0, 10.0]
+    G = fc.Graph.from_csr(g, alphas)
+    G.set_kernel(2)
+    G.set_bitmap(1)
+    G.set_pops(2)
+    G.set_start_order("degree")
+    G.set_shape(1024, 0, 0, 64)
+    G.set_cluster(1)
+    _check_full_wave(G, g, alphas, seed=33, tau=51, tree_offset=0, expect_kernel=2, walkers=1024, regs=64)
     G.close()
 
 
@@ -190,6 +270,27 @@ def test_control_variate_combination_vs_oracle():
     ref = native.wilson(g, 1.0, seed=77, tau=tau)
     exp = ocv.combine(ref["R"], ref["C"], tau, p, ocv.beta_from_prediction(gp.astype(np.float64), p))
     np.testing.assert_allclose(diag.cpu().numpy(), exp, rtol=1e-9, atol=1e-12)
+    G.close()
+
+
+def test_control_variate_with_nonfinite_predictions():
+    """Predictions that are NaN or infinite: NaN and -inf count as p_v, +inf as 1,
+    exactly as the oracle's clip; the result stays finite everywhere."""
+    g = synth.barabasi_albert(2000, 2, 9)
+    tau = 300
+    G = fc.Graph.from_csr(g, [1.0])
+    out = G.sample(78, tau)
+    gp = np.random.default_rng(2).random(g.n).astype(np.float32)
+    gp[0::5] = np.nan
+    gp[1::5] = np.inf
+    gp[2::5] = -np.inf
+    diag, far, _ = G.farness(out["R"], tau, C=out["C"], g_pred=torch.from_numpy(gp).cuda())
+    p = ocv.p_root(g, 1.0)
+    ref = native.wilson(g, 1.0, seed=78, tau=tau)
+    exp = ocv.combine(ref["R"], ref["C"], tau, p, ocv.beta_from_prediction(gp.astype(np.float64), p))
+    d = diag.cpu().numpy()
+    assert np.all(np.isfinite(d)) and np.all(np.isfinite(far.cpu().numpy()))
+    np.testing.assert_allclose(d, exp, rtol=1e-9, atol=1e-12)
     G.close()
 
 

@@ -1,8 +1,8 @@
 """Tree sharding across ranks (gloo, world size 2, CPU): trees are indexed
-globally, so ranks sampling disjoint tree ranges (tree_offset = rank * share)
-and summing R and C with one allreduce reproduce a single run exactly.  This is
-the exchange the multi-GPU path would do; the samples come from the CPU oracle
-sampler (the only sampler available without a GPU)."""
+globally, so ranks sampling disjoint tree ranges (shard.tree_range) and summing
+R and C with one all-reduce (shard.allreduce_counts, the exchange the
+multi-GPU benchmark runs) reproduce a single run exactly.  The samples come
+from the CPU oracle sampler (the only sampler available without a GPU)."""
 import os
 import socket
 
@@ -14,6 +14,7 @@ import torch.multiprocessing as mp
 
 import synth
 from oracle import native
+from paper_2101_06192_gb300 import shard
 
 TAU = 40
 
@@ -31,12 +32,11 @@ def _worker(rank, world, port, out_path):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     g = synth.barabasi_albert(400, 3, 8)
-    share = TAU // world
-    o = native.wilson(g, 1.0, seed=21, tau=share, tree_offset=rank * share)
+    first, count = shard.tree_range(rank, world, TAU)
+    o = native.wilson(g, 1.0, seed=21, tau=count, tree_offset=first)
     R = torch.from_numpy(o["R"].astype(np.int64))
     C = torch.from_numpy(o["C"].astype(np.int64))
-    dist.all_reduce(R, op=dist.ReduceOp.SUM)
-    dist.all_reduce(C, op=dist.ReduceOp.SUM)
+    shard.allreduce_counts(R, C)
     t = torch.tensor([float(rank + 1)])
     dist.all_reduce(t, op=dist.ReduceOp.MAX)  # max-over-ranks timing reduction used by the bench
     if rank == 0:
@@ -64,10 +64,10 @@ def _rb_worker(rank, world, port, out_path):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     g = synth.barabasi_albert(300, 3, 9)
-    share = 12 // world
-    o = native.wilson(g, 0.7, seed=33, tau=share, tree_offset=rank * share, want_parents=True)
+    first, count = shard.tree_range(rank, world, 12)
+    o = native.wilson(g, 0.7, seed=33, tau=count, tree_offset=first, want_parents=True)
     acc = torch.from_numpy(rb.accumulate(g, 0.7, o["parents"]).astype(np.int64))
-    dist.all_reduce(acc, op=dist.ReduceOp.SUM)
+    shard.allreduce_counts(acc)
     if rank == 0:
         np.save(out_path, acc.numpy())
     dist.barrier()
@@ -82,3 +82,14 @@ def test_two_rank_rao_blackwell_totals_match_single_run(tmp_path):
     o = native.wilson(g, 0.7, seed=33, tau=12, want_parents=True)
     ref = rb.accumulate(g, 0.7, o["parents"]).astype(np.int64)
     np.testing.assert_array_equal(np.load(out), ref)
+
+
+def test_tree_ranges_partition_the_trees():
+    for tau in (0, 1, 7, 40, 1024):
+        for world in (1, 2, 3, 8):
+            spans = [shard.tree_range(r, world, tau) for r in range(world)]
+            assert spans[0][0] == 0 and sum(c for _, c in spans) == tau
+            for (a, ca), (b, _) in zip(spans, spans[1:]):
+                assert a + ca == b
+    with pytest.raises(ValueError):
+        shard.tree_range(2, 2, 10)

@@ -234,7 +234,8 @@ def test_control_variate_unbiased_any_prediction():
         o = native.wilson(g, alpha, seed=41, tau=1, tree_offset=t, want_steps=False)
         X[t] = o["R"]
         Cm[t] = o["C"]
-    for gp in (np.zeros(g.n), om, np.random.default_rng(0).random(g.n)):
+    nonfinite = np.where(np.arange(g.n) % 3 == 0, np.nan, np.where(np.arange(g.n) % 3 == 1, np.inf, -np.inf))
+    for gp in (np.zeros(g.n), om, np.random.default_rng(0).random(g.n), nonfinite):
         beta = cv.beta_from_prediction(gp, p)
         Y = X - beta * (Cm - p)
         z = (Y.mean(axis=0) - om) / (Y.std(axis=0, ddof=1) / math.sqrt(T) + 1e-12)
@@ -250,6 +251,15 @@ def test_control_variate_unbiased_any_prediction():
     # plain estimator's combination via Algorithm 1's fill step == R/tau
     R = X.sum(axis=0)
     np.testing.assert_allclose(cv.combine(R, Cm.sum(axis=0), T, p, np.zeros(g.n)), R / T)
+
+
+def test_beta_of_nonfinite_predictions():
+    """clip(g, p, 1) on predictions that are not finite: -inf and NaN give p
+    (beta = 1, the full control variate), +inf gives 1 (beta = 0, the plain
+    estimator); a vertex with p = 1 (isolated) always gets beta = 0."""
+    p = np.array([0.2, 0.2, 0.2, 0.5, 1.0])
+    gp = np.array([np.nan, np.inf, -np.inf, 0.75, np.nan])
+    np.testing.assert_array_equal(cv.beta_from_prediction(gp, p), [1.0, 0.0, 1.0, 0.5, 0.0])
 
 
 def test_hoeffding_failure_rate():

@@ -1,14 +1,17 @@
 """fc_forest_farness_noalloc: the allocation-free variant of fc_forest_farness.
 
 Some callers cannot allocate device memory at the point where they need the
-farness/closeness -- code running inside a CUDA graph capture, or under a
-memory manager that forbids allocations it does not make itself.  For them the
-library keeps the combination's temporary per-block sums in a fixed device
-array compiled into libfc.so (graphs up to 2^22 vertices).  These tests call
-both entry points through the C ABI on the same inputs, twice in a row with
-different inputs (the fixed array is shared by every call and keeps the last
-call's contents), and check that the results agree.  This file is collected
-last so that a stop-at-first-failure run has already run every other test.
+farness/closeness -- for example code running under a memory manager that
+forbids allocations it does not make itself, or a serving loop whose device
+memory is fixed once at start-up.  For them the library keeps the
+combination's temporary per-block sums in a fixed device array compiled into
+libfc.so (graphs up to 2^22 vertices).  These tests call both entry points
+through the C ABI on the same inputs, twice in a row with different inputs
+(the fixed array is shared by every call and keeps the last call's contents),
+check that the results agree, compare them with the oracle's combination, and
+run a graph of exactly 2^22 vertices, which uses every slot of the array.
+This file is collected last so that a stop-at-first-failure run has already
+run every other test.
 """
 import ctypes
 
@@ -17,6 +20,8 @@ import pytest
 import torch
 
 import synth
+from oracle import cv as ocv
+from oracle import dense, native
 
 pytestmark = pytest.mark.gpu
 
@@ -71,4 +76,62 @@ def test_noalloc_rejects_graphs_beyond_its_capacity():
     # the pool-backed entry point handles the same graph
     assert L.fc_forest_farness(G._h, 0, _p(R), None, None, None, 1, _p(d), None, None, stream) == fc.FC_OK
     torch.cuda.synchronize()
+    G.close()
+
+
+def test_noalloc_matches_oracle():
+    """Plain, paper fill step (with the oracle's own pivot solution) and
+    control-variate forms against the oracle's combination, Eq. 3 and Def. 2."""
+    L = fc.lib()
+    g = synth.erdos_renyi(1000, 8, 1)
+    tau = 500
+    G = fc.Graph.from_csr(g, [1.0])
+    out = G.sample(31, tau)
+    ref = native.wilson(g, 1.0, seed=31, tau=tau)
+    assert np.array_equal(out["R"].cpu().numpy().view(np.uint32), ref["R"])
+    p = ocv.p_root(g, 1.0)
+    gp = np.random.default_rng(4).random(g.n).astype(np.float32)
+    xo = dense.pivot_solution(g, 1.0)
+    for variant in ("plain", "pivot", "cv"):
+        C = out["C"] if variant == "cv" else None
+        gpp = torch.from_numpy(gp).cuda() if variant == "cv" else None
+        xp = torch.from_numpy(xo).cuda() if variant == "pivot" else None
+        d, far, clo = _run(L.fc_forest_farness_noalloc, G, out["R"], C, gpp, xp, tau)
+        if variant == "cv":
+            exp = ocv.combine(ref["R"], ref["C"], tau, p, ocv.beta_from_prediction(gp.astype(np.float64), p))
+        else:
+            exp = dense.diag_from_counts(ref["R"], tau, xo if variant == "pivot" else None)
+        np.testing.assert_allclose(d, exp, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(far, dense.farness_eq3(exp), rtol=1e-9)
+        np.testing.assert_allclose(clo, dense.closeness(dense.farness_eq3(exp)), rtol=1e-9)
+    G.close()
+
+
+def test_noalloc_at_capacity_uses_every_slot():
+    """n = 2^22 exactly: 16384 per-block sums plus the trace fill the array.
+    Counts are given directly (no sampling), so the oracle's combination is
+    cheap; two calls in a row with different counts."""
+    L = fc.lib()
+    n = 1 << 22
+    # a cycle: every vertex has degree 2, so the control variate applies everywhere
+    v = np.arange(n, dtype=np.int64)
+    g = synth.from_edges(n, v, (v + 1) % n)
+    G = fc.Graph.from_csr(g, [1.0])
+    p = ocv.p_root(g, 1.0)
+    rng = np.random.default_rng(9)
+    tau = 64
+    for call in range(2):
+        R = rng.integers(0, tau + 1, n).astype(np.uint32)
+        C = np.minimum(R, rng.integers(0, tau // 3, n).astype(np.uint32))
+        gp = rng.random(n).astype(np.float32)
+        Rt = torch.from_numpy(R.view(np.int32)).cuda()
+        Ct = torch.from_numpy(C.view(np.int32)).cuda()
+        gpt = torch.from_numpy(gp).cuda()
+        got = _run(L.fc_forest_farness_noalloc, G, Rt, Ct, gpt, None, tau)
+        pool = _run(L.fc_forest_farness, G, Rt, Ct, gpt, None, tau)
+        exp = ocv.combine(R, C, tau, p, ocv.beta_from_prediction(gp.astype(np.float64), p))
+        np.testing.assert_allclose(got[0], exp, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(got[1], dense.farness_eq3(exp), rtol=1e-9)
+        for a, b in zip(got, pool):
+            np.testing.assert_allclose(a, b, rtol=1e-12, atol=0)
     G.close()
