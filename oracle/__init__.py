@@ -14,6 +14,9 @@ Approximation Algorithms for Forest Closeness Centrality", arXiv 2101.06192):
   cg.py           FP64 CG ground truth (Sec. 6.1).
   cv.py           control-variate combination (not in the paper).
   mlp.py          FP64 forward/backward/Adam of the control-variate network.
+  electrical.py   electrical closeness on G (Sec. 3, Eq. 2): L^+, effective
+                  resistance, the UST path-sum estimator along a BFS tree.
+  wilson_oracle.c also: Wilson on G rooted at a vertex (Sec. 3 insight (iii)).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA path.
@@ -21,4 +24,4 @@ Every function is pinned by ``tests/test_oracle_*.py`` against facts the paper
 and the mathematics fix (closed forms, brute force, invariants, library
 routines); see the pins listed there.
 """
-from . import cg, cv, dense, enumerate, mlp, native  # noqa: F401
+from . import cg, cv, dense, electrical, enumerate, mlp, native  # noqa: F401

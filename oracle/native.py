@@ -50,6 +50,9 @@ def lib():
         L.orc_stack_entries.argtypes = [ctypes.c_int32, P, P, P, ctypes.c_double, ctypes.c_uint32,
                                         ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, P, P, P]
         L.orc_stack_entries.restype = ctypes.c_int
+        L.orc_wilson_rooted.argtypes = [ctypes.c_int32, P, P, P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64,
+                                        ctypes.c_int64, P, P, P]
+        L.orc_wilson_rooted.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -113,3 +116,22 @@ def wilson(g, alpha, seed: int, tau: int, tree_offset: int = 0, alpha_idx: int =
     if rc != 0:
         raise MemoryError("oracle sampler allocation failed")
     return {"R": R, "C": C, "parents": parents, "steps": steps}
+
+
+def wilson_rooted(g, root: int, seed: int, tau: int, tree_offset: int = 0, order=None,
+                  want_parents: bool = True, want_steps: bool = True):
+    """Sequential Wilson sampler on G rooted at ``root`` (uniform spanning trees
+    of G, walks with probability w_vj / d_w(v)).  Returns dict with parents
+    ([tau, n], the root's entry n) and steps ([tau], departures)."""
+    n = g.n
+    parents = np.empty((tau, n), dtype=np.int32) if want_parents else None
+    steps = np.zeros(tau, dtype=np.uint64) if want_steps else None
+    w = None if g.w is None else np.ascontiguousarray(g.w, dtype=np.float32)
+    order_arr = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
+    rc = lib().orc_wilson_rooted(n, _ptr(g.rowptr), _ptr(g.colidx), _ptr(w), int(root), int(seed) & (2**64 - 1),
+                                 int(tree_offset), int(tau), _ptr(order_arr), _ptr(parents), _ptr(steps))
+    if rc == -2:
+        raise ValueError("wilson_rooted: the graph is not connected")
+    if rc != 0:
+        raise MemoryError("oracle sampler allocation failed")
+    return {"parents": parents, "steps": steps}

@@ -273,3 +273,121 @@ int orc_stack_entries(int32_t n, const int64_t* rowptr, const int32_t* colidx, c
     free(S);
     return 0;
 }
+
+/*
+ * Wilson's algorithm on G itself, rooted at the vertex `root` (the uniform
+ * spanning trees of G that the electrical-closeness algorithm samples, Sec. 3
+ * insight (iii); Algorithm 2 with T = {root} at the start).  G must be
+ * connected.  The walk at v leaves to neighbour j with probability
+ * w_vj / d_w(v); stack entry k of v in tree t is Philox4x32-10 with
+ * counter = (k, v, t_global, 0), key = (seed_lo, seed_hi), and
+ *   unweighted: neighbour floor(o2 * d / 2^32) of v's row;
+ *   weighted:   x = fl(U * S_d), clamped below S_d (U as above, S_j the
+ *               row's FP64 weight prefix); the first j with x < S_j.
+ * Outputs (each may be NULL):
+ *   parents [tau][n]: the next vertex on v's tree path to the root; the root's
+ *           entry is n (the root, seen as the only vertex joined to an
+ *           outside vertex n)
+ *   steps   [tau]: stack entries consumed (departures; the root makes none)
+ * Returns 0, -1 on allocation failure, -2 if a walk meets a vertex without
+ * neighbours (G not connected).
+ */
+static int32_t stack_entry_rooted(const orc_graph* g, int32_t v, uint32_t k, uint32_t tg) {
+    uint32_t ctr[4] = {k, (uint32_t)v, tg, 0u};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, g->key, o);
+    const int64_t b = g->rowptr[v];
+    const int64_t d = g->rowptr[v + 1] - b;
+    int64_t j;
+    if (g->S == NULL) {
+        j = (int64_t)(((uint64_t)o[2] * (uint64_t)d) >> 32);
+    } else {
+        const uint64_t u53 = ((uint64_t)o[0] << 21) | (uint64_t)(o[1] >> 11);
+        const double U = (double)u53 * 0x1.0p-53;
+        const double t_last = g->S[b + d - 1];
+        double x = U * t_last;
+        if (x >= t_last) x = below(t_last);
+        j = d - 1;
+        for (int64_t i = 0; i < d; ++i) {
+            if (x < g->S[b + i]) { j = i; break; }
+        }
+    }
+    return g->colidx[b + j];
+}
+
+int orc_wilson_rooted(int32_t n, const int64_t* rowptr, const int32_t* colidx, const float* w, int32_t root,
+                      uint64_t seed, int64_t tree_offset, int64_t tau, const int32_t* order_in,
+                      int32_t* parents, uint64_t* steps) {
+    orc_graph g;
+    g.n = n; g.rowptr = rowptr; g.colidx = colidx; g.alpha = 1.0; g.alpha_idx = 0;
+    g.alpha_v = NULL;
+    g.key[0] = (uint32_t)seed; g.key[1] = (uint32_t)(seed >> 32);
+    g.S = NULL;
+    double* S = NULL;
+    if (w != NULL) {
+        S = (double*)malloc(sizeof(double) * (size_t)(rowptr[n] > 0 ? rowptr[n] : 1));
+        if (!S) return -1;
+        orc_row_prefix(n, rowptr, w, S);
+        g.S = S;
+    }
+    int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    uint8_t* in_tree = (uint8_t*)malloc((size_t)n + 1);
+    int32_t* next = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    uint32_t* cnt = (uint32_t*)malloc(sizeof(uint32_t) * ((size_t)n + 1));
+    if (!order || !in_tree || !next || !cnt) {
+        free(S); free(order); free(in_tree); free(next); free(cnt);
+        return -1;
+    }
+    if (order_in) memcpy(order, order_in, sizeof(int32_t) * (size_t)n);
+    else ascending_degree_order(n, rowptr, order);
+    int rc = 0;
+    /* connectivity: breadth-first search from the root (order[] as the queue
+       is overwritten below only after the check) */
+    {
+        int32_t* q = (int32_t*)next; /* n + 1 slots */
+        int64_t head = 0, tail = 0, seen = 1;
+        memset(in_tree, 0, (size_t)n + 1);
+        in_tree[root] = 1;
+        q[tail++] = root;
+        while (head < tail) {
+            const int32_t x = q[head++];
+            for (int64_t e = rowptr[x]; e < rowptr[x + 1]; ++e) {
+                const int32_t y = colidx[e];
+                if (!in_tree[y]) { in_tree[y] = 1; q[tail++] = y; ++seen; }
+            }
+        }
+        if (seen != n) rc = -2;
+    }
+    for (int64_t t = 0; t < tau && rc == 0; ++t) {
+        const uint32_t tg = (uint32_t)(tree_offset + t);
+        memset(in_tree, 0, (size_t)n + 1);
+        memset(cnt, 0, sizeof(uint32_t) * ((size_t)n + 1));
+        in_tree[root] = 1; /* T = {root} */
+        next[root] = n;
+        for (int32_t i = 0; i < n && rc == 0; ++i) {
+            const int32_t s = order[i];
+            int32_t u = s;
+            while (!in_tree[u]) {
+                if (rowptr[u + 1] == rowptr[u]) { rc = -2; break; }
+                next[u] = stack_entry_rooted(&g, u, cnt[u], tg);
+                cnt[u]++;
+                u = next[u];
+            }
+            u = s;
+            while (rc == 0 && !in_tree[u]) {
+                in_tree[u] = 1;
+                u = next[u];
+            }
+        }
+        if (parents) {
+            for (int32_t v = 0; v < n; ++v) parents[t * (int64_t)n + v] = next[v];
+        }
+        if (steps) {
+            uint64_t s = 0;
+            for (int32_t v = 0; v < n; ++v) s += cnt[v];
+            steps[t] = s;
+        }
+    }
+    free(S); free(order); free(in_tree); free(next); free(cnt);
+    return rc;
+}
