@@ -55,14 +55,20 @@ def parse():
     ap.add_argument("--no-tte", action="store_true",
                     help="leave out the time-to-eps study (R-MAT 22, learned control variate vs plain) that the "
                          "default run appends to its line")
-    ap.add_argument("--workload", choices=["ba", "cv", "grid", "batch", "rb", "group", "roots"], default="ba",
+    ap.add_argument("--workload", choices=["ba", "cv", "grid", "batch", "rb", "group", "roots", "electrical"],
+                    default="ba",
                     help="ba: the benchmark line; cv: time to eps = 0.1, learned control variate vs "
                          "plain (R-MAT scale 22); grid: 2048^2 road-like grid, three alphas in one launch; "
                          "batch: 4096 uneven graphs in one launch; rb: Rao-Blackwellised accumulation of "
                          "32 sampled trees of R-MAT (--rmat-scale); group: greedy group forest closeness "
                          "(Algorithm 3) on a weighted BA graph of --group-n vertices, --group-k members; "
                          "roots: forest roots and depths of 152 sampled trees of BA 2^20 plus root counts "
-                         "for 64 query vertices (Omega columns)")
+                         "for 64 query vertices (Omega columns); electrical: electrical closeness on G (BA 2^20 "
+                         "rooted at its hub, --el-trees trees)")
+    ap.add_argument("--el-trees", type=int, default=1024)
+    ap.add_argument("--el-order", default="bfs_reverse", choices=["bfs", "bfs_reverse", "id", "id_desc"],
+                    help="start order of the rooted sampler (default: the reverse of the root's breadth-first "
+                         "order, the library's automatic choice)")
     ap.add_argument("--group-n", type=int, default=16384)
     ap.add_argument("--group-k", type=int, default=64)
     ap.add_argument("--graphs", type=int, default=4096)
@@ -798,9 +804,116 @@ def run_roots(args):
     print(json.dumps(line), flush=True)
 
 
+def run_electrical(args):
+    """Electrical closeness on G (Sec. 3 insights (i)-(iii), Eq. 2): BA n = 2^20,
+    m = 8 rooted at its largest hub; one step = build G rooted at the pivot
+    (with its BFS tree), sample tau spanning trees with their parents, the
+    Kirchhoff path sums (fc_resistance_accumulate), the pivot column of L^+
+    (fc_laplacian_solve) and the combination (fc_electrical_closeness)."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2101_06192_gb300 import fc
+    torch.cuda.set_device(0)
+    g = synth.barabasi_albert(1 << args.n_log2, BA_M, BA_SEED)
+    root = int(np.argmax(g.degrees()))
+    tau = args.el_trees
+    n = g.n
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    e = torch.zeros(n, dtype=torch.float64, device="cuda")
+    e[root] = 1.0
+    out = {}
+
+    def step(seed, ev=None):
+        G = fc.Graph.rooted(g, root)
+        if args.el_order != "bfs_reverse":
+            # on a rooted graph the order array holds the breadth-first order
+            G.set_start_order({"bfs": 0, "id": 2, "id_desc": 3}[args.el_order])
+        if ev:
+            ev[0].record(stream)
+        o = G.sample(seed, tau, want_parents=True, with_C=False)
+        if ev:
+            ev[1].record(stream)
+        acc = G.resistance_accumulate(o["parents"][0])
+        if ev:
+            ev[2].record(stream)
+        x, it = G.laplacian_solve(e, rel_tol=1e-9)
+        if ev:
+            ev[3].record(stream)
+        r, d, far, clo = G.electrical_closeness(acc, tau, x)
+        out.update(diag=d, iters=it, depth=int(G.bfs_tree()[1].max().item()), stats=G.sampler_stats())
+        G.close()
+        return clo
+
+    for i in range(args.warmup):
+        step(100 + i)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    tot, parts = [], []
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        evs[0].record(stream)
+        step(200 + i, ev=evs[1:5])
+        evs[5].record(stream)
+        torch.cuda.synchronize()
+        tot.append(evs[0].elapsed_time(evs[5]))
+        parts.append([evs[k].elapsed_time(evs[k + 1]) for k in range(5)])
+    clk = clocks.stop()
+    ms = statistics.mean(tot)
+    pm = [statistics.mean(p[k] for p in parts) for k in range(5)]
+    # accuracy: L^+[v, v] of reference vertices by Laplacian solves (exact to 1e-10)
+    J = reference_vertices(g, 64, 7)
+    Gj = fc.Graph.rooted(g, root)
+    B = torch.zeros(J.size, n, dtype=torch.float64, device="cuda")
+    Jt = torch.from_numpy(J).cuda()
+    B[torch.arange(J.size, device="cuda"), Jt] = 1.0
+    X, _ = Gj.laplacian_solve(B, rel_tol=1e-10)
+    exact = X[torch.arange(J.size, device="cuda"), Jt]
+    depth_sum = float(Gj.bfs_tree()[1].to(torch.float64).sum().item())
+    Gj.close()
+    err = (out["diag"][Jt] - exact).abs()
+    peaks, peak_kind = load_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    # algorithmic bytes of the path sums: parents read once (4 B per tree and
+    # vertex) and, per tree and breadth-first step, the parent of the edge's
+    # upper end (4 B); totals 8 B per vertex per chunk of 32 trees
+    acc_bytes = 4.0 * tau * n + 4.0 * tau * depth_sum + 8.0 * n * math.ceil(tau / 32)
+    acc_s = pm[2] / 1000.0
+    line = {
+        "metric": "USTs/s (electrical closeness on G)", "value": tau / (ms / 1000.0), "unit": "trees/s",
+        "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+        "dtype": "u32/i64 fixed point/f64", "data": "synthetic",
+        "config": {"workload": f"BA n=2^{args.n_log2} m={BA_M} (seed {BA_SEED}) rooted at its largest hub "
+                               f"(degree {int(g.degrees()[root])}), {tau} trees/step",
+                   "start_order": args.el_order,
+                   "n": n, "m_edges": g.m, "root": root, "bfs_depth_max": out["depth"],
+                   "bfs_depth_mean": depth_sum / n,
+                   "l2": "flushed before every timed step (512 MB write)"},
+        "ms_build": pm[0], "ms_sample": pm[1], "ms_accumulate": pm[2], "ms_solve": pm[3], "ms_combine": pm[4],
+        "cg_iterations": out["iters"],
+        "departures_per_step": out["stats"][1],
+        "accuracy": {"reference_vertices": int(J.size), "max_abs_err_diag_Lplus": float(err.max()),
+                     "mean_abs_err": float(err.mean())},
+        "roofline": {"bound": "hbm", "kernel": "k_rb<1> (resistance path sums)",
+                     "achieved": acc_bytes / acc_s / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": acc_bytes / acc_s / 1e9 / peak, "algorithmic_bytes": acc_bytes,
+                     "peak_source": peak_kind, "traffic": None},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.workload == "electrical":
+        if rank == 0:
+            run_electrical(args)
+        return
     if args.workload == "roots":
         if rank == 0:
             run_roots(args)

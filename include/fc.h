@@ -224,7 +224,8 @@ fc_status fc_sampler_last_shape(const fc_graph* g, int32_t* walkers_per_tree, in
  *   steps_out uint64[n_alpha * tau] stack entries consumed by each tree
  *            (= departures of the sequential algorithm) -- optional
  * max_steps_per_tree: watchdog on the iterations of each walker (0 = default
- * 8 n + 2^20); exceeding it aborts the launch with FC_ETIMEOUT.
+ * 8 n + 2^20; graphs from fc_build_rooted: 2^26 + 64 n, since walks on G have
+ * a single exit); exceeding it aborts the launch with FC_ETIMEOUT.
  * Requires tau >= 0, tree_offset >= 0, tree_offset + tau <= 2^32.
  * Synchronises `stream` (reads the device error word).
  */
@@ -446,6 +447,107 @@ fc_status fc_tree_roots(const int32_t* parents, int32_t n, int64_t T, int32_t* r
  */
 fc_status fc_root_counts(const int32_t* roots, int32_t n, int64_t T, const int32_t* queries, int32_t k,
                          uint32_t* counts, void* stream);
+
+/*
+ * ---- Electrical closeness on G (Sec. 3) --------------------------------------
+ * The paper's forest algorithm transfers an algorithm for diag(L^+) of a
+ * connected graph G to G*; that algorithm rests on three facts (Sec. 3):
+ * (i) the electrical closeness of u needs only L^+[u, u] and tr(L^+); (ii)
+ * one Laplacian solve gives the column x = L^+ e_u of a pivot u, and with the
+ * effective resistances r(u, v) Eq. 2 gives every diagonal entry,
+ *   L^+[v, v] = r(u, v) - x[u] + 2 x[v];
+ * (iii) r(u, v) is estimated from uniform spanning trees of G (Kirchhoff).
+ * Electrical farness and closeness follow Def. 2 with r in place of the
+ * forest distance: farness(v) = sum_w r(v, w) = n L^+[v, v] + tr(L^+),
+ * closeness(v) = n / farness(v).  The calls below are that pipeline:
+ *   fc_build_rooted -> fc_sample_usts -> fc_resistance_accumulate
+ *   -> fc_laplacian_solve -> fc_electrical_closeness.
+ */
+
+/*
+ * Build G (not G*) for uniform spanning trees rooted at the pivot `root`:
+ * Wilson's walks on G leave v to neighbour j with probability w_vj / d_w(v)
+ * and have the root as their only exit.  The graph is represented like G*
+ * with u* joined to the root alone, so fc_sample_usts on it samples trees
+ * whose parent arrays hold the root's parent as n and a uniform spanning tree
+ * of G (probability proportional to the product of its edge weights) on the
+ * other vertices; R counts the root in every tree, C is meaningless.
+ * Random stacks (fc_sample_usts, alpha index 0): entry k of v != root with
+ * Philox words o0..o3, u53 and U as in fc_build_augmented:
+ *   unweighted: neighbour floor(o2 d / 2^32);
+ *   weighted:   x = fl(U S_d), clamped below S_d; the first j with x < S_j
+ *               (S_j the FP64 left-to-right prefix of the row's weights);
+ * the root's every entry goes to n.  steps_out counts the root's one step.
+ * Also builds the root's breadth-first tree (the fixed paths of the resistance
+ * estimator): the parent of v is its smallest-id neighbour one level closer
+ * to the root.  The sampler's automatic choices differ from G*'s because
+ * walks on G are long and cross each other: start vertices in the reverse of
+ * that tree's breadth-first order (fc_set_start_order: 1 selects it, 0 the
+ * breadth-first order itself), at most 128 walkers per tree, and tree
+ * membership as state flags (several CTAs per SM); as for every launch
+ * shape and order, the trees do not depend on them.
+ * CSR contract as fc_build_augmented; n >= 2, 0 <= root < n;
+ * FC_EINVAL if G is not connected (electrical closeness is defined on
+ * connected graphs).  Synchronises `stream`.
+ */
+fc_status fc_build_rooted(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx, const float* w,
+                          int32_t root, uint32_t flags, void* stream, fc_graph** out);
+
+/*
+ * The root's breadth-first tree of a graph from fc_build_rooted: parent_out
+ * int32 device [n] (-1 at the root), depth_out int32 device [n] (either may
+ * be NULL).  Asynchronous.
+ */
+fc_status fc_bfs_tree(const fc_graph* g, int32_t* parent_out, int32_t* depth_out, void* stream);
+
+/*
+ * Effective-resistance path sums (Sec. 3 insight (iii); Kirchhoff's current
+ * theorem).  For each of the T trees in parents (device int32 [T][n], as
+ * written by fc_sample_usts on a graph from fc_build_rooted: the root's entry
+ * n, every other entry a neighbour), and every vertex v, with
+ * (x, b(x)) the edges of v's path in the breadth-first tree from v to the root:
+ *   S_T(v) = sum over that path, from v upward, of
+ *            ( [tree parent of x is b(x), x ancestor-or-self of v in the tree]
+ *            - [tree parent of b(x) is x, b(x) ancestor-or-self of v] ) / w(x, b(x))
+ * (E[S_T(v)] = r(root, v): the tree path from v to the root crosses an edge
+ * a -> b with a probability whose net value is the unit current from v to the
+ * root on that edge).  S_T(v) is summed in FP64 in path order, one rounding
+ * per addition, 1 / w one FP64 division of the FP32 weight; acc[v] (device
+ * int64 [n], caller-owned, accumulates) += floor(S_T(v) 2^32 + 1/2), so
+ * totals do not depend on the order of the trees.  Work per tree: the sum of
+ * the vertices' depths in the breadth-first tree.  FC_EINVAL for a graph not
+ * from fc_build_rooted or parent arrays that are not spanning trees of G
+ * rooted at the root.  Allocates temporary device memory.  Synchronous.
+ */
+fc_status fc_resistance_accumulate(fc_graph* g, const int32_t* parents, int64_t T, int64_t* acc, void* stream);
+
+/*
+ * x_j = L^+ b_j for n_rhs right-hand sides on a graph from fc_build_rooted
+ * (L the Laplacian of the connected G): b is projected onto the complement
+ * of span(1), L x = b solved by fc_solve's CG (Jacobi preconditioner d_w,
+ * FP32 inner / FP64 residual and refinement to rel_tol), and x shifted to
+ * zero mean.  b, x: FP64 device [n_rhs * n], column j at offset j*n; x is
+ * the initial guess.  FC_ENOCONV after max_iter inner iterations (best x
+ * kept).  With b = e_root this is the pivot column of insight (ii).
+ * Allocates temporary device memory.  Synchronises `stream`.
+ */
+fc_status fc_laplacian_solve(fc_graph* g, const double* b, double* x, int32_t n_rhs, double rel_tol,
+                             int32_t max_iter, int32_t* iters_out, void* stream);
+
+/*
+ * Electrical closeness from T trees' resistance totals acc (from
+ * fc_resistance_accumulate) and the pivot column x_pivot = L^+ e_root (device
+ * double [n], fc_laplacian_solve), FP64 throughout:
+ *   r^(root, v) = acc[v] / (2^32 T)                       -> resist_out
+ *   L^+[v, v]   = r^ - x[root] + 2 x[v]     (Eq. 2)       -> diag_out
+ *   farness_v   = n L^+[v, v] + sum_w L^+[w, w]           -> farness_out
+ *   closeness_v = n / farness_v             (Def. 2)      -> closeness_out
+ * Outputs device double [n]; all but diag_out may be NULL.  T >= 1.
+ * Allocates temporary device memory.  Asynchronous.
+ */
+fc_status fc_electrical_closeness(fc_graph* g, const int64_t* acc, int64_t T, const double* x_pivot,
+                                  double* resist_out, double* diag_out, double* farness_out, double* closeness_out,
+                                  void* stream);
 
 /*
  * Top-k ranking (Sec. 6.1): the k vertices with the smallest diag values

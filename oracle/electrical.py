@@ -86,27 +86,29 @@ def electrical_closeness(farness: np.ndarray) -> np.ndarray:
 def bfs_tree(g, root: int):
     """(parent, depth): breadth-first levels from root; the parent of v != root
     is its smallest-id neighbour one level closer (root: -1; unreachable
-    vertices: parent -1 and depth -1)."""
+    vertices: parent -1 and depth -1).  Frontiers as numpy arrays."""
     n = g.n
+    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(g.rowptr))
+    dst = g.colidx.astype(np.int64)
     depth = np.full(n, -1, dtype=np.int64)
     depth[root] = 0
-    frontier = [root]
-    while frontier:
-        nxt = []
-        for x in frontier:
-            for e in range(g.rowptr[x], g.rowptr[x + 1]):
-                y = int(g.colidx[e])
-                if depth[y] < 0:
-                    depth[y] = depth[x] + 1
-                    nxt.append(y)
-        frontier = nxt
+    frontier = np.array([root], dtype=np.int64)
+    level = 0
+    while frontier.size:
+        # every neighbour of the frontier not yet reached joins the next level
+        rows = [dst[g.rowptr[x]:g.rowptr[x + 1]] for x in frontier] if frontier.size < 64 else None
+        nb = np.concatenate(rows) if rows is not None else dst[np.isin(src, frontier)]
+        nb = np.unique(nb[depth[nb] < 0])
+        level += 1
+        depth[nb] = level
+        frontier = nb
     parent = np.full(n, -1, dtype=np.int64)
-    for v in range(n):
-        if v == root or depth[v] < 0:
-            continue
-        cands = [int(g.colidx[e]) for e in range(g.rowptr[v], g.rowptr[v + 1])
-                 if depth[int(g.colidx[e])] == depth[v] - 1]
-        parent[v] = min(cands)
+    closer = (depth[src] > 0) & (depth[dst] == depth[src] - 1)
+    big = np.iinfo(np.int64).max
+    best = np.full(n, big, dtype=np.int64)
+    np.minimum.at(best, src[closer], dst[closer])
+    has = best != big
+    parent[has] = best[has]
     return parent, depth
 
 
@@ -118,11 +120,17 @@ def edge_weight(g, a: int, b: int) -> float:
 
 
 def bfs_inverse_weights(g, bpar) -> np.ndarray:
-    """1 / w(v, b(v)) in FP64 (0 for the root)."""
+    """1 / w(v, b(v)) in FP64 (0 for the root), one FP64 division of the FP32
+    weight converted to FP64 (1 for unweighted graphs)."""
+    bpar = np.asarray(bpar, dtype=np.int64)
     inv = np.zeros(g.n)
-    for v in range(g.n):
-        if bpar[v] >= 0:
-            inv[v] = 1.0 / np.float64(np.float32(edge_weight(g, v, int(bpar[v]))))
+    has = bpar >= 0
+    if g.w is None:
+        inv[has] = 1.0
+        return inv
+    src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.rowptr))
+    hit = g.colidx.astype(np.int64) == bpar[src]  # the CSR entry (v, b(v)) of each row
+    inv[src[hit]] = 1.0 / g.w[hit].astype(np.float64)
     return inv
 
 
@@ -175,6 +183,32 @@ def path_sums(g, root: int, bpar, binv, parent: np.ndarray) -> np.ndarray:
             x = b
         out[v] = s
     return out
+
+
+def path_sums_np(g, root: int, bpar, binv, parent: np.ndarray) -> np.ndarray:
+    """path_sums with the walk along the BFS paths taken for all vertices at
+    once (numpy, same FP64 additions in the same order per vertex; a zero
+    term leaves s unchanged exactly).  For large graphs."""
+    n = g.n
+    tin, size = tree_intervals(parent, root)
+    bpar = np.asarray(bpar, dtype=np.int64)
+    parent = np.asarray(parent, dtype=np.int64)
+    tv = tin
+    x = np.arange(n, dtype=np.int64)
+    s = np.zeros(n)
+    live = x != root
+    while live.any():
+        xs = x[live]
+        b = bpar[xs]
+        tvl = tv[live]
+        up = (parent[xs] == b) & (tin[xs] <= tvl) & (tvl < tin[xs] + size[xs])
+        bb = np.where(b == root, 0, b)
+        down = (b != root) & (parent[bb] == xs) & (tin[bb] <= tvl) & (tvl < tin[bb] + size[bb])
+        c = up.astype(np.float64) - down.astype(np.float64)
+        s[live] = s[live] + c * binv[xs]
+        x[live] = b
+        live = x != root
+    return s
 
 
 def fixed_point(values: np.ndarray) -> np.ndarray:

@@ -274,34 +274,40 @@ __global__ void k_iota_keys(int32_t n, const int32_t* __restrict__ deg, uint32_t
 
 // ---------------------------------------------------------------------------
 // Selector thresholds for one alpha.
-//   T_v = count_below(1, t_v): stack entries selecting u* (slot 0),
+//   T_v = count_below(gamma, t_v): stack entries selecting u* (slot 0),
 //   B_e = count_below(t_j, t_v) for the entry e of slot j (weighted rows),
-// with t_v = fl(1 + fl(alpha s_v)), s_v = d_v (unweighted) or d_w(v) (weighted).
+// with t_v = fl(gamma + fl(alpha s_v)), s_v = d_v (unweighted) or d_w(v)
+// (weighted), t_j = fl(gamma + fl(alpha S_j)).  gamma = 1 on G* (the edge to
+// u*).  Walks on G rooted at a vertex (fc_build_rooted) take gamma = 0 and
+// alpha = 1 (no exit to u*, neighbours in proportion to w), except at the
+// root, whose every stack entry selects u* (T = 2^53): the sampled tree of
+// G* is then {root, u*} plus a uniform spanning tree of G rooted at the root.
 // ---------------------------------------------------------------------------
 __global__ void k_thr_vertex(int32_t n, double alpha_s, const double* __restrict__ alpha_v, bool weighted,
                              const int64_t* __restrict__ rowptr, const int32_t* __restrict__ deg,
-                             const double* __restrict__ dw, uint4* __restrict__ rowinfo) {
+                             const double* __restrict__ dw, double gamma, int32_t root,
+                             uint4* __restrict__ rowinfo) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     const double alpha = alpha_v ? alpha_v[v] : alpha_s;
     const int32_t d = deg[v];
-    const double t = deg_star(alpha, weighted ? dw[v] : (double)d);
-    const uint64_t T = count_below(1.0, t);
+    const double t = deg_gamma(gamma, alpha, weighted ? dw[v] : (double)d);
+    const uint64_t T = v == root ? TWO53 : count_below(gamma, t);
     rowinfo[v] = make_uint4((uint32_t)rowptr[v], (uint32_t)d, (uint32_t)T, (uint32_t)(T >> 32));
   }
 }
 
 __global__ void k_thr_nnz(int32_t n, double alpha_s, const double* __restrict__ alpha_v,
                           const int64_t* __restrict__ rowptr, const double* __restrict__ S,
-                          const double* __restrict__ dw, uint64_t* __restrict__ B) {
+                          const double* __restrict__ dw, double gamma, uint64_t* __restrict__ B) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t v = warp; v < n; v += nwarps) {
     const double alpha = alpha_v ? alpha_v[v] : alpha_s;
-    const double t = deg_star(alpha, dw[v]);
+    const double t = deg_gamma(gamma, alpha, dw[v]);
     for (int64_t e = rowptr[v] + lane; e < rowptr[v + 1]; e += 32)
-      B[e] = count_below(deg_star(alpha, S[e]), t);
+      B[e] = count_below(deg_gamma(gamma, alpha, S[e]), t);
   }
 }
 
@@ -395,10 +401,10 @@ __global__ void k_edge_records_w(int64_t nnz, const int32_t* __restrict__ colidx
   }
 }
 
-static void free_graph_arrays(fc_graph* g, cudaStream_t st) {
+void free_graph_arrays(fc_graph* g, cudaStream_t st) {
   void* ptrs[] = {g->rowptr, g->colidx, g->w, g->deg, g->dw, g->S, g->order, g->rowinfo, g->B, g->edges,
                   g->alphas_d, g->d_err, g->d_counter, g->d_stats, g->voff, g->gid, g->alpha_v,
-                  g->gorder, g->item_ns, g->t0_ns};
+                  g->gorder, g->item_ns, g->t0_ns, g->bpar, g->binv, g->bdepth};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, st);
   if (g->ws) cudaFree(g->ws);
@@ -450,9 +456,9 @@ extern "C" fc_status fc_release_scratch(void) {
     }                                                    \
   } while (0)
 
-static fc_status build_impl(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
-                            const float* w, const double* alphas, int32_t n_alpha, uint32_t flags, void* stream,
-                            fc_graph** out, int32_t G, const int64_t* voff_h, const double* galpha_h) {
+fc_status fcx::build_impl(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx, const float* w,
+                          const double* alphas, int32_t n_alpha, uint32_t flags, void* stream, fc_graph** out,
+                          int32_t G, const int64_t* voff_h, const double* galpha_h, int32_t root) {
   if (out == nullptr) return fcx::invalid("fc_build_augmented / fc_build_batch: null output pointer");
   *out = nullptr;
   if (n < 1 || n >= (1 << 30) || nnz < 0 || nnz >= (int64_t(1) << 32) || n_alpha < 1 || n_alpha > 64 ||
@@ -474,6 +480,7 @@ static fc_status build_impl(int32_t n, int64_t nnz, const int64_t* rowptr, const
   g->n_alpha = n_alpha;
   g->weighted = (w != nullptr);
   g->alphas.assign(alphas, alphas + n_alpha);
+  g->root = root;
   BUILD_CK(cudaGetDevice(&g->device));
   {
     size_t freeb = 0;
@@ -616,12 +623,13 @@ static fc_status build_impl(int32_t n, int64_t nnz, const int64_t* rowptr, const
   }
 
   for (int a = 0; a < n_alpha; ++a) {
+    const double gamma = root >= 0 ? 0.0 : 1.0;
     k_thr_vertex<<<grid_for(n, 256), 256, 0, st>>>(n, g->alphas[a], g->alpha_v, g->weighted, g->rowptr,
-                                                   g->deg, g->dw, g->rowinfo + (size_t)a * n);
+                                                   g->deg, g->dw, gamma, root, g->rowinfo + (size_t)a * n);
     BUILD_CK((fcx::note_launch(), cudaGetLastError()));
     if (g->weighted && nnz > 0) {
       k_thr_nnz<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(n, g->alphas[a], g->alpha_v, g->rowptr, g->S,
-                                                                g->dw, g->B + (size_t)a * nnz);
+                                                                g->dw, gamma, g->B + (size_t)a * nnz);
       BUILD_CK((fcx::note_launch(), cudaGetLastError()));
     }
   }
@@ -656,7 +664,7 @@ static fc_status build_impl(int32_t n, int64_t nnz, const int64_t* rowptr, const
 extern "C" fc_status fc_build_augmented(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
                                         const float* w, const double* alphas, int32_t n_alpha, uint32_t flags,
                                         void* stream, fc_graph** out) {
-  return build_impl(n, nnz, rowptr, colidx, w, alphas, n_alpha, flags, stream, out, 0, nullptr, nullptr);
+  return build_impl(n, nnz, rowptr, colidx, w, alphas, n_alpha, flags, stream, out, 0, nullptr, nullptr, -1);
 }
 
 extern "C" fc_status fc_build_batch(int32_t num_graphs, const int64_t* vertex_offsets, int64_t nnz,
@@ -681,7 +689,7 @@ extern "C" fc_status fc_build_batch(int32_t num_graphs, const int64_t* vertex_of
   }
   const double one = 1.0;
   return build_impl((int32_t)n, nnz, rowptr, colidx, w, &one, 1, flags, stream, out, num_graphs, vertex_offsets,
-                    graph_alphas);
+                    graph_alphas, -1);
 }
 
 extern "C" fc_status fc_graph_info(const fc_graph* g, int32_t* n, int64_t* nnz, int32_t* n_alpha,

@@ -37,6 +37,13 @@ void note_launch();
 // demand, reused across graphs and calls, released by fc_release_scratch.
 fc_status sampler_scratch(int device, size_t bytes, cudaStream_t st, void** out, bool capturing = false);
 
+// Graph construction shared by fc_build_augmented, fc_build_batch and
+// fc_build_rooted (root >= 0: walks on G whose only exit is that vertex).
+fc_status build_impl(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx, const float* w,
+                     const double* alphas, int32_t n_alpha, uint32_t flags, void* stream, fc_graph** out, int32_t G,
+                     const int64_t* voff_h, const double* galpha_h, int32_t root);
+void free_graph_arrays(fc_graph* g, cudaStream_t st);
+
 // Keep freed stream-ordered allocations in the device's default pool.
 void retain_pool(int device);
 
@@ -135,6 +142,12 @@ __device__ __forceinline__ double deg_star(double alpha, double s) {
   return __dadd_rn(1.0, __dmul_rn(alpha, s));
 }
 
+// t = fl(gamma + fl(alpha * s)): gamma = 1 on G* (the u* edge), 0 for walks
+// on G itself (fl(0 + s) = s exactly)
+__device__ __forceinline__ double deg_gamma(double gamma, double alpha, double s) {
+  return __dadd_rn(gamma, __dmul_rn(alpha, s));
+}
+
 }  // namespace fcx
 
 // ---------------------------------------------------------------------------
@@ -161,6 +174,13 @@ struct fc_graph {
   uint4* edges = nullptr;      // [n_alpha][nnz] edge records (single graphs; 64 bytes when weighted)
   double* alphas_d = nullptr;  // [n_alpha]
   int32_t max_deg = 0;
+  // G rooted at a pivot vertex (fc_build_rooted; -1 for G*): walks on G whose
+  // only exit is the pivot, and the pivot's breadth-first tree
+  int32_t root = -1;
+  int32_t* bpar = nullptr;     // [n] BFS parent (-1 at the root)
+  double* binv = nullptr;      // [n] 1 / w(v, bpar(v)) in FP64 (0 at the root)
+  int32_t* bdepth = nullptr;   // [n] BFS depth
+  int32_t max_bdepth = 0;
   // batch of graphs (block-diagonal union with one alpha per graph)
   int32_t num_graphs = 0;      // 0 = a single graph
   int64_t* voff = nullptr;     // [G+1] vertex offsets

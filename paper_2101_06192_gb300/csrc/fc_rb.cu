@@ -29,6 +29,22 @@
 // tree's weights in row order.  Every loop bound and every early exit is
 // read from global memory after a barrier, so all CTAs take the same path
 // through the barriers.
+//
+// The same kernel, in its second mode, aggregates the effective resistances
+// r(u, v) between a pivot u and every vertex v (Sec. 3, insight (iii)) from
+// uniform spanning trees of G rooted at u (sampled on a graph from
+// fc_build_rooted, whose trees are u* -> u -> ...).  Kirchhoff's current
+// theorem: a unit current from v to u puts current P(a->b) - P(b->a) on an
+// edge {a, b}, where P(a->b) is the probability that v's tree path to u
+// crosses it from a to b; summing current / w along any fixed path from v to
+// u (here v's path in a breadth-first tree B of u) gives r(u, v).  Per tree,
+//   S_T(v) = sum over the edges (x, b(x)) of v's B-path, from v upward, of
+//            ( [par_T(x) = b(x), x ancestor-or-self of v in T]
+//            - [par_T(b(x)) = x, b(x) ancestor-or-self of v in T] ) / w(x, b(x)),
+// summed in FP64 in path order and added in signed fixed point
+// floor(S_T(v) 2^32 + 1/2).  Ancestry uses the same preorder numbers and
+// subtree sizes; a warp takes a vertex and walks its B-path once for the
+// chunk's trees (one lane per tree, tree parents stored vertex-major).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -72,8 +88,15 @@ struct RBParams {
   uint32_t* bsum;             // [gridDim.x] block totals of the scan
   uint32_t* ctr;              // [2] error, [4..6] active counts of the jumping rounds, [7] chunk grabs (zeroed)
   const uint64_t* qtab;       // unweighted, one alpha: fixed-point value for each count of outside neighbours, or null
-
+  // resistance mode
+  int32_t root;               // the pivot u (the only child of u*), -1 in the diag(Omega) mode
+  const int32_t* bpar;        // [n] breadth-first parent of each vertex (-1 at the root)
+  const double* binv;         // [n] 1 / w(v, bpar(v))
+  int64_t* racc;              // [n] signed fixed-point totals of S_T(v)
+  int32_t* pvm;               // [n][Tc] tree parents, vertex-major
 };
+
+constexpr int RES_FRAC = 32;
 
 __device__ __forceinline__ uint32_t block_exscan_u32(uint32_t x, uint32_t* total, uint32_t* wsum) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -149,6 +172,8 @@ __device__ __forceinline__ unsigned long long jw_pack(int32_t anc, int32_t sum) 
 
 constexpr int RB_TILE = 256;  // vertices per tile of the vertex-major transpose
 
+// MODE 0: Rao-Blackwellised diag(Omega); MODE 1: effective resistances to the pivot.
+template <int MODE>
 __global__ void __launch_bounds__(RB_T, 5) k_rb(RBParams p) {
   cg::grid_group grid = cg::this_grid();
   __shared__ int32_t tile[RB_TMAX][RB_TILE + 1];
@@ -174,6 +199,8 @@ __global__ void __launch_bounds__(RB_T, 5) k_rb(RBParams p) {
     }
     const int32_t par = p.parents[(int64_t)t * n + v];
     if (par < 0 || par > n || par == v) atomicOr(&p.ctr[2], ERR_INVAL);
+    // a tree of G rooted at the pivot: the pivot, and only the pivot, hangs from u*
+    else if (MODE == 1 && ((par == n) != (v == p.root))) atomicOr(&p.ctr[2], ERR_INVAL);
     else if (par < n) atomicAdd(&p.cnt[(int64_t)t * n1 + par], 1u);  // u*'s children: a scan below
   }
   grid.sync();
@@ -341,12 +368,66 @@ __global__ void __launch_bounds__(RB_T, 5) k_rb(RBParams p) {
     for (int64_t k = threadIdx.x; k < k1; k += blockDim.x) {
       const int32_t x = (int32_t)(k / Tc), t = (int32_t)(k - (int64_t)x * Tc);
       p.tin[v0 * Tc + k] = tile[t][x];
-      if (p.w) p.sout[v0 * Tc + k] = 0.0;
-      else p.outc[v0 * Tc + k] = 0u;
+      if (MODE == 0) {
+        if (p.w) p.sout[v0 * Tc + k] = 0.0;
+        else p.outc[v0 * Tc + k] = 0u;
+      }
     }
     __syncthreads();
+    if (MODE == 1) {  // the tree parents, vertex-major, through the same tile
+      for (int t = 0; t < Tc; ++t)
+        for (int x = threadIdx.x; x < nv; x += blockDim.x) tile[t][x] = p.parents[(int64_t)t * n + v0 + x];
+      __syncthreads();
+      for (int64_t k = threadIdx.x; k < k1; k += blockDim.x) {
+        const int32_t x = (int32_t)(k / Tc), t = (int32_t)(k - (int64_t)x * Tc);
+        p.pvm[v0 * Tc + k] = tile[t][x];
+      }
+      __syncthreads();
+    }
   }
   grid.sync();
+
+  if (MODE == 1) {
+    // ---- path sums along the breadth-first tree: a warp per vertex, a lane
+    // per tree; the B-path is the same for every lane ----
+    const int32_t root = p.root;
+    for (int64_t v = gwarp; v < n; v += nwarps) {
+      const bool on = lane < Tc;
+      const int32_t tv = on ? p.tin[VT(lane, v)] : 0;
+      double s = 0.0;
+      int32_t x = (int32_t)v;
+      int32_t px = on ? p.pvm[VT(lane, x)] : -1;  // parent of x in this lane's tree
+      int32_t hops = 0;
+      while (x != root) {
+        const int32_t b = __ldg(p.bpar + x);
+        const double wi = __ldg(p.binv + x);
+        if (b < 0 || ++hops > n) {  // not a breadth-first tree of the root: never for fc_build_rooted graphs
+          atomicOr(&p.ctr[2], ERR_INVAL);
+          break;
+        }
+        const int32_t pb = (on && b != root) ? p.pvm[VT(lane, b)] : -1;  // parent of b
+        if (on) {
+          int c = 0;
+          if (px == b) {  // the tree crosses x -> b: on v's tree path iff x is an ancestor-or-self of v
+            const int32_t t0 = p.tin[VT(lane, x)];
+            if (t0 <= tv && tv < t0 + p.size[VT(lane, x)]) c = 1;
+          } else if (pb == x) {  // the tree crosses b -> x
+            const int32_t t0 = p.tin[VT(lane, b)];
+            if (t0 <= tv && tv < t0 + p.size[VT(lane, b)]) c = -1;
+          }
+          if (c != 0) s = __dadd_rn(s, c > 0 ? wi : -wi);
+        }
+        x = b;
+        px = pb;
+      }
+      long long q = 0;
+      if (on) q = (long long)floor(__dadd_rn(__dmul_rn(s, (double)(1ull << RES_FRAC)), 0.5));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      if (lane == 0 && q != 0) atomicAdd((unsigned long long*)&p.racc[v], (unsigned long long)q);
+    }
+    return;
+  }
 
   // ---- neighbours outside the subtree: a warp per row segment, a lane per
   // tree (each lane sums its tree's weights in row order; unweighted counts
@@ -466,27 +547,22 @@ __global__ void k_seg_fill(int32_t n, const uint32_t* __restrict__ cnt, const ui
 
 using namespace fcx;
 
-extern "C" fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int32_t* parents, int64_t T,
-                                      uint64_t* acc, void* stream) {
-  if (g == nullptr || parents == nullptr || acc == nullptr || T < 0 || alpha_idx < 0 ||
-      alpha_idx >= g->n_alpha) {
-    set_error("fc_rb_accumulate: bad argument");
-    return FC_EINVAL;
-  }
-  if (T == 0) return FC_OK;
-  cudaStream_t st = (cudaStream_t)stream;
+// Chunks of up to 32 trees through k_rb<mode>: mode 0 adds the
+// Rao-Blackwellised values to acc (uint64), mode 1 the path sums S_T(v) to
+// acc (int64).
+static fc_status tree_chunks(fc_graph* g, int mode, int32_t alpha_idx, const int32_t* parents, int64_t T, void* acc,
+                             cudaStream_t st, const char* who) {
   const int32_t n = g->n;
   int dev = g->device, nsm = 0, coop = 0, per_sm = 0;
   FC_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   FC_CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   if (!coop) {
-    set_error("fc_rb_accumulate: the device does not support cooperative launches");
+    set_error(std::string(who) + ": the device does not support cooperative launches");
     return FC_ECUDA;
   }
-  FC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rb, RB_T, 0));
+  const void* kern = mode == 0 ? (const void*)k_rb<0> : (const void*)k_rb<1>;
+  FC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RB_T, 0));
   const int grid = std::max(1, per_sm) * nsm;  // every CTA resident: required by the grid barriers
-  // trees per chunk: one per lane, 32 bytes of scratch per (tree, vertex), at
-  // most 4 GB and flat ids below 2^31
   // trees per chunk: one per lane, 44 bytes of scratch per (tree, vertex)
   // within a sixteenth of the device (1 to 16 GB), flat ids below 2^31
   const int64_t budget = std::max<int64_t>(1ll << 30, std::min<int64_t>(16ll << 30, (int64_t)(g->device_bytes / 16)));
@@ -512,7 +588,11 @@ extern "C" fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int3
   p.w = g->w;
   p.alpha = g->alphas[alpha_idx];
   p.alpha_v = g->num_graphs > 0 ? g->alpha_v : nullptr;
-  p.acc = acc;
+  p.acc = mode == 0 ? (uint64_t*)acc : nullptr;
+  p.racc = mode == 1 ? (int64_t*)acc : nullptr;
+  p.root = mode == 1 ? g->root : -1;
+  p.bpar = g->bpar;
+  p.binv = g->binv;
   p.cnt = (uint32_t*)carve(N1 * 4);
   p.word = (unsigned long long*)carve(N1 * 8);
   p.rsz = (uint32_t*)carve(N1 * 4);
@@ -521,10 +601,11 @@ extern "C" fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int3
   p.tin = (int32_t*)carve(N * 4);
   p.sout = (double*)carve(N * 8);  // the unweighted counts use its first half
   p.outc = (uint32_t*)p.sout;
+  p.pvm = (int32_t*)p.sout;        // resistance mode: the tree parents, vertex-major
   p.rsum = (uint32_t*)carve(N1 * 4);
   p.bsum = (uint32_t*)carve((size_t)grid * 4);
   p.ctr = (uint32_t*)carve(32);
-  const bool table = g->w == nullptr && g->num_graphs == 0;
+  const bool table = mode == 0 && g->w == nullptr && g->num_graphs == 0;
   uint64_t* qtab = table ? (uint64_t*)carve(((size_t)g->max_deg + 1) * 8) : nullptr;
   p.qtab = qtab;
   uint32_t* scnt = (uint32_t*)carve(((size_t)n + 1) * 4);
@@ -533,7 +614,7 @@ extern "C" fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int3
   ws = base;
   p.segs = segs;
   p.nseg = soff + n;
-  {
+  if (mode == 0) {  // row segments (the resistance mode reads no rows)
     const unsigned b = (unsigned)std::min<int64_t>(((int64_t)n + 256) / 256, (int64_t)nsm * 16);
     k_seg_count<<<b, 256, 0, st>>>(n, g->rowptr, g->w != nullptr, scnt);
     FC_LAUNCHED();
@@ -559,18 +640,44 @@ extern "C" fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int3
     FC_CK(cudaMemsetAsync(p.word, 0, (size_t)Tc * (n + 1) * 8, st));
     FC_CK(cudaMemsetAsync(p.ctr, 0, 32, st));
     void* args[] = {&p};
-    FC_CK(cudaLaunchCooperativeKernel((void*)k_rb, dim3(grid), dim3(RB_T), args, 0, st));
+    FC_CK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(RB_T), args, 0, st));
     FC_LAUNCHED();
     uint32_t herr = 0;
     FC_CK(cudaMemcpyAsync(&herr, p.ctr + 2, 4, cudaMemcpyDeviceToHost, st));
     FC_CK(cudaStreamSynchronize(st));
     if (herr != 0) {
-      set_error("fc_rb_accumulate: parents do not form spanning trees of G* rooted at u* = n");
+      set_error(std::string(who) + (mode == 0 ? ": parents do not form spanning trees of G* rooted at u* = n"
+                                              : ": parents do not form spanning trees of G rooted at the pivot"));
       status = FC_EINVAL;
     }
   }
   FC_CK(cudaFreeAsync(base, st));
   return status;
+}
+
+extern "C" fc_status fc_rb_accumulate(fc_graph* g, int32_t alpha_idx, const int32_t* parents, int64_t T,
+                                      uint64_t* acc, void* stream) {
+  if (g == nullptr || parents == nullptr || acc == nullptr || T < 0 || alpha_idx < 0 ||
+      alpha_idx >= g->n_alpha) {
+    set_error("fc_rb_accumulate: bad argument");
+    return FC_EINVAL;
+  }
+  if (T == 0) return FC_OK;
+  return tree_chunks(g, 0, alpha_idx, parents, T, acc, (cudaStream_t)stream, "fc_rb_accumulate");
+}
+
+extern "C" fc_status fc_resistance_accumulate(fc_graph* g, const int32_t* parents, int64_t T, int64_t* acc,
+                                              void* stream) {
+  if (g == nullptr || parents == nullptr || acc == nullptr || T < 0) {
+    set_error("fc_resistance_accumulate: bad argument");
+    return FC_EINVAL;
+  }
+  if (g->root < 0 || g->bpar == nullptr) {
+    set_error("fc_resistance_accumulate: needs a graph from fc_build_rooted");
+    return FC_EINVAL;
+  }
+  if (T == 0) return FC_OK;
+  return tree_chunks(g, 1, 0, parents, T, acc, (cudaStream_t)stream, "fc_resistance_accumulate");
 }
 
 extern "C" fc_status fc_rb_diag(const uint64_t* acc, int32_t n, int64_t T, double* diag_out, void* stream) {

@@ -1,5 +1,7 @@
 // Linear solves in A = I + alpha L (the matrix of the grounded pivot system of
-// Algorithm 1, and of the CG ground truth of Sec. 6.1).
+// Algorithm 1, and of the CG ground truth of Sec. 6.1), and in the Laplacian
+// L of a connected G itself (the pivot column of L^+ that the electrical-
+// closeness algorithm of Sec. 3 needs): A = sigma I + alpha L, sigma 1 or 0.
 //
 // Mixed precision: the outer loop is iterative refinement in FP64
 // (r = b - A x with FP64 x and FP64 arithmetic, x += correction); the
@@ -60,7 +62,7 @@ __device__ __forceinline__ float group_sumf(float v) {
 
 // ---- FP64 residual r = b - A x, partial sums of r.r and b.b ---------------
 __global__ void k_resid64(int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                          const float* __restrict__ w, const double* __restrict__ dw, double alpha,
+                          const float* __restrict__ w, const double* __restrict__ dw, double sigma, double alpha,
                           const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ r,
                           double* __restrict__ prr, double* __restrict__ pbb, int nb) {
   // blocks stride over the chunks of ROWS_PER_BLOCK rows; nb = gridDim.x partials per column
@@ -79,7 +81,7 @@ __global__ void k_resid64(int32_t n, const int64_t* __restrict__ rowptr, const i
     }
     acc = group_sum(acc);
     if (v < n && gl == 0) {
-      const double ax = x[off + v] * (1.0 + alpha * dw[v]) - alpha * acc;
+      const double ax = x[off + v] * (sigma + alpha * dw[v]) - alpha * acc;
       const double rv = b[off + v] - ax;
       r[off + v] = rv;
       rr += rv * rv;
@@ -229,9 +231,10 @@ __global__ void k_correct(int32_t n, const double* __restrict__ scal, const floa
     x[off + v] += (double)d[off + v] / sc[4];
 }
 
-__global__ void k_diag32(int32_t n, const double* __restrict__ dw, double alpha, float* __restrict__ diag32) {
+__global__ void k_diag32(int32_t n, const double* __restrict__ dw, double sigma, double alpha,
+                         float* __restrict__ diag32) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v < n) diag32[v] = (float)(1.0 + alpha * dw[v]);
+  if (v < n) diag32[v] = (float)(sigma + alpha * dw[v]);
 }
 
 __global__ void k_fill(int64_t len, double val, double* __restrict__ a) {
@@ -257,6 +260,41 @@ __global__ void k_partial_sum(int64_t len, const double* __restrict__ a, double*
   if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
+
+// Singular systems (sigma = 0, L of a connected graph): the residual's
+// component along 1 lies in L's kernel, where CG cannot reduce it; rounding
+// in the FP64 residual leaves a little there, so each refinement step
+// projects it out.  One block per column (fixed-order sums): r_j -= mean(r_j)
+// and rr[j] = |r_j|^2 after the projection.  il: element (v, j) at v m + j,
+// else at j n + v.
+__global__ void k_proj_mean(int32_t n, int m, bool il, double* __restrict__ r, double* __restrict__ rr) {
+  __shared__ double red[SV_T];
+  const int j = blockIdx.x;
+  auto at = [&](int64_t v) -> double& { return r[il ? (size_t)v * m + j : (size_t)j * n + v]; };
+  double s = 0.0;
+  for (int64_t v = threadIdx.x; v < n; v += SV_T) s += at(v);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = SV_T / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  const double mean = red[0] / (double)n;
+  __syncthreads();
+  double q = 0.0;
+  for (int64_t v = threadIdx.x; v < n; v += SV_T) {
+    const double x = at(v) - mean;
+    at(v) = x;
+    q += x * x;
+  }
+  red[threadIdx.x] = q;
+  __syncthreads();
+  for (int k = SV_T / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rr[j] = red[0];
+}
 
 // ---------------------------------------------------------------------------
 // Many right-hand sides (m >= 32): the solver's vectors interleaved by
@@ -306,7 +344,7 @@ __global__ void k_il_transpose(int64_t rows, int64_t cols, const double* __restr
 
 __global__ void __launch_bounds__(256) k_resid64_il(int32_t n, int m, const int64_t* __restrict__ rowptr,
                                                     const int32_t* __restrict__ colidx, const float* __restrict__ w,
-                                                    const double* __restrict__ dw, double alpha,
+                                                    const double* __restrict__ dw, double sigma, double alpha,
                                                     const double* __restrict__ b, const double* __restrict__ x,
                                                     double* __restrict__ r, double* __restrict__ prr,
                                                     double* __restrict__ pbb, int nb) {
@@ -320,7 +358,7 @@ __global__ void __launch_bounds__(256) k_resid64_il(int32_t n, int m, const int6
       for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e)
         acc += (w ? (double)w[e] : 1.0) * x[(size_t)colidx[e] * m + j];
       const size_t i = (size_t)v * m + j;
-      const double rv = b[i] - (x[i] * (1.0 + alpha * dw[v]) - alpha * acc);
+      const double rv = b[i] - (x[i] * (sigma + alpha * dw[v]) - alpha * acc);
       r[i] = rv;
       rr += rv * rv;
       bb += b[i] * b[i];
@@ -437,7 +475,8 @@ __global__ void __launch_bounds__(256) k_correct_il(int32_t n, int m, const doub
 using namespace fcx;
 
 static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, double* x, int32_t n_rhs,
-                            double rel_tol, int32_t max_iter, int32_t* iters_out, cudaStream_t st, bool jacobi) {
+                            double rel_tol, int32_t max_iter, int32_t* iters_out, cudaStream_t st, bool jacobi,
+                            double sigma = 1.0) {
   if (g == nullptr || b == nullptr || x == nullptr || n_rhs < 1 || n_rhs > 65535 || alpha_idx < 0 ||
       alpha_idx >= g->n_alpha || !(rel_tol > 0.0) || max_iter < 1) {
     set_error("fc_solve: bad argument");
@@ -488,7 +527,7 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
   double* pB = part + (size_t)m * npart;
   double* sums = part + (size_t)2 * m * npart;  // [0..m): rr, [m..2m): bb
   const float* prec = jacobi ? diag32 : nullptr;
-  k_diag32<<<(n + 255) / 256, 256, 0, st>>>(n, g->dw, alpha, diag32);
+  k_diag32<<<(n + 255) / 256, 256, 0, st>>>(n, g->dw, sigma, alpha, diag32);
   FC_LAUNCHED();
   // blocks per column: a few thousand blocks in all, each striding over its
   // column's chunks (many right-hand sides would otherwise launch millions of
@@ -505,14 +544,19 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
   fc_status result = FC_ENOCONV;
   for (int outer = 0; outer < 64; ++outer) {
     if (il)
-      k_resid64_il<<<gridi, blki, 0, st>>>(n, m, g->rowptr, g->colidx, g->w, g->dw, alpha, bv, xv, r64, pA, pB, gxi);
+      k_resid64_il<<<gridi, blki, 0, st>>>(n, m, g->rowptr, g->colidx, g->w, g->dw, sigma, alpha, bv, xv, r64, pA, pB,
+                                           gxi);
     else
-      k_resid64<<<gridr, SV_T, 0, st>>>(n, g->rowptr, g->colidx, g->w, g->dw, alpha, b, x, r64, pA, pB, nbrx);
+      k_resid64<<<gridr, SV_T, 0, st>>>(n, g->rowptr, g->colidx, g->w, g->dw, sigma, alpha, b, x, r64, pA, pB, nbrx);
     FC_LAUNCHED();
     k_colsum<<<m, SV_T, 0, st>>>(pA, il ? gxi : nbrx, sums);
     fcx::note_launch();
     k_colsum<<<m, SV_T, 0, st>>>(pB, il ? gxi : nbrx, sums + m);
     fcx::note_launch();
+    if (sigma == 0.0) {  // singular L: keep the residual in L's range
+      k_proj_mean<<<m, SV_T, 0, st>>>(n, m, il, r64, sums);
+      FC_LAUNCHED();
+    }
     FC_CK(cudaMemcpyAsync(h_rr.data(), sums, m * sizeof(double), cudaMemcpyDeviceToHost, st));
     FC_CK(cudaMemcpyAsync(h_bb.data(), sums + m, m * sizeof(double), cudaMemcpyDeviceToHost, st));
     FC_CK(cudaStreamSynchronize(st));
@@ -646,6 +690,51 @@ extern "C" fc_status fc_pivot_solve(fc_graph* g, int32_t alpha_idx, double* x, d
   FC_LAUNCHED();
   FC_CK(cudaFreeAsync(rhs, st));
   FC_CK(cudaFreeAsync(part, st));
+  FC_CK(cudaStreamSynchronize(st));
+  return s;
+}
+
+// Column sums of an [m][n] block (one block per column, fixed order) and the
+// mean of each column subtracted: out[j][v] = in[j][v] - sum_j / n.
+__global__ void k_col_mean_sub(int32_t n, const double* __restrict__ in, double* __restrict__ out) {
+  __shared__ double red[SV_T];
+  const size_t off = (size_t)blockIdx.x * n;
+  double s = 0.0;
+  for (int64_t v = threadIdx.x; v < n; v += SV_T) s += in[off + v];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = SV_T / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  const double mean = red[0] / (double)n;
+  for (int64_t v = threadIdx.x; v < n; v += SV_T) out[off + v] = in[off + v] - mean;
+}
+
+extern "C" fc_status fc_laplacian_solve(fc_graph* g, const double* b, double* x, int32_t n_rhs, double rel_tol,
+                                        int32_t max_iter, int32_t* iters_out, void* stream) {
+  if (g == nullptr || b == nullptr || x == nullptr || n_rhs < 1 || n_rhs > 65535) {
+    set_error("fc_laplacian_solve: bad argument");
+    return FC_EINVAL;
+  }
+  if (g->root < 0) {
+    set_error("fc_laplacian_solve: needs a graph from fc_build_rooted (G connected)");
+    return FC_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int32_t n = g->n;
+  double* rhs = nullptr;
+  FC_CK(cudaMallocAsync((void**)&rhs, (size_t)n * n_rhs * sizeof(double), st));
+  // b projected onto the range of L (the complement of span(1))
+  k_col_mean_sub<<<n_rhs, SV_T, 0, st>>>(n, b, rhs);
+  FC_LAUNCHED();
+  const fc_status s = solve_impl(g, 0, rhs, x, n_rhs, rel_tol, max_iter, iters_out, st, true, 0.0);
+  if (s == FC_OK || s == FC_ENOCONV) {
+    // the mean-zero solution: L^+ b
+    k_col_mean_sub<<<n_rhs, SV_T, 0, st>>>(n, x, x);
+    FC_LAUNCHED();
+  }
+  FC_CK(cudaFreeAsync(rhs, st));
   FC_CK(cudaStreamSynchronize(st));
   return s;
 }

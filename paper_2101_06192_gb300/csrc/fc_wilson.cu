@@ -504,7 +504,11 @@ struct Shape {
 static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool smem, bool edge, int bits,
                               bool ring, int cl, int nsm, int smem_optin, Shape* out) {
   const bool sbits = bits == 1;
-  const int wcap = std::max(32, std::min(1024, (int)((n / 8) & ~31)));
+  // walks on G with one exit (fc_build_rooted) are long and cross each other:
+  // measured on GB300 (BA n = 2^20 rooted at its hub, 256 trees), walkers
+  // that release their paths under wait-die repeat 2.3x the departures at
+  // 1024 walkers per tree and 1.03x at 128, which ran 2.7x faster
+  const int wcap = std::max(32, std::min(g->root >= 0 ? 128 : 1024, (int)((n / 8) & ~31)));
   // measured on GB300 (BA n = 2^20, tau = 1024): the 40-register variant is
   // fastest; graphs with long walks prefer more walkers per tree, which the
   // score below already favours
@@ -672,7 +676,8 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
     while (c_util < 8 && total * (int64_t)(c_util * 2) <= (int64_t)nsm) c_util *= 2;
     cl = g->cluster > 0 ? g->cluster : c_util;
     if (g->bitmap_mode == 0) {
-      bits = (g->smem_mode != 1 && fits_c(cl)) ? 1 : 0;
+      // rooted graphs: state flags, so that several small CTAs share an SM
+      bits = (g->root < 0 && g->smem_mode != 1 && fits_c(cl)) ? 1 : 0;
     } else {
       bits = g->bitmap_mode - 1;
       if (bits == 1 && g->cluster == 0)
@@ -769,7 +774,13 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   p.err = g->d_err;
   p.stats = g->d_stats;
   {
-    const uint64_t mi = max_steps_per_tree ? max_steps_per_tree : (uint64_t)8 * (uint64_t)n + (1ull << 20);
+    // default watchdog: 8 n + 2^20 iterations per walker on G* (every step can
+    // exit to u*); walks on G with one exit (fc_build_rooted) take
+    // sum_v d_w(v) r(root, v) steps in all, up to quadratic in n on long
+    // paths, and walkers wait for each other longer: 2^26 + 64 n
+    const uint64_t mi = max_steps_per_tree ? max_steps_per_tree
+                        : (g->root >= 0 ? (1ull << 26) + (uint64_t)64 * (uint64_t)n
+                                        : (uint64_t)8 * (uint64_t)n + (1ull << 20));
     p.max_iters = (uint32_t)std::min<uint64_t>(mi, 0xffffffffull);
   }
   p.pre_cleared = 0;

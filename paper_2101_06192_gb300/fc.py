@@ -75,6 +75,11 @@ def lib():
             "fc_mlp_adam": ([P, P, P, P, I32, I32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                              ctypes.c_float, P], ctypes.c_int),
             "fc_tau_for": ([D, D, D, I64], I64),
+            "fc_build_rooted": ([I32, I64, P, P, P, I32, U32, P, ctypes.POINTER(P)], ctypes.c_int),
+            "fc_bfs_tree": ([P, P, P, P], ctypes.c_int),
+            "fc_resistance_accumulate": ([P, P, I64, P, P], ctypes.c_int),
+            "fc_laplacian_solve": ([P, P, P, I32, D, I32, P, P], ctypes.c_int),
+            "fc_electrical_closeness": ([P, P, I64, P, P, P, P, P, P], ctypes.c_int),
             "fc_destroy": ([P], None),
             "fc_status_str": ([ctypes.c_int], ctypes.c_char_p),
             "fc_last_error_message": ([], ctypes.c_char_p),
@@ -166,6 +171,61 @@ class Graph:
         self.num_graphs = int(ga.size)
         self.vertex_offsets = voff.copy()
         return self
+
+    @classmethod
+    def rooted(cls, g, root: int, stream=None):
+        """fc_build_rooted: G (host CSR) with walks whose only exit is ``root``
+        (uniform spanning trees of G rooted there) and root's BFS tree."""
+        self = cls.__new__(cls)
+        rp = np.ascontiguousarray(g.rowptr, dtype=np.int64)
+        ci = np.ascontiguousarray(g.colidx, dtype=np.int32)
+        ww = None if g.w is None else np.ascontiguousarray(g.w, dtype=np.float32)
+        h = ctypes.c_void_p()
+        _check(lib().fc_build_rooted(int(rp.shape[0]) - 1, int(ci.shape[0]), _ptr(rp), _ptr(ci), _ptr(ww), int(root),
+                                     FC_HOST_PTRS, _stream(stream), ctypes.byref(h)), "fc_build_rooted")
+        self._h = h
+        self.n = int(rp.shape[0]) - 1
+        self.nnz = int(ci.shape[0])
+        self.alphas = np.ones(1)
+        self.n_alpha = 1
+        self.weighted = ww is not None
+        self.root = int(root)
+        return self
+
+    def bfs_tree(self, stream=None):
+        """fc_bfs_tree: (parent, depth) of the root's breadth-first tree."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        par = torch.empty(self.n, dtype=torch.int32, device=dev)
+        dep = torch.empty(self.n, dtype=torch.int32, device=dev)
+        _check(lib().fc_bfs_tree(self._h, _ptr(par), _ptr(dep), _stream(stream)), "fc_bfs_tree")
+        return par, dep
+
+    def resistance_accumulate(self, parents, acc=None, stream=None):
+        """fc_resistance_accumulate over parents [T, n]; acc (int64 [n]) accumulates."""
+        parents = parents.reshape(-1, self.n).to(torch.int32).contiguous()
+        if acc is None:
+            acc = torch.zeros(self.n, dtype=torch.int64, device=parents.device)
+        _dev_tensor(acc, torch.int64, self.n, "acc")
+        _check(lib().fc_resistance_accumulate(self._h, _ptr(parents), int(parents.shape[0]), _ptr(acc),
+                                              _stream(stream)), "fc_resistance_accumulate")
+        return acc
+
+    def laplacian_solve(self, b, x=None, rel_tol: float = 1e-9, max_iter: int = 20000, stream=None):
+        """fc_laplacian_solve: L^+ b for b of shape [n] or [m, n] (FP64, CUDA).  Returns (x, iters)."""
+        b2 = b.reshape(-1, self.n).contiguous()
+        x = torch.zeros_like(b2) if x is None else x.reshape(-1, self.n)
+        it = ctypes.c_int32()
+        _check(lib().fc_laplacian_solve(self._h, _ptr(b2), _ptr(x), int(b2.shape[0]), float(rel_tol), int(max_iter),
+                                        ctypes.byref(it), _stream(stream)), "fc_laplacian_solve")
+        return x.reshape(b.shape), it.value
+
+    def electrical_closeness(self, acc, trees: int, x_pivot, stream=None):
+        """fc_electrical_closeness: (r^(root, .), diag(L^+), farness, closeness), FP64 [n] each."""
+        dev = acc.device
+        outs = [torch.empty(self.n, dtype=torch.float64, device=dev) for _ in range(4)]
+        _check(lib().fc_electrical_closeness(self._h, _ptr(acc), int(trees), _ptr(x_pivot.contiguous()),
+                                             *[_ptr(o) for o in outs], _stream(stream)), "fc_electrical_closeness")
+        return tuple(outs)
 
     def batch_latency_ms(self):
         out = np.zeros(self.num_graphs, dtype=np.float64)

@@ -89,6 +89,15 @@ def test_farness_identity_and_closeness():
         np.testing.assert_allclose(el.diag_from_resistance(r, Lp[:, root], root), np.diag(Lp), atol=1e-12)
 
 
+def test_bfs_inverse_weights_by_edge_lookup():
+    g = synth.barabasi_albert(200, 3, 8, weighted=True)
+    bpar, _ = el.bfs_tree(g, 5)
+    inv = el.bfs_inverse_weights(g, bpar)
+    for v in range(g.n):
+        exp = 0.0 if bpar[v] < 0 else 1.0 / float(np.float32(el.edge_weight(g, v, int(bpar[v]))))
+        assert inv[v] == exp
+
+
 def test_bfs_tree_against_scipy_shortest_paths():
     for g in (synth.barabasi_albert(300, 2, 7), synth.perturbed_grid(20, 15, 2)):
         A = scipy.sparse.csr_matrix((np.ones(g.nnz), g.colidx, g.rowptr), shape=(g.n, g.n))
@@ -233,3 +242,19 @@ def test_sampled_estimator_unbiased_and_diag_within_bound():
     assert np.max(np.abs(z)) < scipy.stats.norm.isf(1e-4 / (2 * g.n))
     d_hat = el.diag_from_resistance(r_hat, el.pivot_column(g, root), root)
     assert np.max(np.abs(d_hat - np.diag(Lp))) < 6 * sd.max()
+
+
+def test_vectorised_path_sums_equal_the_loop_bit_for_bit():
+    """path_sums_np (numpy over all vertices at once) gives the same bits as
+    the plain per-vertex loop, weighted and unweighted."""
+    for g in (synth.barabasi_albert(400, 3, 4, weighted=True), synth.erdos_renyi(300, 6, 2),
+              synth.perturbed_grid(15, 12, 4)):
+        if not el.is_connected(g):
+            continue
+        for root in (0, int(np.argmax(g.degrees())), g.n - 1):
+            bpar, _ = el.bfs_tree(g, root)
+            binv = el.bfs_inverse_weights(g, bpar)
+            for par in native.wilson_rooted(g, root, seed=3, tau=3)["parents"]:
+                a = el.path_sums(g, root, bpar, binv, par)
+                b = el.path_sums_np(g, root, bpar, binv, par)
+                np.testing.assert_array_equal(a.view(np.uint64), b.view(np.uint64))
