@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-tte", action="store_true",
                     help="leave out the time-to-eps study (R-MAT 22, learned control variate vs plain) that the "
                          "default run appends to its line")
-    ap.add_argument("--workload", choices=["ba", "cv", "grid", "batch", "rb", "group", "roots", "electrical"],
+    ap.add_argument("--workload", choices=["ba", "cv", "grid", "batch", "rb", "group", "roots", "electrical", "solve"],
                     default="ba",
                     help="ba: the benchmark line; cv: time to eps = 0.1, learned control variate vs "
                          "plain (R-MAT scale 22); grid: 2048^2 road-like grid, three alphas in one launch; "
@@ -66,6 +66,7 @@ def parse():
                          "for 64 query vertices (Omega columns); electrical: electrical closeness on G (BA 2^20 "
                          "rooted at its hub, --el-trees trees)")
     ap.add_argument("--el-trees", type=int, default=1024)
+    ap.add_argument("--rhs", type=int, default=64, help="right-hand sides of --workload solve")
     ap.add_argument("--el-order", default="bfs_reverse", choices=["bfs", "bfs_reverse", "id", "id_desc"],
                     help="start order of the rooted sampler (default: the reverse of the root's breadth-first "
                          "order, the library's automatic choice)")
@@ -907,9 +908,76 @@ def run_electrical(args):
     print(json.dumps(line), flush=True)
 
 
+def run_solve(args):
+    """CG on I + alpha L (fc_solve: Jacobi-preconditioned FP32 inner CG, FP64
+    residual and refinement to 1e-9) with --rhs right-hand sides e_v of
+    degree-stratified reference vertices: on BA n = 2^20, m = 8 (alpha = 1) and
+    on the 2048^2 road-like grid (weights U[1, 10], alpha = 1).  Roofline:
+    algorithmic bytes of one inner iteration (SpMV: row pointers 8 B per row,
+    column index 4 B and weight 4 B per entry, 4 B per entry and right-hand
+    side for the gathered vector; the vector updates: 48 B per vertex and
+    right-hand side) times the inner iterations, over the solve's time."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2101_06192_gb300 import fc
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    peaks, peak_kind = load_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    results = []
+    for name, g in (("BA n=2^20 m=8 (seed 2)", synth.barabasi_albert(1 << N_LOG2, BA_M, BA_SEED)),
+                    ("grid 2048^2 (seed 3), w~U[1,10]", synth.perturbed_grid(2048, 2048, 3))):
+        G = fc.Graph.from_csr(g, [1.0])
+        m = args.rhs
+        J = reference_vertices(g, m, 5)[:m]
+        m = int(J.size)
+        B = torch.zeros((m, g.n), dtype=torch.float64, device="cuda")
+        B[torch.arange(m, device="cuda"), torch.from_numpy(J).cuda()] = 1.0
+        for _ in range(max(1, args.warmup)):
+            G.solve(B, rel_tol=1e-9)
+        ms, its = [], []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            X, it = G.solve(B, rel_tol=1e-9)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+            its.append(it)
+        n, nnz = g.n, g.nnz
+        wbytes = 4 if g.w is not None else 0
+        spmv = 8.0 * (n + 1) + (4.0 + wbytes) * nnz + 4.0 * m * nnz
+        it_bytes = spmv + 48.0 * m * n
+        t = statistics.median(ms) / 1000.0
+        it = statistics.median(its)
+        results.append({"graph": name, "n": n, "nnz": nnz, "rhs": m, "ms": statistics.median(ms),
+                        "inner_iterations": it, "ms_per_iteration": 1000.0 * t / max(1, it),
+                        "spmv_bytes_per_iteration": spmv, "bytes_per_iteration": it_bytes,
+                        "achieved_gbs": it_bytes * it / t / 1e9, "frac": it_bytes * it / t / 1e9 / peak})
+        G.close()
+        del B, X
+    line = {"metric": "CG on I + alpha L, achieved algorithmic GB/s", "value": results[0]["achieved_gbs"],
+            "unit": "GB/s", "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
+            "dtype": "f32 inner / f64 residual", "data": "synthetic", "results": results,
+            "roofline": {"bound": "hbm", "kernel": "CG inner iteration (k_spmv_pq_il + vector kernels)",
+                         "achieved": results[0]["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": results[0]["frac"], "traffic": None, "peak_source": peak_kind},
+            "config": {"workload": f"fc_solve, {args.rhs} right-hand sides e_v, rel_tol 1e-9, alpha=1",
+                       "l2": "flushed before every timed solve (512 MB write)"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.workload == "solve":
+        if rank == 0:
+            run_solve(args)
+        return
     if args.workload == "electrical":
         if rank == 0:
             run_electrical(args)

@@ -125,16 +125,17 @@ __global__ void k_inner_init(int32_t n, const double* __restrict__ r64, const fl
   const int j = blockIdx.y;
   const size_t off = (size_t)j * n;
   const double sc = scal[j * 8 + 4];
-  double rz = 0.0, rr = 0.0;
+  float rzf = 0.0f, rrf = 0.0f;  // per-thread partials in FP32, then FP64 across threads
   for (int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x; v < n; v += (int64_t)gridDim.x * SV_T) {
     const float rv = (float)(r64[off + v] * sc);
-    const float z = prec ? rv / prec[v] : rv;
+    const float z = prec ? rv * prec[v] : rv;
     in.r[off + v] = rv;
     in.p[off + v] = z;
     in.d[off + v] = 0.0f;
-    rz += (double)rv * (double)z;
-    rr += (double)rv * (double)rv;
+    rzf = fmaf(rv, z, rzf);
+    rrf = fmaf(rv, rv, rrf);
   }
+  double rz = rzf, rr = rrf;
   block_sum2(rz, rr);
   if (threadIdx.x == 0) {
     prz[(size_t)j * nb + blockIdx.x] = rz;
@@ -150,7 +151,7 @@ __global__ void k_spmv_pq(int32_t n, const int64_t* __restrict__ rowptr, const i
   const int gl = threadIdx.x % RG;
   const size_t off = (size_t)j * n;
   const float* pj = in.p + off;
-  double pq = 0.0, unused = 0.0;
+  float pqf = 0.0f;
   for (int64_t c = blockIdx.x; c * ROWS_PER_BLOCK < n; c += gridDim.x) {
     const int64_t v = c * ROWS_PER_BLOCK + threadIdx.x / RG;
     float acc = 0.0f;
@@ -162,9 +163,10 @@ __global__ void k_spmv_pq(int32_t n, const int64_t* __restrict__ rowptr, const i
       const float pv = pj[v];
       const float qv = pv * diag32[v] - alpha * acc;
       in.q[off + v] = qv;
-      pq += (double)pv * (double)qv;
+      pqf = fmaf(pv, qv, pqf);
     }
   }
+  double pq = pqf, unused = 0.0;
   block_sum2(pq, unused);
   if (threadIdx.x == 0) ppq[(size_t)j * nb + blockIdx.x] = pq;
 }
@@ -176,15 +178,16 @@ __global__ void k_inner_update(int32_t n, const float* __restrict__ prec, const 
   const size_t off = (size_t)j * n;
   const double* sc = scal + j * 8;
   const float a = (sc[5] != 0.0 && sc[1] != 0.0) ? (float)(sc[0] / sc[1]) : 0.0f;
-  double rz = 0.0, rr = 0.0;
+  float rzf = 0.0f, rrf = 0.0f;
   for (int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x; v < n; v += (int64_t)gridDim.x * SV_T) {
     in.d[off + v] += a * in.p[off + v];
     const float rv = in.r[off + v] - a * in.q[off + v];
     in.r[off + v] = rv;
-    const float z = prec ? rv / prec[v] : rv;
-    rz += (double)rv * (double)z;
-    rr += (double)rv * (double)rv;
+    const float z = prec ? rv * prec[v] : rv;
+    rzf = fmaf(rv, z, rzf);
+    rrf = fmaf(rv, rv, rrf);
   }
+  double rz = rzf, rr = rrf;
   block_sum2(rz, rr);
   if (threadIdx.x == 0) {
     prz[(size_t)j * nb + blockIdx.x] = rz;
@@ -199,7 +202,7 @@ __global__ void k_inner_p(int32_t n, const float* __restrict__ prec, const doubl
   const double* sc = scal + j * 8;
   const float beta = sc[0] != 0.0 ? (float)(sc[2] / sc[0]) : 0.0f;
   for (int64_t v = (int64_t)blockIdx.x * SV_T + threadIdx.x; v < n; v += (int64_t)gridDim.x * SV_T) {
-    const float z = prec ? in.r[off + v] / prec[v] : in.r[off + v];
+    const float z = prec ? in.r[off + v] * prec[v] : in.r[off + v];
     in.p[off + v] = z + beta * in.p[off + v];
   }
 }
@@ -231,10 +234,16 @@ __global__ void k_correct(int32_t n, const double* __restrict__ scal, const floa
     x[off + v] += (double)d[off + v] / sc[4];
 }
 
+// the FP32 diagonal and its reciprocal (the Jacobi preconditioner, applied
+// as a product)
 __global__ void k_diag32(int32_t n, const double* __restrict__ dw, double sigma, double alpha,
-                         float* __restrict__ diag32) {
+                         float* __restrict__ diag32, float* __restrict__ inv32) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v < n) diag32[v] = (float)(sigma + alpha * dw[v]);
+  if (v < n) {
+    const double d = sigma + alpha * dw[v];
+    diag32[v] = (float)d;
+    inv32[v] = (float)(1.0 / d);
+  }
 }
 
 __global__ void k_fill(int64_t len, double val, double* __restrict__ a) {
@@ -374,18 +383,18 @@ __global__ void __launch_bounds__(256) k_inner_init_il(int32_t n, int m, const d
   const int j = blockIdx.y * 32 + threadIdx.x;
   const bool on = j < m;
   const double sc = on ? scal[j * 8 + 4] : 0.0;
-  double rz = 0.0, rr = 0.0;
+  float rz = 0.0f, rr = 0.0f;  // per-thread partials in FP32, then FP64 across threads
   for (int64_t c = blockIdx.x; c * IL_R < n; c += gridDim.x) {
     const int64_t v = c * IL_R + threadIdx.y;
     if (v < n && on) {
       const size_t i = (size_t)v * m + j;
       const float rv = (float)(r64[i] * sc);
-      const float z = prec ? rv / prec[v] : rv;
+      const float z = prec ? rv * prec[v] : rv;
       in.r[i] = rv;
       in.p[i] = z;
       in.d[i] = 0.0f;
-      rz += (double)rv * (double)z;
-      rr += (double)rv * (double)rv;
+      rz = fmaf(rv, z, rz);
+      rr = fmaf(rv, rv, rr);
     }
   }
   il_sum2(rz, rr, j, on, prz, prr, nb);
@@ -397,7 +406,7 @@ __global__ void __launch_bounds__(256) k_spmv_pq_il(int32_t n, int m, const int6
                                                     double* __restrict__ ppq, int nb) {
   const int j = blockIdx.y * 32 + threadIdx.x;
   const bool on = j < m;
-  double pq = 0.0;
+  float pq = 0.0f;
   for (int64_t c = blockIdx.x; c * IL_R < n; c += gridDim.x) {
     const int64_t v = c * IL_R + threadIdx.y;
     if (v < n && on) {
@@ -407,7 +416,7 @@ __global__ void __launch_bounds__(256) k_spmv_pq_il(int32_t n, int m, const int6
       const float pv = in.p[i];
       const float qv = pv * diag32[v] - alpha * acc;
       in.q[i] = qv;
-      pq += (double)pv * (double)qv;
+      pq = fmaf(pv, qv, pq);
     }
   }
   il_sum2(pq, 0.0, j, on, ppq, nullptr, nb);
@@ -423,7 +432,7 @@ __global__ void __launch_bounds__(256) k_inner_update_il(int32_t n, int m, const
     const double* sc = scal + j * 8;
     a = (sc[5] != 0.0 && sc[1] != 0.0) ? (float)(sc[0] / sc[1]) : 0.0f;
   }
-  double rz = 0.0, rr = 0.0;
+  float rz = 0.0f, rr = 0.0f;
   for (int64_t c = blockIdx.x; c * IL_R < n; c += gridDim.x) {
     const int64_t v = c * IL_R + threadIdx.y;
     if (v < n && on) {
@@ -431,9 +440,9 @@ __global__ void __launch_bounds__(256) k_inner_update_il(int32_t n, int m, const
       in.d[i] += a * in.p[i];
       const float rv = in.r[i] - a * in.q[i];
       in.r[i] = rv;
-      const float z = prec ? rv / prec[v] : rv;
-      rz += (double)rv * (double)z;
-      rr += (double)rv * (double)rv;
+      const float z = prec ? rv * prec[v] : rv;
+      rz = fmaf(rv, z, rz);
+      rr = fmaf(rv, rv, rr);
     }
   }
   il_sum2(rz, rr, j, on, prz, prr, nb);
@@ -449,7 +458,7 @@ __global__ void __launch_bounds__(256) k_inner_p_il(int32_t n, int m, const floa
     const int64_t v = c * IL_R + threadIdx.y;
     if (v < n) {
       const size_t i = (size_t)v * m + j;
-      const float z = prec ? in.r[i] / prec[v] : in.r[i];
+      const float z = prec ? in.r[i] * prec[v] : in.r[i];
       in.p[i] = z + beta * in.p[i];
     }
   }
@@ -498,7 +507,7 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
   double* part = nullptr;
   double* scal = nullptr;
   FC_CK(cudaMallocAsync((void**)&r64, nm * sizeof(double), st));
-  FC_CK(cudaMallocAsync((void**)&f32, (4 * nm + n) * sizeof(float), st));
+  FC_CK(cudaMallocAsync((void**)&f32, (4 * nm + 2 * (size_t)n) * sizeof(float), st));
   const int npart = std::max(std::max(nb, nbr), il ? gxi : 1);
   double* bi = nullptr;  // interleaved copies of b and x
   double* xi = nullptr;
@@ -523,11 +532,12 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
   in.d = f32 + 3 * nm;
   in.scal = scal;
   float* diag32 = f32 + 4 * nm;
+  float* inv32 = diag32 + n;  // the reciprocal of the diagonal
   double* pA = part;
   double* pB = part + (size_t)m * npart;
   double* sums = part + (size_t)2 * m * npart;  // [0..m): rr, [m..2m): bb
-  const float* prec = jacobi ? diag32 : nullptr;
-  k_diag32<<<(n + 255) / 256, 256, 0, st>>>(n, g->dw, sigma, alpha, diag32);
+  const float* prec = jacobi ? inv32 : nullptr;  // z = r * prec
+  k_diag32<<<(n + 255) / 256, 256, 0, st>>>(n, g->dw, sigma, alpha, diag32, inv32);
   FC_LAUNCHED();
   // blocks per column: a few thousand blocks in all, each striding over its
   // column's chunks (many right-hand sides would otherwise launch millions of
