@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-tte", action="store_true",
                     help="leave out the time-to-eps study (R-MAT 22, learned control variate vs plain) that the "
                          "default run appends to its line")
-    ap.add_argument("--workload", choices=["ba", "cv", "grid", "batch", "rb", "group", "roots", "electrical", "solve"],
+    ap.add_argument("--workload", choices=["ba", "cv", "grid", "batch", "rb", "group", "roots", "electrical", "solve", "mlp"],
                     default="ba",
                     help="ba: the benchmark line; cv: time to eps = 0.1, learned control variate vs "
                          "plain (R-MAT scale 22); grid: 2048^2 road-like grid, three alphas in one launch; "
@@ -67,6 +67,11 @@ def parse():
                          "rooted at its hub, --el-trees trees)")
     ap.add_argument("--el-trees", type=int, default=1024)
     ap.add_argument("--rhs", type=int, default=64, help="right-hand sides of --workload solve")
+    ap.add_argument("--grid-side", type=int, default=2048, help="grid workload: side of the grid")
+    ap.add_argument("--grid-alphas", default="0.1,1,10", help="grid workload: alphas, comma-separated")
+    ap.add_argument("--grid-trees", type=int, default=512, help="grid workload: trees per alpha and step")
+    ap.add_argument("--batch-trees", type=int, default=256, help="batch workload: trees per graph and step")
+    ap.add_argument("--roots-trees", type=int, default=152, help="roots workload: trees")
     ap.add_argument("--el-order", default="bfs_reverse", choices=["bfs", "bfs_reverse", "id", "id_desc"],
                     help="start order of the rooted sampler (default: the reverse of the root's breadth-first "
                          "order, the library's automatic choice)")
@@ -493,11 +498,17 @@ def run_grid(args):
     import synth
     from paper_2101_06192_gb300 import fc, tune
     torch.cuda.set_device(0)
-    g = synth.perturbed_grid(2048, 2048, 3)
-    alphas = [0.1, 1.0, 10.0]
-    tau = 512
+    side = args.grid_side
+    g = synth.perturbed_grid(side, side, 3)
+    alphas = [float(a) for a in args.grid_alphas.split(",")]
+    tau = args.grid_trees
     G = fc.Graph.from_csr(g, alphas)
-    shape = tune.autotune(G, tau)
+    if args.shape:  # fixed shape 'walkers,regs[,order]' (profiling cases)
+        parts = args.shape.split(",")
+        shape = {"walkers": int(parts[0]), "regs": int(parts[1]), "order": parts[2] if len(parts) > 2 else "auto"}
+        tune.apply(G, shape)
+    else:
+        shape = tune.autotune(G, tau)
     stream = torch.cuda.current_stream()
     R = torch.zeros(len(alphas) * g.n, dtype=torch.int32, device="cuda")
     for i in range(max(1, args.warmup)):
@@ -505,6 +516,7 @@ def run_grid(args):
     times, stats = [], []
     clocks = ClockSampler(0)
     clocks.start()
+    nvtx_push("timed")
     for i in range(args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         R.zero_()
@@ -516,6 +528,7 @@ def run_grid(args):
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
         stats.append(G.sampler_stats())
+    nvtx_pop()
     clk = clocks.stop()
     ms = statistics.mean(times)
     pops = statistics.mean(s[0] for s in stats)
@@ -528,7 +541,8 @@ def run_grid(args):
     line = {
         "metric": "USTs/s", "value": n_trees / (ms / 1000.0), "unit": "trees/s", "ms_per_step": ms,
         "higher_is_better": True, "steps": args.steps, "dtype": "u32/f64", "data": "synthetic",
-        "config": {"workload": "grid 2048^2, 10% deleted, 1% diagonals, w~U[1,10] fp32, alpha {0.1,1,10} x 512 trees",
+        "config": {"workload": f"grid {side}^2, 10% deleted, 1% diagonals, w~U[1,10] fp32, alpha "
+                               f"{{{args.grid_alphas}}} x {tau} trees",
                    "n": g.n, "m_edges": g.m, "shape": shape},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": float(peaks.get("hbm_gbs", 6800.0)),
                      "unit": "GB/s", "frac": achieved / float(peaks.get("hbm_gbs", 6800.0)),
@@ -555,7 +569,7 @@ def run_batch(args):
     u, offs = synth.union(graphs)
     gen_s = time.perf_counter() - t0
     G = fc.Graph.batch(u, offs, alphas)
-    tau = 256
+    tau = args.batch_trees
     shape = tune.autotune(G, tau, probe_trees=32)  # start order and shape, untimed
     # control-variate network: trained on small R-MAT graphs (untimed)
     train = []
@@ -571,6 +585,7 @@ def run_batch(args):
     C = torch.zeros(u.n, dtype=torch.int32, device="cuda")
     G.sample(1, 4, R=R, C=C)  # warm-up
     times = []
+    nvtx_push("timed")
     for i in range(args.steps):
         R.zero_()
         C.zero_()
@@ -582,6 +597,7 @@ def run_batch(args):
         b.record(stream)
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
+    nvtx_pop()
     lat = G.batch_latency_ms()
     d_plain, _, _ = G.farness(R, tau)
     # accuracy on the small graphs; reference: diag(Omega) from the library's CG
@@ -758,9 +774,9 @@ def run_roots(args):
     import synth
     from paper_2101_06192_gb300 import fc
     torch.cuda.set_device(0)
-    g = synth.barabasi_albert(1 << N_LOG2, BA_M, BA_SEED)
+    g = synth.barabasi_albert(1 << args.n_log2, BA_M, BA_SEED)
     G = fc.Graph.from_csr(g, [ALPHA])
-    T = 152
+    T = args.roots_trees
     par = G.sample(11, T, want_parents=True)["parents"][0].contiguous()
     queries = torch.from_numpy(np.linspace(0, g.n - 1, 64).astype(np.int64)).cuda()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -795,7 +811,7 @@ def run_roots(args):
             "unit": "tree-vertices/s", "ms_tree_roots": 1000.0 * t_r, "ms_root_counts_64": statistics.median(ms_counts),
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "i32",
             "data": "synthetic",
-            "config": {"workload": f"BA n=2^{N_LOG2} m={BA_M}, alpha={ALPHA:g}, {T} trees with parents, 64 queries",
+            "config": {"workload": f"BA n=2^{args.n_log2} m={BA_M}, alpha={ALPHA:g}, {T} trees with parents, 64 queries",
                        "l2": "flushed before every timed call (512 MB write)"},
             "roofline": {"bound": "hbm", "achieved": alg / t_r / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": alg / t_r / 1e9 / peak, "traffic": None, "kernel": "k_roots_jump",
@@ -853,6 +869,7 @@ def run_electrical(args):
     clocks = ClockSampler(0)
     clocks.start()
     tot, parts = [], []
+    nvtx_push("timed")
     for i in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
@@ -863,6 +880,7 @@ def run_electrical(args):
         torch.cuda.synchronize()
         tot.append(evs[0].elapsed_time(evs[5]))
         parts.append([evs[k].elapsed_time(evs[k + 1]) for k in range(5)])
+    nvtx_pop()
     clk = clocks.stop()
     ms = statistics.mean(tot)
     pm = [statistics.mean(p[k] for p in parts) for k in range(5)]
@@ -938,6 +956,7 @@ def run_solve(args):
         for _ in range(max(1, args.warmup)):
             G.solve(B, rel_tol=1e-9)
         ms, its = [], []
+        nvtx_push("timed")
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
@@ -948,6 +967,7 @@ def run_solve(args):
             torch.cuda.synchronize()
             ms.append(a.elapsed_time(b))
             its.append(it)
+        nvtx_pop()
         n, nnz = g.n, g.nnz
         wbytes = 4 if g.w is not None else 0
         spmv = 8.0 * (n + 1) + (4.0 + wbytes) * nnz + 4.0 * m * nnz
@@ -971,9 +991,54 @@ def run_solve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mlp(args):
+    """Training step of the control-variate network (fc_mlp_loss_grad_acc per
+    graph, then fc_mlp_adam) on R-MAT scale 16, 17 and 18 (one graph each,
+    plain-estimator targets from 512 trees): graph-steps per second; about
+    3 kFLOP FP32 per vertex (forward 1.55 k, backward 1.5 k)."""
+    import torch
+    import synth
+    from paper_2101_06192_gb300 import cvnet, fc
+    torch.cuda.set_device(0)
+    data = []
+    nv = 0
+    for i, sc in enumerate((16, 17, 18)):
+        g = synth.rmat(sc, 16, 100 + sc)
+        G = fc.Graph.from_csr(g, [1.0])
+        data.append((G, G.features(), cvnet.plain_targets(G, 512, seed=i), 0))
+        nv += g.n
+    params = cvnet.init_params(1)
+    cvnet.train(data, steps=max(1, args.warmup), lr=1e-3, params=params)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nvtx_push("timed")
+    a.record(stream)
+    cvnet.train(data, steps=args.steps, lr=1e-3, params=params)
+    b.record(stream)
+    torch.cuda.synchronize()
+    nvtx_pop()
+    ms = a.elapsed_time(b) / args.steps
+    tflops = 3.05e3 * nv / (ms / 1000.0) / 1e12
+    line = {"metric": "control-variate training steps/s (3 graphs per step)", "value": 1000.0 / ms,
+            "unit": "steps/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "bf16 weights / fp32", "data": "synthetic",
+            "config": {"workload": "R-MAT scale 16, 17, 18 (ef 16), 4->128->1 MLP", "vertices": nv},
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": 80.5, "unit": "TFLOP/s (FP32)",
+                         "frac": tflops / 80.5, "kernel": "k_mlp_grad",
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "traffic": None}}
+    for (G, _, _, _) in data:
+        G.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.workload == "mlp":
+        if rank == 0:
+            run_mlp(args)
+        return
     if args.workload == "solve":
         if rank == 0:
             run_solve(args)
