@@ -229,6 +229,29 @@ def resistance_from_totals(acc: np.ndarray, trees: int) -> np.ndarray:
     return acc.astype(np.float64) / (float(1 << FRAC_BITS) * trees)
 
 
+def weighted_degrees(g) -> np.ndarray:
+    """d_w(v): the row's weights (FP32 converted to FP64) summed left to right."""
+    d = np.zeros(g.n)
+    for v in range(g.n):
+        s = 0.0
+        for e in range(g.rowptr[v], g.rowptr[v + 1]):
+            s = s + (1.0 if g.w is None else float(g.w[e]))
+        d[v] = s
+    return d
+
+
+def resistance_from_visits(visits: np.ndarray, trees: int, dw: np.ndarray, root: int) -> np.ndarray:
+    """The visit estimator (not in the paper): in Wilson's algorithm rooted at
+    u the departures K_v from v in one tree do not depend on the start order,
+    and taking v as the first start vertex shows that K_v is the number of
+    visits to v of a walk from v killed at u, whose mean is the Green's
+    function d_w(v) r(u, v).  So K_v / d_w(v) is unbiased for r(u, v):
+    r^(u, v) = visits[v] / (trees d_w(v)), 0 at the root."""
+    r = visits.astype(np.float64) / (float(trees) * dw)
+    r[root] = 0.0
+    return r
+
+
 def pivot_column(g, root: int) -> np.ndarray:
     """x = L^+ e_root (insight (ii): one Laplacian solve; here the dense pinv)."""
     return laplacian_pinv(g)[:, root].copy()

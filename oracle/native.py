@@ -39,7 +39,7 @@ def lib():
                                  ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P]
         L.orc_wilson.restype = ctypes.c_int
         L.orc_wilson_v.argtypes = [ctypes.c_int32, P, P, P, ctypes.c_double, P, ctypes.c_uint32,
-                                   ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P]
+                                   ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P, P]
         L.orc_wilson_v.restype = ctypes.c_int
         L.orc_philox_batch.argtypes = [ctypes.c_int64, P, ctypes.c_uint64, P]
         L.orc_philox_batch.restype = None
@@ -51,7 +51,7 @@ def lib():
                                         ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, P, P, P]
         L.orc_stack_entries.restype = ctypes.c_int
         L.orc_wilson_rooted.argtypes = [ctypes.c_int32, P, P, P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64,
-                                        ctypes.c_int64, P, P, P]
+                                        ctypes.c_int64, P, P, P, P]
         L.orc_wilson_rooted.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -94,15 +94,18 @@ def stack_entries(g, alpha: float, seed: int, tree: int, verts, ks, alpha_idx: i
 
 
 def wilson(g, alpha, seed: int, tau: int, tree_offset: int = 0, alpha_idx: int = 0,
-           order=None, want_parents: bool = False, want_C: bool = True, want_steps: bool = True):
+           order=None, want_parents: bool = False, want_C: bool = True, want_steps: bool = True,
+           want_visits: bool = False):
     """Sequential Wilson sampler on G* (Algorithm 2).  ``alpha`` is a float or a
     per-vertex array (a batch of graphs as one block-diagonal union).  Returns
-    dict with R, C, parents ([tau, n], n = u*) and steps ([tau])."""
+    dict with R, C, parents ([tau, n], n = u*), steps ([tau]) and visits ([n],
+    departures from each vertex summed over the trees)."""
     n = g.n
     R = np.zeros(n, dtype=np.uint32)
     C = np.zeros(n, dtype=np.uint32) if want_C else None
     parents = np.empty((tau, n), dtype=np.int32) if want_parents else None
     steps = np.zeros(tau, dtype=np.uint64) if want_steps else None
+    visits = np.zeros(n, dtype=np.uint64) if want_visits else None
     w = None if g.w is None else np.ascontiguousarray(g.w, dtype=np.float32)
     order_arr = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
     av = None
@@ -112,26 +115,29 @@ def wilson(g, alpha, seed: int, tau: int, tree_offset: int = 0, alpha_idx: int =
         alpha = 0.0
     rc = lib().orc_wilson_v(n, _ptr(g.rowptr), _ptr(g.colidx), _ptr(w), float(alpha), _ptr(av), int(alpha_idx),
                             int(seed) & (2**64 - 1), int(tree_offset), int(tau), _ptr(order_arr),
-                            _ptr(R), _ptr(C), _ptr(parents), _ptr(steps))
+                            _ptr(R), _ptr(C), _ptr(parents), _ptr(steps), _ptr(visits))
     if rc != 0:
         raise MemoryError("oracle sampler allocation failed")
-    return {"R": R, "C": C, "parents": parents, "steps": steps}
+    return {"R": R, "C": C, "parents": parents, "steps": steps, "visits": visits}
 
 
 def wilson_rooted(g, root: int, seed: int, tau: int, tree_offset: int = 0, order=None,
-                  want_parents: bool = True, want_steps: bool = True):
+                  want_parents: bool = True, want_steps: bool = True, want_visits: bool = False):
     """Sequential Wilson sampler on G rooted at ``root`` (uniform spanning trees
     of G, walks with probability w_vj / d_w(v)).  Returns dict with parents
-    ([tau, n], the root's entry n) and steps ([tau], departures)."""
+    ([tau, n], the root's entry n), steps ([tau], departures) and visits ([n],
+    departures from each vertex summed over the trees; the root's 0)."""
     n = g.n
     parents = np.empty((tau, n), dtype=np.int32) if want_parents else None
     steps = np.zeros(tau, dtype=np.uint64) if want_steps else None
+    visits = np.zeros(n, dtype=np.uint64) if want_visits else None
     w = None if g.w is None else np.ascontiguousarray(g.w, dtype=np.float32)
     order_arr = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
     rc = lib().orc_wilson_rooted(n, _ptr(g.rowptr), _ptr(g.colidx), _ptr(w), int(root), int(seed) & (2**64 - 1),
-                                 int(tree_offset), int(tau), _ptr(order_arr), _ptr(parents), _ptr(steps))
+                                 int(tree_offset), int(tau), _ptr(order_arr), _ptr(parents), _ptr(steps),
+                                 _ptr(visits))
     if rc == -2:
         raise ValueError("wilson_rooted: the graph is not connected")
     if rc != 0:
         raise MemoryError("oracle sampler allocation failed")
-    return {"parents": parents, "steps": steps}
+    return {"parents": parents, "steps": steps, "visits": visits}

@@ -145,20 +145,21 @@ void orc_row_prefix(int32_t n, const int64_t* rowptr, const float* w, double* S)
  *   C[v]       += number of trees whose stack entry 0 of v selects u*   (may be NULL)
  *   parents    [tau][n]: tree parent of v (n = u*)                      (may be NULL)
  *   steps      [tau]: number of stack entries consumed (= departures)  (may be NULL)
+ *   visits     [n]: += departures from v, summed over the trees        (may be NULL)
  *   order      start-vertex order, NULL = ascending degree
  * Returns 0 on success, -1 on allocation failure.
  */
 int orc_wilson_v(int32_t n, const int64_t* rowptr, const int32_t* colidx, const float* w,
                  double alpha, const double* alpha_v, uint32_t alpha_idx, uint64_t seed,
                  int64_t tree_offset, int64_t tau, const int32_t* order_in, uint32_t* R, uint32_t* C,
-                 int32_t* parents, uint64_t* steps);
+                 int32_t* parents, uint64_t* steps, uint64_t* visits);
 
 int orc_wilson(int32_t n, const int64_t* rowptr, const int32_t* colidx, const float* w,
                double alpha, uint32_t alpha_idx, uint64_t seed, int64_t tree_offset,
                int64_t tau, const int32_t* order_in, uint32_t* R, uint32_t* C,
                int32_t* parents, uint64_t* steps) {
     return orc_wilson_v(n, rowptr, colidx, w, alpha, NULL, alpha_idx, seed, tree_offset, tau,
-                        order_in, R, C, parents, steps);
+                        order_in, R, C, parents, steps, NULL);
 }
 
 /* As orc_wilson with an optional per-vertex alpha (alpha_v != NULL overrides
@@ -167,7 +168,7 @@ int orc_wilson(int32_t n, const int64_t* rowptr, const int32_t* colidx, const fl
 int orc_wilson_v(int32_t n, const int64_t* rowptr, const int32_t* colidx, const float* w,
                  double alpha, const double* alpha_v, uint32_t alpha_idx, uint64_t seed,
                  int64_t tree_offset, int64_t tau, const int32_t* order_in, uint32_t* R, uint32_t* C,
-                 int32_t* parents, uint64_t* steps) {
+                 int32_t* parents, uint64_t* steps, uint64_t* visits) {
     orc_graph g;
     g.n = n; g.rowptr = rowptr; g.colidx = colidx; g.alpha = alpha; g.alpha_idx = alpha_idx;
     g.alpha_v = alpha_v;
@@ -229,6 +230,9 @@ int orc_wilson_v(int32_t n, const int64_t* rowptr, const int32_t* colidx, const 
             for (int32_t v = 0; v < n; ++v) s += cnt[v];
             steps[t] = s;
         }
+        if (visits) {
+            for (int32_t v = 0; v < n; ++v) visits[v] += cnt[v];
+        }
     }
     free(S); free(order); free(in_tree); free(next); free(cnt);
     return 0;
@@ -289,8 +293,8 @@ int orc_stack_entries(int32_t n, const int64_t* rowptr, const int32_t* colidx, c
  *           entry is n (the root, seen as the only vertex joined to an
  *           outside vertex n)
  *   steps   [tau]: stack entries consumed (departures; the root makes none)
- * Returns 0, -1 on allocation failure, -2 if a walk meets a vertex without
- * neighbours (G not connected).
+ *   visits  [n]: += departures from v, summed over the trees (the root's 0)
+ * Returns 0, -1 on allocation failure, -2 if G is not connected.
  */
 static int32_t stack_entry_rooted(const orc_graph* g, int32_t v, uint32_t k, uint32_t tg) {
     uint32_t ctr[4] = {k, (uint32_t)v, tg, 0u};
@@ -317,7 +321,7 @@ static int32_t stack_entry_rooted(const orc_graph* g, int32_t v, uint32_t k, uin
 
 int orc_wilson_rooted(int32_t n, const int64_t* rowptr, const int32_t* colidx, const float* w, int32_t root,
                       uint64_t seed, int64_t tree_offset, int64_t tau, const int32_t* order_in,
-                      int32_t* parents, uint64_t* steps) {
+                      int32_t* parents, uint64_t* steps, uint64_t* visits) {
     orc_graph g;
     g.n = n; g.rowptr = rowptr; g.colidx = colidx; g.alpha = 1.0; g.alpha_idx = 0;
     g.alpha_v = NULL;
@@ -386,6 +390,9 @@ int orc_wilson_rooted(int32_t n, const int64_t* rowptr, const int32_t* colidx, c
             uint64_t s = 0;
             for (int32_t v = 0; v < n; ++v) s += cnt[v];
             steps[t] = s;
+        }
+        if (visits) {
+            for (int32_t v = 0; v < n; ++v) visits[v] += cnt[v];
         }
     }
     free(S); free(order); free(in_tree); free(next); free(cnt);

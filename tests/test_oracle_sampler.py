@@ -171,6 +171,23 @@ def test_expected_departures_equal_sum_deg_star_omega():
     assert pred <= alpha * dw.sum() + g.n
 
 
+def test_visits_per_vertex_equal_deg_star_omega():
+    """Departures from v per tree of G* have mean deg*(v) Omega_vv (visits of a
+    walk killed at u*): per-vertex z-scores over 3000 trees; totals = steps."""
+    g = synth.erdos_renyi(40, 4, 17, weighted=True)
+    alpha = 0.7
+    T = 3000
+    K = np.stack([native.wilson(g, alpha, seed=4, tau=1, tree_offset=t, want_C=False, want_visits=True)["visits"]
+                  for t in range(T)]).astype(np.float64)
+    tot = native.wilson(g, alpha, seed=4, tau=T, want_C=False, want_visits=True)
+    assert int(tot["visits"].sum()) == int(tot["steps"].sum())
+    om = np.diag(dense.forest_matrix(g, alpha))
+    dstar = 1.0 + alpha * np.array([g.w[g.rowptr[v]:g.rowptr[v + 1]].astype(np.float64).sum() for v in range(g.n)])
+    z = (K.mean(axis=0) - dstar * om) / (K.std(axis=0, ddof=1) / math.sqrt(T) + 1e-300)
+    z[K.std(axis=0) == 0] = 0
+    assert np.max(np.abs(z)) < scipy.stats.norm.isf(1e-4 / (2 * g.n))
+
+
 def test_tree_offset_additivity():
     """Trees are indexed globally: sampling [0, a) and [a, a+b) separately gives the
     same counts as [0, a+b) (resume / sharding identity)."""
