@@ -66,6 +66,8 @@ def parse():
                          "for 64 query vertices (Omega columns); electrical: electrical closeness on G (BA 2^20 "
                          "rooted at its hub, --el-trees trees)")
     ap.add_argument("--el-trees", type=int, default=1024)
+    ap.add_argument("--el-estimator", default="visits", choices=["visits", "kirchhoff"],
+                    help="electrical workload: r(root, v) from the sampler's visit totals or the Kirchhoff path sums")
     ap.add_argument("--rhs", type=int, default=64, help="right-hand sides of --workload solve")
     ap.add_argument("--grid-side", type=int, default=2048, help="grid workload: side of the grid")
     ap.add_argument("--grid-alphas", default="0.1,1,10", help="grid workload: alphas, comma-separated")
@@ -824,9 +826,12 @@ def run_roots(args):
 def run_electrical(args):
     """Electrical closeness on G (Sec. 3 insights (i)-(iii), Eq. 2): BA n = 2^20,
     m = 8 rooted at its largest hub; one step = build G rooted at the pivot
-    (with its BFS tree), sample tau spanning trees with their parents, the
-    Kirchhoff path sums (fc_resistance_accumulate), the pivot column of L^+
-    (fc_laplacian_solve) and the combination (fc_electrical_closeness)."""
+    (with its BFS tree), sample tau spanning trees, estimate r(root, v) -- by
+    default from the sampler's visit totals (Green's function), with
+    --el-estimator kirchhoff from the parents by the Kirchhoff path sums
+    (fc_resistance_accumulate) -- the pivot column of L^+ (fc_laplacian_solve)
+    and the combination (fc_electrical_closeness).  Untimed: both estimates
+    from the same 256 trees against L^+[v, v] of reference vertices."""
     import numpy as np
     import torch
     import synth
@@ -849,16 +854,17 @@ def run_electrical(args):
             G.set_start_order({"bfs": 0, "id": 2, "id_desc": 3}[args.el_order])
         if ev:
             ev[0].record(stream)
-        o = G.sample(seed, tau, want_parents=True, with_C=False)
+        kir = args.el_estimator == "kirchhoff"
+        o = G.sample(seed, tau, want_parents=kir, want_visits=not kir, with_C=False)
         if ev:
             ev[1].record(stream)
-        acc = G.resistance_accumulate(o["parents"][0])
+        acc = G.resistance_accumulate(o["parents"][0]) if kir else None
         if ev:
             ev[2].record(stream)
         x, it = G.laplacian_solve(e, rel_tol=1e-9)
         if ev:
             ev[3].record(stream)
-        r, d, far, clo = G.electrical_closeness(acc, tau, x)
+        r, d, far, clo = G.electrical_closeness(acc, tau, x, visits=o["visits"])
         out.update(diag=d, iters=it, depth=int(G.bfs_tree()[1].max().item()), stats=G.sampler_stats())
         G.close()
         return clo
@@ -893,6 +899,17 @@ def run_electrical(args):
     X, _ = Gj.laplacian_solve(B, rel_tol=1e-10)
     exact = X[torch.arange(J.size, device="cuda"), Jt]
     depth_sum = float(Gj.bfs_tree()[1].to(torch.float64).sum().item())
+    # both estimators on the same 256 trees (untimed)
+    tc = 256
+    o = Gj.sample(99, tc, want_parents=True, want_visits=True, with_C=False)
+    xj, _ = Gj.laplacian_solve(e, rel_tol=1e-10)
+    cmp = {}
+    for name, acc_, vis_ in (("kirchhoff", Gj.resistance_accumulate(o["parents"][0]), None),
+                             ("visits", None, o["visits"])):
+        _, dd, _, _ = Gj.electrical_closeness(acc_, tc, xj, visits=vis_)
+        ee = (dd[Jt] - exact).abs()
+        cmp[name] = {"max_abs_err": float(ee.max()), "mean_abs_err": float(ee.mean())}
+    del o
     Gj.close()
     err = (out["diag"][Jt] - exact).abs()
     peaks, peak_kind = load_peaks()
@@ -901,7 +918,19 @@ def run_electrical(args):
     # vertex) and, per tree and breadth-first step, the parent of the edge's
     # upper end (4 B); totals 8 B per vertex per chunk of 32 trees
     acc_bytes = 4.0 * tau * n + 4.0 * tau * depth_sum + 8.0 * n * math.ceil(tau / 32)
-    acc_s = pm[2] / 1000.0
+    acc_s = max(pm[2], 1e-6) / 1000.0
+    if args.el_estimator == "kirchhoff":
+        roofline = {"bound": "hbm", "kernel": "k_rb<1> (resistance path sums)",
+                    "achieved": acc_bytes / acc_s / 1e9, "peak": peak, "unit": "GB/s",
+                    "frac": acc_bytes / acc_s / 1e9 / peak, "algorithmic_bytes": acc_bytes,
+                    "peak_source": peak_kind, "traffic": None}
+    else:  # the sampler dominates: 20 B per walk step + 8 B per vertex and tree
+        smp_bytes = algorithmic_bytes(out["stats"][1], n, tau)
+        smp_s = pm[1] / 1000.0
+        roofline = {"bound": "hbm", "kernel": "k_wilson_edge<flags> on G rooted at the hub (+ visit totals)",
+                    "achieved": smp_bytes / smp_s / 1e9, "peak": peak, "unit": "GB/s",
+                    "frac": smp_bytes / smp_s / 1e9 / peak, "algorithmic_bytes": smp_bytes,
+                    "peak_source": peak_kind, "traffic": None}
     line = {
         "metric": "USTs/s (electrical closeness on G)", "value": tau / (ms / 1000.0), "unit": "trees/s",
         "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
@@ -916,11 +945,9 @@ def run_electrical(args):
         "cg_iterations": out["iters"],
         "departures_per_step": out["stats"][1],
         "accuracy": {"reference_vertices": int(J.size), "max_abs_err_diag_Lplus": float(err.max()),
-                     "mean_abs_err": float(err.mean())},
-        "roofline": {"bound": "hbm", "kernel": "k_rb<1> (resistance path sums)",
-                     "achieved": acc_bytes / acc_s / 1e9, "peak": peak, "unit": "GB/s",
-                     "frac": acc_bytes / acc_s / 1e9 / peak, "algorithmic_bytes": acc_bytes,
-                     "peak_source": peak_kind, "traffic": None},
+                     "mean_abs_err": float(err.mean()), "estimators_256_trees": cmp},
+        "estimator": args.el_estimator,
+        "roofline": roofline,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -234,6 +234,21 @@ fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_o
                          uint64_t* steps_out, void* stream);
 
 /*
+ * fc_sample_usts with one more optional output (NULL skips it):
+ *   visits   uint64[n_alpha * n]   visits[a*n + v] += departures from v in each
+ *            tree (its popped stack entries plus the one that gives its tree
+ *            edge; accumulated).  The count does not depend on the start order
+ *            (cycle popping).  Its mean per tree is deg*(v) Omega[v, v] on G*
+ *            and d_w(v) r(root, v) on a graph from fc_build_rooted, where the
+ *            root departs once per tree (the visits of a walk from v killed at
+ *            the root: its Green's function).  Sum over v = steps_out per tree.
+ * Everything else as fc_sample_usts.  Synchronises `stream`.
+ */
+fc_status fc_sample_usts_ex(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R, uint32_t* C,
+                            int32_t* parents, uint64_t* visits, uint64_t max_steps_per_tree, uint64_t* steps_out,
+                            void* stream);
+
+/*
  * fc_sample_usts without the synchronising error read-back, for enqueueing on
  * a stream that is being captured into a CUDA graph (the persistent sampling
  * launch, its memsets and the combinations after it become graph nodes).
@@ -535,19 +550,27 @@ fc_status fc_laplacian_solve(fc_graph* g, const double* b, double* x, int32_t n_
                              int32_t max_iter, int32_t* iters_out, void* stream);
 
 /*
- * Electrical closeness from T trees' resistance totals acc (from
- * fc_resistance_accumulate) and the pivot column x_pivot = L^+ e_root (device
- * double [n], fc_laplacian_solve), FP64 throughout:
- *   r^(root, v) = acc[v] / (2^32 T)                       -> resist_out
+ * Electrical closeness from T trees and the pivot column x_pivot = L^+ e_root
+ * (device double [n], fc_laplacian_solve), FP64 throughout.  Exactly one of
+ * two estimates of r(root, v) is given:
+ *   acc     (device int64 [n], fc_resistance_accumulate): the Kirchhoff path
+ *           sums, r^ = acc[v] / (2^32 T);
+ *   visits  (device uint64 [n], fc_sample_usts_ex on the rooted graph): the
+ *           departures from v, r^ = visits[v] / (T d_w(v)), 0 at the root (not
+ *           in the paper: the Green's-function identity; no parent arrays and
+ *           no aggregation pass, and on BA and road-like graphs several times
+ *           smaller per-tree variance than the path sums).
+ * Then
+ *   r^(root, v)                                           -> resist_out
  *   L^+[v, v]   = r^ - x[root] + 2 x[v]     (Eq. 2)       -> diag_out
  *   farness_v   = n L^+[v, v] + sum_w L^+[w, w]           -> farness_out
  *   closeness_v = n / farness_v             (Def. 2)      -> closeness_out
  * Outputs device double [n]; all but diag_out may be NULL.  T >= 1.
  * Allocates temporary device memory.  Asynchronous.
  */
-fc_status fc_electrical_closeness(fc_graph* g, const int64_t* acc, int64_t T, const double* x_pivot,
-                                  double* resist_out, double* diag_out, double* farness_out, double* closeness_out,
-                                  void* stream);
+fc_status fc_electrical_closeness(fc_graph* g, const int64_t* acc, const uint64_t* visits, int64_t T,
+                                  const double* x_pivot, double* resist_out, double* diag_out, double* farness_out,
+                                  double* closeness_out, void* stream);
 
 /*
  * Top-k ranking (Sec. 6.1): the k vertices with the smallest diag values

@@ -8,8 +8,10 @@
 //   fc_sample_usts            (fc_wilson*.cu) uniform spanning trees of G rooted at u
 //   fc_resistance_accumulate  (fc_rb.cu) Kirchhoff path sums along B
 //   fc_laplacian_solve        (fc_solve.cu) the pivot column x = L^+ e_u
-//   fc_electrical_closeness   r^(u, v), L^+[v, v] = r^ - x[u] + 2 x[v] (Eq. 2),
-//                             farness n L^+[v, v] + tr(L^+), closeness n / farness
+//   fc_electrical_closeness   r^(u, v) from the path sums or from the sampler's
+//                             visit totals (Green's function), L^+[v, v] = r^ -
+//                             x[u] + 2 x[v] (Eq. 2), farness n L^+[v, v] +
+//                             tr(L^+), closeness n / farness
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -106,16 +108,20 @@ __global__ void k_bfs_parent(int32_t n, const int64_t* __restrict__ rowptr, cons
   }
 }
 
-// d_v = acc[v] / (2^32 T) - x[root] + 2 x[v] (Eq. 2 solved for L^+[v, v]) and
-// per-block partial sums of d (fixed-order tree).
-__global__ void k_el_combine(int32_t n, const int64_t* __restrict__ acc, double denom,
+// r^(root, v) from the path-sum totals, acc[v] / (2^32 T), or from the visit
+// totals, visits[v] / (T d_w(v)) (0 at the root); then d_v = r^ - x[root] +
+// 2 x[v] (Eq. 2 solved for L^+[v, v]) and per-block partial sums of d
+// (fixed-order tree).
+__global__ void k_el_combine(int32_t n, const int64_t* __restrict__ acc, const unsigned long long* __restrict__ visits,
+                             const double* __restrict__ dw, double trees, double denom,
                              const double* __restrict__ x, int32_t root, double* __restrict__ resist,
                              double* __restrict__ diag, double* __restrict__ partial) {
   __shared__ double red[EL_T];
   const int64_t v = (int64_t)blockIdx.x * EL_T + threadIdx.x;
   double d = 0.0;
   if (v < n) {
-    const double r = __ddiv_rn((double)acc[v], denom);
+    const double r = acc ? __ddiv_rn((double)acc[v], denom)
+                         : (v == root ? 0.0 : __ddiv_rn((double)visits[v], __dmul_rn(trees, dw[v])));
     d = __dadd_rn(__dadd_rn(r, -x[root]), __dmul_rn(2.0, x[v]));
     if (resist) resist[v] = r;
     diag[v] = d;
@@ -251,10 +257,11 @@ extern "C" fc_status fc_bfs_tree(const fc_graph* g, int32_t* parent_out, int32_t
   return FC_OK;
 }
 
-extern "C" fc_status fc_electrical_closeness(fc_graph* g, const int64_t* acc, int64_t T, const double* x_pivot,
-                                             double* resist_out, double* diag_out, double* farness_out,
-                                             double* closeness_out, void* stream) {
-  if (g == nullptr || acc == nullptr || x_pivot == nullptr || diag_out == nullptr || T < 1) {
+extern "C" fc_status fc_electrical_closeness(fc_graph* g, const int64_t* acc, const uint64_t* visits, int64_t T,
+                                             const double* x_pivot, double* resist_out, double* diag_out,
+                                             double* farness_out, double* closeness_out, void* stream) {
+  if (g == nullptr || (acc == nullptr) == (visits == nullptr) || x_pivot == nullptr || diag_out == nullptr ||
+      T < 1) {
     set_error("fc_electrical_closeness: bad argument");
     return FC_EINVAL;
   }
@@ -268,7 +275,8 @@ extern "C" fc_status fc_electrical_closeness(fc_graph* g, const int64_t* acc, in
   double* part = nullptr;
   FC_CK(cudaMallocAsync((void**)&part, (size_t)(nb + 1) * sizeof(double), st));
   const double denom = (double)(1ull << EL_FRAC) * (double)T;  // exact: a power of two times T < 2^53
-  k_el_combine<<<(unsigned)nb, EL_T, 0, st>>>(n, acc, denom, x_pivot, g->root, resist_out, diag_out, part);
+  k_el_combine<<<(unsigned)nb, EL_T, 0, st>>>(n, acc, (const unsigned long long*)visits, g->dw, (double)T, denom,
+                                              x_pivot, g->root, resist_out, diag_out, part);
   FC_LAUNCHED();
   k_el_sum<<<1, 1024, 0, st>>>(part, nb, part + nb);
   FC_LAUNCHED();

@@ -433,6 +433,10 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
       int32_t* par = p.parents + (p.num_graphs > 0 ? (size_t)tloc : (size_t)tree) * n + base;
       for (int32_t v = me; v < nl; v += W) par[v] = (int32_t)S[v].nxt;
     }
+    if (p.visits != nullptr) {  // departures from v = its popped stack entries + the tree edge's
+      unsigned long long* vis = p.visits + (size_t)a * n + base;
+      for (int32_t v = me; v < nl; v += W) atomicAdd(&vis[v], (S[v].st & K_MASK) + 1ull);
+    }
     if (me == 0) {
       if (p.steps != nullptr) p.steps[item] = (uint64_t)nl + sh_pops;
       if (p.item_ns != nullptr) p.item_ns[item] = global_ns();
@@ -585,19 +589,25 @@ static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool 
 using namespace fcx;
 
 static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R, uint32_t* C,
-                             int32_t* parents, uint64_t max_steps_per_tree, uint64_t* steps_out, void* stream,
-                             bool sync);
+                             int32_t* parents, uint64_t* visits, uint64_t max_steps_per_tree, uint64_t* steps_out,
+                             void* stream, bool sync);
 
 extern "C" fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R,
                                     uint32_t* C, int32_t* parents, uint64_t max_steps_per_tree,
                                     uint64_t* steps_out, void* stream) {
-  return sample_impl(g, seed, tau, tree_offset, R, C, parents, max_steps_per_tree, steps_out, stream, true);
+  return sample_impl(g, seed, tau, tree_offset, R, C, parents, nullptr, max_steps_per_tree, steps_out, stream, true);
+}
+
+extern "C" fc_status fc_sample_usts_ex(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R,
+                                       uint32_t* C, int32_t* parents, uint64_t* visits, uint64_t max_steps_per_tree,
+                                       uint64_t* steps_out, void* stream) {
+  return sample_impl(g, seed, tau, tree_offset, R, C, parents, visits, max_steps_per_tree, steps_out, stream, true);
 }
 
 extern "C" fc_status fc_sample_usts_async(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R,
                                           uint32_t* C, int32_t* parents, uint64_t max_steps_per_tree,
                                           uint64_t* steps_out, void* stream) {
-  return sample_impl(g, seed, tau, tree_offset, R, C, parents, max_steps_per_tree, steps_out, stream, false);
+  return sample_impl(g, seed, tau, tree_offset, R, C, parents, nullptr, max_steps_per_tree, steps_out, stream, false);
 }
 
 extern "C" fc_status fc_sampler_check(fc_graph* g, void* stream) {
@@ -624,8 +634,8 @@ extern "C" fc_status fc_sampler_check(fc_graph* g, void* stream) {
 }
 
 static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R, uint32_t* C,
-                             int32_t* parents, uint64_t max_steps_per_tree, uint64_t* steps_out, void* stream,
-                             bool sync) {
+                             int32_t* parents, uint64_t* visits, uint64_t max_steps_per_tree, uint64_t* steps_out,
+                             void* stream, bool sync) {
   if (g == nullptr || R == nullptr || tau < 0 || tree_offset < 0 || tree_offset + tau > (int64_t(1) << 32)) {
     set_error("fc_sample_usts: bad argument");
     return FC_EINVAL;
@@ -744,6 +754,7 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   p.R = R;
   p.C = C;
   p.parents = parents;
+  p.visits = (unsigned long long*)visits;
   p.steps = steps_out;
   p.gstate = (VState*)gstate;
   p.gbits = gbits;

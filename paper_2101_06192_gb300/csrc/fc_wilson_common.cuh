@@ -33,6 +33,7 @@ struct WParams {
   uint32_t* C;              // [n_alpha][n] or null
   int32_t* parents;         // [n_alpha*tau][n] or null
   uint64_t* steps;          // [n_alpha*tau] or null
+  unsigned long long* visits;  // [n_alpha][n]: += departures from each vertex per tree, or null
   VState* gstate;           // [gridDim.x][n] (global-state variant)
   uint32_t* gbits;          // [gridDim.x][words] in-tree bitmaps (global-state variant)
   int32_t words;            // bitmap words per tree: ceil(nmax / 32)

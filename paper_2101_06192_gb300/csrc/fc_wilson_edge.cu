@@ -740,6 +740,10 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
       int32_t* par = p.parents + (p.num_graphs > 0 ? (size_t)tloc : (size_t)tree) * n + base;
       for (int32_t v = (int32_t)wid; v < nl; v += (int32_t)WT) par[v] = (int32_t)S[v].nxt;
     }
+    if (p.visits != nullptr) {  // departures from v = its popped stack entries + the tree edge's
+      unsigned long long* vis = p.visits + (size_t)a * n + base;
+      for (int32_t v = (int32_t)wid; v < nl; v += (int32_t)WT) atomicAdd(&vis[v], (S[v].st & K_MASK) + 1ull);
+    }
     if (me == 0 && rank == 0) {
       if (p.steps != nullptr) p.steps[item] = (uint64_t)nl + sh_pops;
       if (p.item_ns != nullptr) p.item_ns[item] = global_ns();

@@ -79,7 +79,8 @@ def lib():
             "fc_bfs_tree": ([P, P, P, P], ctypes.c_int),
             "fc_resistance_accumulate": ([P, P, I64, P, P], ctypes.c_int),
             "fc_laplacian_solve": ([P, P, P, I32, D, I32, P, P], ctypes.c_int),
-            "fc_electrical_closeness": ([P, P, I64, P, P, P, P, P, P], ctypes.c_int),
+            "fc_electrical_closeness": ([P, P, P, I64, P, P, P, P, P, P], ctypes.c_int),
+            "fc_sample_usts_ex": ([P, U64, I64, I64, P, P, P, P, U64, P, P], ctypes.c_int),
             "fc_destroy": ([P], None),
             "fc_status_str": ([ctypes.c_int], ctypes.c_char_p),
             "fc_last_error_message": ([], ctypes.c_char_p),
@@ -219,11 +220,12 @@ class Graph:
                                         ctypes.byref(it), _stream(stream)), "fc_laplacian_solve")
         return x.reshape(b.shape), it.value
 
-    def electrical_closeness(self, acc, trees: int, x_pivot, stream=None):
-        """fc_electrical_closeness: (r^(root, .), diag(L^+), farness, closeness), FP64 [n] each."""
-        dev = acc.device
+    def electrical_closeness(self, acc, trees: int, x_pivot, visits=None, stream=None):
+        """fc_electrical_closeness from path-sum totals ``acc`` or (acc None) visit
+        totals ``visits``: (r^(root, .), diag(L^+), farness, closeness), FP64 [n] each."""
+        dev = x_pivot.device
         outs = [torch.empty(self.n, dtype=torch.float64, device=dev) for _ in range(4)]
-        _check(lib().fc_electrical_closeness(self._h, _ptr(acc), int(trees), _ptr(x_pivot.contiguous()),
+        _check(lib().fc_electrical_closeness(self._h, _ptr(acc), _ptr(visits), int(trees), _ptr(x_pivot.contiguous()),
                                              *[_ptr(o) for o in outs], _stream(stream)), "fc_electrical_closeness")
         return tuple(outs)
 
@@ -316,8 +318,9 @@ class Graph:
 
     def sample(self, seed: int, tau: int, tree_offset: int = 0, R=None, C=None, with_C: bool = True,
                want_parents: bool = False, want_steps: bool = False, max_steps_per_tree: int = 0,
-               stream=None):
-        """fc_sample_usts.  R/C accumulate (allocated zeroed when not given)."""
+               visits=None, want_visits: bool = False, stream=None):
+        """fc_sample_usts (fc_sample_usts_ex when visit totals are wanted).  R, C
+        and visits accumulate (allocated zeroed when not given)."""
         dev = torch.device("cuda", torch.cuda.current_device())
         na, n = self.n_alpha, self.n
         if R is None:
@@ -330,10 +333,18 @@ class Graph:
         parents = torch.empty(na * tau * n, dtype=torch.int32, device=dev) if want_parents else None
         nrow = getattr(self, "num_graphs", 0) or na
         steps = torch.zeros(nrow * tau, dtype=torch.int64, device=dev) if want_steps else None
-        _check(lib().fc_sample_usts(self._h, int(seed) & (2**64 - 1), int(tau), int(tree_offset), _ptr(R),
-                                    _ptr(C), _ptr(parents), int(max_steps_per_tree), _ptr(steps),
-                                    _stream(stream)), "fc_sample_usts")
-        out = {"R": R, "C": C}
+        if visits is None and want_visits:
+            visits = torch.zeros(na * n, dtype=torch.int64, device=dev)
+        if visits is not None:
+            _dev_tensor(visits, torch.int64, na * n, "visits")
+            _check(lib().fc_sample_usts_ex(self._h, int(seed) & (2**64 - 1), int(tau), int(tree_offset), _ptr(R),
+                                           _ptr(C), _ptr(parents), _ptr(visits), int(max_steps_per_tree),
+                                           _ptr(steps), _stream(stream)), "fc_sample_usts_ex")
+        else:
+            _check(lib().fc_sample_usts(self._h, int(seed) & (2**64 - 1), int(tau), int(tree_offset), _ptr(R),
+                                        _ptr(C), _ptr(parents), int(max_steps_per_tree), _ptr(steps),
+                                        _stream(stream)), "fc_sample_usts")
+        out = {"R": R, "C": C, "visits": visits}
         if want_parents:
             out["parents"] = parents.view(na, tau, n)
         if want_steps:

@@ -216,6 +216,73 @@ def test_electrical_closeness_vs_oracle_and_dense(name):
     G.close()
 
 
+@pytest.mark.parametrize("name", ["ba", "ba_w", "er_w", "torus", "path", "star"])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+def test_rooted_visit_totals_bit_exact(name, kernel):
+    """Departures from every vertex summed over the trees (fc_sample_usts_ex)
+    equal the oracle's; the root departs once per tree (to u*)."""
+    g = _graphs()[name]
+    root = int(np.argmax(g.degrees()))
+    G = fc.Graph.rooted(g, root)
+    G.set_kernel(kernel)
+    tau = 40
+    out = G.sample(13, tau, want_visits=True, with_C=False, want_steps=True)
+    ref = native.wilson_rooted(g, root, seed=13, tau=tau, want_parents=False, want_visits=True)
+    vis = out["visits"].cpu().numpy().astype(np.uint64)
+    exp = ref["visits"].copy()
+    exp[root] = tau
+    np.testing.assert_array_equal(vis, exp)
+    assert int(vis.sum()) == int(out["steps"].sum().item())
+    G.close()
+
+
+@pytest.mark.parametrize("weighted,alphas,kernel", [(False, [1.0], 2), (True, [0.3, 5.0], 2), (False, [1.0], 1),
+                                                    (True, [1.0], 1)])
+def test_augmented_visit_totals_bit_exact(weighted, alphas, kernel):
+    """On G* the same output: departures from each vertex, per alpha."""
+    g = synth.barabasi_albert(3000, 3, 7, weighted=weighted)
+    G = fc.Graph.from_csr(g, alphas)
+    G.set_kernel(kernel)
+    out = G.sample(21, 30, want_visits=True)
+    vis = out["visits"].cpu().numpy().astype(np.uint64).reshape(len(alphas), g.n)
+    for a, al in enumerate(alphas):
+        ref = native.wilson(g, al, seed=21, tau=30, alpha_idx=a, want_C=False, want_visits=True)
+        np.testing.assert_array_equal(vis[a], ref["visits"])
+    G.close()
+
+
+@pytest.mark.parametrize("name", ["ba_w", "er_w", "torus"])
+def test_electrical_closeness_from_visits(name):
+    """The visit estimator through fc_electrical_closeness: equal to the
+    oracle's (same totals, the oracle's column) to 1e-12 / 1e-9, and within a
+    sampling bound of the dense L^+."""
+    g = _graphs()[name]
+    root = int(np.argmax(g.degrees()))
+    tau = 400
+    G = fc.Graph.rooted(g, root)
+    out = G.sample(9, tau, want_visits=True, with_C=False)
+    xo = el.pivot_column(g, root)
+    r, d, far, clo = G.electrical_closeness(None, tau, torch.from_numpy(xo).cuda(), visits=out["visits"])
+    ref = native.wilson_rooted(g, root, seed=9, tau=tau, want_parents=False, want_visits=True)
+    dw = el.weighted_degrees(g)
+    r_o = el.resistance_from_visits(ref["visits"], tau, dw, root)
+    d_o = el.diag_from_resistance(r_o, xo, root)
+    np.testing.assert_allclose(r.cpu().numpy(), r_o, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(d.cpu().numpy(), d_o, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(far.cpu().numpy(), el.farness_from_diag(d_o), rtol=1e-9)
+    np.testing.assert_allclose(clo.cpu().numpy(), el.electrical_closeness(el.farness_from_diag(d_o)), rtol=1e-9)
+    # against the definition: per-vertex spread of K_v / d_w(v) over 200 single trees
+    K = np.stack([native.wilson_rooted(g, root, seed=9, tau=1, tree_offset=t, want_parents=False,
+                                       want_visits=True)["visits"] for t in range(200)]).astype(np.float64) / dw
+    sd = K.std(axis=0, ddof=1).max() / math.sqrt(tau)
+    Lp = el.laplacian_pinv(g)
+    assert np.max(np.abs(d.cpu().numpy() - np.diag(Lp))) < 6 * sd + 1e-9
+    # exactly one estimate must be given
+    with pytest.raises(fc.FcError):
+        G.electrical_closeness(None, tau, torch.from_numpy(xo).cuda())
+    G.close()
+
+
 def test_full_size_ba_hub_pivot_bit_exact():
     """BA n = 2^20, m = 8 (the complex-network benchmark graph) rooted at its
     largest hub: the BFS tree, 4 trees and their path-sum totals equal the
@@ -228,10 +295,13 @@ def test_full_size_ba_hub_pivot_bit_exact():
     np.testing.assert_array_equal(par.cpu().numpy(), bpar)
     np.testing.assert_array_equal(dep.cpu().numpy(), depth)
     tau = 4
-    out = G.sample(2020, tau, want_parents=True, want_steps=True)
-    ref = native.wilson_rooted(g, root, seed=2020, tau=tau)
+    out = G.sample(2020, tau, want_parents=True, want_steps=True, want_visits=True)
+    ref = native.wilson_rooted(g, root, seed=2020, tau=tau, want_visits=True)
     np.testing.assert_array_equal(out["parents"][0].cpu().numpy(), ref["parents"])
     np.testing.assert_array_equal(out["steps"][0].cpu().numpy().astype(np.uint64), ref["steps"] + 1)
+    exp = ref["visits"].copy()
+    exp[root] = tau
+    np.testing.assert_array_equal(out["visits"].cpu().numpy().astype(np.uint64), exp)
     acc = G.resistance_accumulate(out["parents"][0])
     binv = el.bfs_inverse_weights(g, bpar)
     exp = sum(el.fixed_point(el.path_sums_np(g, root, bpar, binv, p)) for p in ref["parents"])
