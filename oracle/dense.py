@@ -139,3 +139,24 @@ def diag_from_counts(R: np.ndarray, tau: int, x: np.ndarray | None = None) -> np
     if x is None:
         return R.astype(np.float64) / tau
     return combine_fill_step(R, tau, x) + pinv_block_offset(R.size)
+
+
+def deg_star(g, alpha) -> np.ndarray:
+    """deg*(v) = fl(1 + fl(alpha d_w(v))) with d_w(v) the row's FP32 weights
+    summed left to right in FP64 (alpha a float or a per-vertex array)."""
+    dw = np.zeros(g.n)
+    for v in range(g.n):
+        s = 0.0
+        for e in range(g.rowptr[v], g.rowptr[v + 1]):
+            s = s + (1.0 if g.w is None else float(g.w[e]))
+        dw[v] = s
+    return 1.0 + np.asarray(alpha, dtype=np.float64) * dw
+
+
+def diag_from_visits(visits: np.ndarray, tau: int, dstar: np.ndarray) -> np.ndarray:
+    """Visit estimate of diag(Omega) (not in the paper).  In Wilson's algorithm
+    on G* the departures K_v from v in one tree do not depend on the start
+    order; with v as the first start vertex they are the visits to v of a walk
+    from v killed at u*, whose mean is the Green's function deg*(v) r_{G*}(u*, v)
+    = deg*(v) Omega_vv.  So visits[v] / (tau deg*(v)) is unbiased for Omega_vv."""
+    return visits.astype(np.float64) / (float(tau) * dstar)

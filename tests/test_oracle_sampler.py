@@ -186,6 +186,13 @@ def test_visits_per_vertex_equal_deg_star_omega():
     z = (K.mean(axis=0) - dstar * om) / (K.std(axis=0, ddof=1) / math.sqrt(T) + 1e-300)
     z[K.std(axis=0) == 0] = 0
     assert np.max(np.abs(z)) < scipy.stats.norm.isf(1e-4 / (2 * g.n))
+    # the visit estimate of diag(Omega), with deg* summed as the builder does
+    np.testing.assert_allclose(dense.deg_star(g, alpha), dstar, rtol=1e-15)
+    est = dense.diag_from_visits(tot["visits"], T, dense.deg_star(g, alpha))
+    np.testing.assert_allclose(est, (K / dstar).mean(axis=0), rtol=1e-12)
+    # much smaller per-tree variance than Prop. 1's indicator on this graph
+    X = np.stack([native.wilson(g, alpha, seed=4, tau=1, tree_offset=t, want_C=False)["R"] for t in range(T)])
+    assert (K / dstar).var(axis=0).mean() < 0.2 * X.astype(np.float64).var(axis=0).mean()
 
 
 def test_tree_offset_additivity():
