@@ -339,9 +339,10 @@ def cv_study(g, train_graphs, seeds: int, rmat_scale: int):
     """Time to max-abs diag(Omega) error <= 0.1 on a 4096-vertex reference set,
     for the plain estimator (Prop. 1), the learned control variate (trained
     network), the same control variate with the untrained network and with the
-    feature-free prediction g = p_v (beta = 1), and the Rao-Blackwellised
-    estimator; median GPU time over seeds (CUDA events: sampling, features and
-    inference, combination).  Training time is reported separately."""
+    feature-free prediction g = p_v (beta = 1), the Rao-Blackwellised estimator
+    and the visit estimator (departures / deg*, fc_visit_diag); median GPU time
+    over seeds (CUDA events: sampling, features and inference, combination).
+    Training time is reported separately."""
     import numpy as np
     import torch
     from paper_2101_06192_gb300 import cvnet, fc, tune
@@ -391,7 +392,7 @@ def cv_study(g, train_graphs, seeds: int, rmat_scale: int):
         torch.cuda.synchronize()
         return r, a.elapsed_time(b)
 
-    forms = {"plain": None, "cv": params, "cv_untrained": untrained, "cv_p": "p", "rb": None}
+    forms = {"plain": None, "cv": params, "cv_untrained": untrained, "cv_p": "p", "rb": None, "visits": None}
     results = {}
     infer_ms = []  # features + MLP forward (fc_vertex_features, fc_mlp_forward)
     for form, prm in forms.items():
@@ -414,8 +415,17 @@ def cv_study(g, train_graphs, seeds: int, rmat_scale: int):
             done = 0
             hit = None
             err = None
+            vis = torch.zeros(g.n, dtype=torch.int64, device="cuda") if form == "visits" else None
             for cp in checkpoints:
-                if form == "rb":
+                if form == "visits":
+                    # the same trees, departures from each vertex (visit estimate)
+                    def vis_step():
+                        G.sample(50_000 + 1000 * sd, cp - done, tree_offset=done, R=R, C=C, visits=vis)
+                        return G.visit_diag(vis, cp)
+                    d, dt = timed(vis_step)
+                    ms += dt
+                    done = cp
+                elif form == "rb":
                     # the same trees, with their parents, summarised by the
                     # Rao-Blackwellised conditional probabilities
                     def rb_step():
@@ -451,7 +461,7 @@ def cv_study(g, train_graphs, seeds: int, rmat_scale: int):
         "eps": TTE_EPS, "unit": "ms", "seeds": seeds,
         "workload": f"R-MAT scale {rmat_scale} ef 16 (0.57,0.19,0.19) seed 4, alpha=1",
         "plain_ms": med["plain"], "cv_ms": med["cv"], "cv_untrained_ms": med["cv_untrained"],
-        "cv_p_ms": med["cv_p"], "rb_ms": med["rb"],
+        "cv_p_ms": med["cv_p"], "rb_ms": med["rb"], "visits_ms": med["visits"],
         "trees": {f: results[f]["median_trees"] for f in forms},
         "speedup_cv_over_plain": (med["plain"] / med["cv"]) if med["cv"] and med["plain"] else None,
         "speedup_cv_over_untrained": (med["cv_untrained"] / med["cv"]) if med["cv"] and med["cv_untrained"] else None,

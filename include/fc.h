@@ -389,6 +389,23 @@ fc_status fc_forest_farness_noalloc(fc_graph* g, int32_t alpha_idx, const uint32
                                     void* stream);
 
 /*
+ * Visit estimate of diag(Omega) (not in the paper; an estimator on the same
+ * samples as Prop. 1): diag_out[v] = visits[a*n + v] / (tau deg*(v)), with
+ * visits from fc_sample_usts_ex (departures from v summed over tau trees of
+ * alpha index a) and deg*(v) = fl(1 + fl(alpha d_w(v))).  In Wilson's
+ * algorithm the departures from v do not depend on the start order, and with
+ * v as the first start vertex they are the visits to v of a walk from v
+ * killed at u*, whose mean is the Green's function deg*(v) r_{G*}(u*, v) =
+ * deg*(v) Omega[v, v]: unbiased, and on BA and R-MAT graphs its per-tree
+ * variance is tens of times below the indicator's.  Farness and closeness
+ * follow with fc_farness_from_diag.  visits: device uint64 [n_alpha * n];
+ * diag_out: device double [n]; batches use each vertex's graph alpha.
+ * FC_EINVAL for graphs from fc_build_rooted.  Asynchronous.
+ */
+fc_status fc_visit_diag(fc_graph* g, int32_t alpha_idx, const uint64_t* visits, int64_t tau, double* diag_out,
+                        void* stream);
+
+/*
  * Exact probability p_v that one stack entry of v selects u* (the selector's
  * discrete probability, 1/deg*(v) up to 2^-52), FP64 device [n].  Asynchronous.
  */

@@ -112,6 +112,16 @@ __global__ void k_farness_seg(int32_t n, const int32_t* __restrict__ gid, const 
   if (closeness) closeness[v] = ng / f;          // Def. 2
 }
 
+// diag_v = visits[v] / (tau deg*(v)), deg*(v) = fl(1 + fl(alpha d_w(v)))
+__global__ void k_visit_diag(int32_t n, const unsigned long long* __restrict__ visits, double alpha_s,
+                             const double* __restrict__ alpha_v, const double* __restrict__ dw, double tau,
+                             double* __restrict__ diag) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const double a = alpha_v ? alpha_v[v] : alpha_s;
+  diag[v] = __ddiv_rn((double)visits[v], __dmul_rn(tau, deg_star(a, dw[v])));
+}
+
 __global__ void k_p_root(int32_t n, const uint4* __restrict__ rinfo, double* __restrict__ p) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v < n) p[v] = p_from_rowinfo(rinfo[v]);
@@ -407,5 +417,21 @@ extern "C" fc_status fc_forest_farness_noalloc(fc_graph* g, int32_t alpha_idx, c
     k_farness<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, diag_out, partial + nb, farness_out, closeness_out);
     FC_LAUNCHED();
   }
+  return FC_OK;
+}
+
+extern "C" fc_status fc_visit_diag(fc_graph* g, int32_t alpha_idx, const uint64_t* visits, int64_t tau,
+                                   double* diag_out, void* stream) {
+  if (g == nullptr || visits == nullptr || diag_out == nullptr || tau < 1 || alpha_idx < 0 ||
+      alpha_idx >= g->n_alpha || g->root >= 0) {
+    set_error("fc_visit_diag: bad argument (a graph from fc_build_augmented or fc_build_batch)");
+    return FC_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int32_t n = g->n;
+  k_visit_diag<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      n, (const unsigned long long*)visits + (size_t)alpha_idx * n, g->alphas[alpha_idx],
+      g->num_graphs > 0 ? g->alpha_v : nullptr, g->dw, (double)tau, diag_out);
+  FC_LAUNCHED();
   return FC_OK;
 }

@@ -81,6 +81,7 @@ def lib():
             "fc_laplacian_solve": ([P, P, P, I32, D, I32, P, P], ctypes.c_int),
             "fc_electrical_closeness": ([P, P, P, I64, P, P, P, P, P, P], ctypes.c_int),
             "fc_sample_usts_ex": ([P, U64, I64, I64, P, P, P, P, U64, P, P], ctypes.c_int),
+            "fc_visit_diag": ([P, I32, P, I64, P, P], ctypes.c_int),
             "fc_destroy": ([P], None),
             "fc_status_str": ([ctypes.c_int], ctypes.c_char_p),
             "fc_last_error_message": ([], ctypes.c_char_p),
@@ -422,6 +423,13 @@ class Graph:
         diag = torch.empty(self.n, dtype=torch.float64, device=acc.device)
         _check(lib().fc_rb_diag(_ptr(acc), int(self.n), int(trees), _ptr(diag), _stream(stream)), "fc_rb_diag")
         return diag
+
+    def visit_diag(self, visits, tau: int, alpha_idx: int = 0, stream=None):
+        """fc_visit_diag: diag(Omega) from the visit totals of tau trees."""
+        out = torch.empty(self.n, dtype=torch.float64, device=visits.device)
+        _check(lib().fc_visit_diag(self._h, alpha_idx, _ptr(visits), int(tau), _ptr(out), _stream(stream)),
+               "fc_visit_diag")
+        return out
 
     def farness_from_diag(self, diag, stream=None):
         """fc_farness_from_diag: (farness, closeness) of a diag(Omega) estimate."""

@@ -294,6 +294,42 @@ def test_control_variate_with_nonfinite_predictions():
     G.close()
 
 
+@pytest.mark.parametrize("weighted,alphas", [(False, [1.0]), (True, [0.3, 4.0])])
+def test_visit_diag_vs_oracle_and_dense(weighted, alphas):
+    """fc_visit_diag: visits / (tau deg*) equal to the oracle's to 1e-12 on
+    the same (bit-exact) visit totals, and within a sampling bound of the dense
+    diag(Omega); far below the indicator's error at the same tau."""
+    g = synth.erdos_renyi(800, 8, 11, weighted=weighted)
+    tau = 300
+    G = fc.Graph.from_csr(g, alphas)
+    out = G.sample(55, tau, want_visits=True)
+    for a, al in enumerate(alphas):
+        d = G.visit_diag(out["visits"], tau, alpha_idx=a).cpu().numpy()
+        ref = native.wilson(g, al, seed=55, tau=tau, alpha_idx=a, want_C=False, want_visits=True)
+        exp = dense.diag_from_visits(ref["visits"], tau, dense.deg_star(g, al))
+        np.testing.assert_allclose(d, exp, rtol=1e-12, atol=0)
+        om = np.diag(dense.forest_matrix(g, al))
+        err_v = np.max(np.abs(d - om))
+        err_r = np.max(np.abs(ref["R"] / tau - om))
+        assert err_v < 0.5 * err_r, (err_v, err_r)
+        assert err_v < 0.1
+    G.close()
+
+
+def test_visit_diag_batch_uses_each_graphs_alpha():
+    graphs, alphas = synth.uneven_batch(12, 3, n_min=50, n_max=400)
+    u, offs = synth.union(graphs)
+    G = fc.Graph.batch(u, offs, alphas)
+    tau = 64
+    out = G.sample(8, tau, want_visits=True)
+    d = G.visit_diag(out["visits"], tau).cpu().numpy()
+    av = np.concatenate([np.full(gi.n, a) for gi, a in zip(graphs, alphas)])
+    ref = native.wilson(u, av, seed=8, tau=tau, want_C=False, want_visits=True)
+    np.testing.assert_array_equal(out["visits"].cpu().numpy().astype(np.uint64), ref["visits"])
+    np.testing.assert_allclose(d, dense.diag_from_visits(ref["visits"], tau, dense.deg_star(u, av)), rtol=1e-12)
+    G.close()
+
+
 @pytest.mark.parametrize("kind,alpha", [("ba", 1.0), ("grid", 10.0), ("grid", 0.1)])
 def test_solve_vs_oracle(kind, alpha):
     if kind == "ba":
