@@ -1020,7 +1020,10 @@ def run_solve(args):
     line = {"metric": "CG on I + alpha L, achieved algorithmic GB/s", "value": results[0]["achieved_gbs"],
             "unit": "GB/s", "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
             "dtype": "f32 inner / f64 residual", "data": "synthetic", "results": results,
-            "roofline": {"bound": "hbm", "kernel": "CG inner iteration (k_spmv_pq_il + vector kernels)",
+            "roofline": {"bound": "hbm",
+                         "kernel": ("CG inner iteration (k_cg1: edge-tile SpMV + vector phases, one cooperative "
+                                    "launch per refinement step)" if args.rhs == 1 else
+                                    "CG inner iteration (k_spmv_pq_il + vector kernels)"),
                          "achieved": results[0]["achieved_gbs"], "peak": peak, "unit": "GB/s",
                          "frac": results[0]["frac"], "traffic": None, "peak_source": peak_kind},
             "config": {"workload": f"fc_solve, {args.rhs} right-hand sides e_v, rel_tol 1e-9, alpha=1",

@@ -349,6 +349,54 @@ def test_solve_vs_oracle(kind, alpha):
     G.close()
 
 
+@pytest.mark.parametrize("kind,alpha", [("ba", 1.0), ("grid", 0.1)])
+def test_solve_single_rhs_vs_oracle(kind, alpha):
+    # one right-hand side: the inner CG runs as one cooperative launch that
+    # sums its block partials in a fixed order, so repeated solves agree bit for bit
+    g = synth.barabasi_albert(20000, 4, 7, weighted=True) if kind == "ba" else synth.perturbed_grid(150, 140, 3)
+    G = fc.Graph.from_csr(g, [alpha])
+    v = g.n // 3
+    b = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    b[v] = 1.0
+    x, iters = G.solve(b, rel_tol=1e-10)
+    x2, iters2 = G.solve(b, rel_tol=1e-10)
+    assert iters == iters2 and torch.equal(x, x2)
+    ref = ocg.omega_columns(g, alpha, np.array([v]))[:, 0]
+    np.testing.assert_allclose(x.cpu().numpy(), ref, atol=1e-9 * np.abs(ref).max())
+    A = ocg.system_matrix(g, alpha)
+    assert np.linalg.norm(b.cpu().numpy() - A @ x.cpu().numpy()) <= 1e-10 * 1.01
+    # too few iterations: FC_ENOCONV
+    with pytest.raises(fc.FcError) as e:
+        G.solve(b, rel_tol=1e-14, max_iter=3)
+    assert e.value.status == fc.FC_ENOCONV
+    G.close()
+
+
+def test_solve_single_rhs_hubs_and_empty_rows():
+    # rows of 0 entries between others (the tiles' general walk), rows of
+    # thousands of entries spread over many tiles, and a ragged last tile
+    rng = np.random.default_rng(11)
+    n = 9000
+    hubs = np.array([5, 4000, 8999])
+    u = [np.repeat(hubs, [3000, 700, 2600]), rng.integers(0, n, 6000)]
+    v = [rng.choice(n, 3000, replace=False), rng.choice(n, 700, replace=False), rng.choice(n, 2600, replace=False),
+         rng.integers(0, n, 6000)]
+    u = np.concatenate(u)
+    v = np.concatenate(v)
+    keep = (u != v) & ~np.isin(u, np.arange(2000, 2600)) & ~np.isin(v, np.arange(2000, 2600))
+    g = synth.from_edges(n, u[keep], v[keep], rng.uniform(0.5, 4.0, keep.sum()))
+    assert (np.diff(g.rowptr) == 0).sum() >= 600 and g.nnz % 256 != 0
+    G = fc.Graph.from_csr(g, [3.0])
+    vs = [5, 2100, 8000]
+    B = np.zeros((len(vs), n))
+    B[np.arange(len(vs)), vs] = 1.0
+    ref = ocg.omega_columns(g, 3.0, vs)
+    for j in range(len(vs)):
+        x, _ = G.solve(torch.from_numpy(B[j]).cuda(), rel_tol=1e-11)
+        np.testing.assert_allclose(x.cpu().numpy(), ref[:, j], atol=1e-10 * np.abs(ref[:, j]).max())
+    G.close()
+
+
 def test_pivot_solve_closed_form():
     g = synth.barabasi_albert(5000, 3, 4, weighted=True)
     G = fc.Graph.from_csr(g, [2.0])
