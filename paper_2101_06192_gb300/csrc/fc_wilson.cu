@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
           // cycle x -> ... -> h -> x: free every vertex but x at its next entry
           CNT(CNT_POP);
           if (!rskip) {
-            ADD_ST(c, 1ull - (mytag << K_BITS));
+            if (nxt_read(nc)) ADD_ST(c, 1ull - (mytag << K_BITS));
             ++pops;
           }
           rskip = false;
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson(WParams p) 
           break;
         }
         case P_RELEASE: {
-          ADD_ST(c, 0ull - (mytag << K_BITS));
+          if (nxt_read(nc)) ADD_ST(c, 0ull - (mytag << K_BITS));
           if (c == rh) mode = P_WAIT;
           else c = (int32_t)nc;
           break;
@@ -782,6 +782,14 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   p.gorder = g->gorder;
   p.item_ns = nullptr;
   p.t0_ns = nullptr;
+  // walks on G with one exit: warp w of a CTA starts walks once its tree
+  // holds w n / 256 vertices.  Measured on GB300 (BA n = 2^20 rooted at its
+  // hub, 1024 trees, 128 walkers per tree): iterations in conflict waits 0.73
+  // -> 0.15 per departure, repeated departures 9% -> 0.5%, sampling 246 ->
+  // 211 ms.  A tree's growth stays sequential while it is small (a walk
+  // needs about 2m / vol(tree) steps to hit it), so larger shapes (1024
+  // walkers, in-tree bitmap) with the ramp ran no faster (214 ms).
+  p.ramp_q = (edge && cl == 1 && g->root >= 0) ? (uint32_t)std::max<int64_t>(1, (int64_t)nmax >> 8) : 0u;
   if (batch) {
     const size_t items = (size_t)g->num_graphs * (size_t)tau;
     if (g->item_cap < items && capturing) {

@@ -54,7 +54,19 @@ struct WParams {
   const int32_t* gorder;    // [G] graphs by decreasing size
   unsigned long long* item_ns;  // [G*tau] %globaltimer at completion, indexed graph-major (or null)
   unsigned long long* t0_ns;    // earliest CTA start (or null)
+  // edge-record kernel without clusters: warp w of a CTA takes start vertices
+  // only once its tree holds at least w * ramp_q vertices (or every start
+  // position is handed out); 0 = every warp from the start
+  uint32_t ramp_q;
 };
+
+// Pop and release walks read a vertex's nxt, then free the vertex with an
+// atomic on its state word.  The two are different fields, so neither the
+// compiler nor the memory system has to keep that order, and a vertex freed
+// first can be claimed by another walker, which rewrites its nxt before the
+// read.  Freeing under a test of the loaded value (never all ones: nxt holds a
+// vertex id or n) makes the atomic wait for the load.
+__device__ __forceinline__ bool nxt_read(uint32_t nc) { return nc != 0xffffffffu; }
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;

@@ -98,7 +98,7 @@ template <int BITS, bool WGT, bool RINGP, bool CL, int MAXREG>
 __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long sh_tree, sh_pops, sh_deps;
-  __shared__ uint32_t sh_next;
+  __shared__ uint32_t sh_next, sh_tsize;
   __shared__ volatile uint32_t sh_abort;
   const int me = threadIdx.x;
   const int W = blockDim.x;
@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
     sh_gen[me] = 1u;
     if (me == 0) {
       sh_next = 0;
+      sh_tsize = 0;
       sh_abort = 0;
       sh_pops = 0;
       sh_deps = 0;
@@ -241,6 +242,20 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
       __syncwarp();
       const bool fin = (mode == E_DONE) || (sh_abort != 0u);
       if (__all_sync(FULL, fin)) break;
+      // walker ramp (walks on G with one exit): while the tree is small,
+      // concurrent walks are long and cross each other, and wait-die makes
+      // them repeat work; a warp whose walkers are all idle waits until the
+      // tree has grown (or every start position is handed out)
+      if (!CL && p.ramp_q != 0u) {
+        // lane 0's reading of the shared counters decides for the whole warp
+        bool gated = (uint32_t)(me >> 5) > *(volatile uint32_t*)&sh_tsize / p.ramp_q &&
+                     *(volatile uint32_t*)&sh_next < (uint32_t)nl;
+        gated = __shfl_sync(FULL, gated, 0);
+        if (__all_sync(FULL, gated && mode == E_IDLE)) {
+          __nanosleep(256);
+          continue;
+        }
+      }
 
       // ---- start vertices: hand out the window; a dry window is refilled by
       // copies issued with this iteration's memory operations ----
@@ -349,12 +364,14 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
               // first slot j with u < B_j; B_{d-1} = 2^53
               const uint32_t uh = (uint32_t)(u >> 32);
               const uint32_t m = xd > 13u ? 12u : xd - 1u;
+              // (a loop of m trips: low-degree rows, the common case on road-like
+              // graphs, skip the rest of the 12 words)
               slot = 0xffffffffu;
-#pragma unroll
-              for (uint32_t j = 0; j < 12u; ++j) {
-                if (j < m && slot == 0xffffffffu) {
-                  const uint32_t b = thr_cur[j];
-                  if (uh < b || (uh == b && u < __ldg(Brow + xo + j))) slot = j;
+              for (uint32_t j = 0; j < m; ++j) {
+                const uint32_t b = thr_cur[j];
+                if (uh < b || (uh == b && u < __ldg(Brow + xo + j))) {
+                  slot = j;
+                  break;
                 }
               }
               if (slot == 0xffffffffu) {
@@ -580,7 +597,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             // cycle x -> ... -> h -> x: free every vertex but x at its next entry
             CNT(CNT_POP);
             if (!rskip) {
-              ADD_ST(c, 1ull - (mytag << K_BITS));
+              if (nxt_read(nc)) ADD_ST(c, 1ull - (mytag << K_BITS));
               ++pops;
               if (RINGP) ++rh;
             }
@@ -624,7 +641,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             break;
           }
           case E_RELEASE: {
-            ADD_ST(c, 0ull - (mytag << K_BITS));
+            if (nxt_read(nc)) ADD_ST(c, 0ull - (mytag << K_BITS));
             if (RINGP ? --rh == 0 : c == rh) mode = E_WAIT;
             else c = (int32_t)nc;
             break;
@@ -645,6 +662,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
           // the path s -> ... -> h joins the tree: bump the generation, then flag
           // the ring part and walk the older part from s
           if (len > 0) {
+            if (!CL && p.ramp_q != 0u) atomicAdd(&sh_tsize, (uint32_t)len);
             ++gen;
             if (gen >= GEN_LIMIT) {  // the tag has 26 generation bits
               atomicOr(p.err, ERR_OVERFLOW);
@@ -696,7 +714,11 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             cand = (sh_wst[lane].y & (uint32_t)(IN_TREE >> 32)) == 0u;
           }
         }
-        // compact the candidates to the front of the window
+        // compact the candidates to the front of the window, in place: a lane
+        // writes slot pos <= lane, which another lane reads as its own, so every
+        // read comes before every write (a vote orders no memory accesses
+        // between lanes; only __syncwarp does: without it a lane's read was
+        // moved after another lane's write, and start vertices were lost)
         uint4 wr = make_uint4(0u, 0u, 0u, 0u);
         uint32_t wv = 0;
         if (cand) {
@@ -704,8 +726,9 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
           wv = sh_wv[lane];
         }
         const unsigned cm = __ballot_sync(FULL, cand);
+        __syncwarp();
         if (cand) {
-          const uint32_t pos = (uint32_t)__popc(cm & lt_mask);  // <= lane: read above, before this write
+          const uint32_t pos = (uint32_t)__popc(cm & lt_mask);
           sh_wri[pos] = wr;
           sh_wv[pos] = wv;
         }

@@ -229,6 +229,37 @@ def test_grid_full_size_benchmark_shape_full_wave_bit_exact():
     G.close()
 
 
+def test_grid_full_size_full_wave_repeatable():
+    """Races show as trees that differ between runs of the same seed.  The
+    2048 x 2048 weighted launch of the road-like benchmark (state flags, ring
+    pops, 153 trees over 152 CTAs) three times: identical parents each time,
+    and every parent is a grid neighbour (rows of 2048, diagonals included) or
+    u*.  A missing warp barrier in the start-window compaction once lost a few
+    start vertices per launch here (parent 0), depending on code generation."""
+    g = synth.perturbed_grid(2048, 2048, 3)
+    n = g.n
+    vid = torch.arange(n, device="cuda", dtype=torch.int64)
+    ok = torch.tensor([1, -1, 2048, -2048, 2047, -2047, 2049, -2049], device="cuda")
+    first = None
+    for _ in range(3):
+        G = fc.Graph.from_csr(g, [0.1, 1.0, 10.0])
+        G.set_kernel(2)
+        G.set_bitmap(1)
+        G.set_pops(2)
+        G.set_start_order("degree")
+        G.set_shape(1024, 0, 0, 64)
+        G.set_cluster(1)
+        par = G.sample(33, 51, want_parents=True)["parents"].reshape(-1, n).to(torch.int64)
+        G.close()
+        bad = (par != n) & ~torch.isin(par - vid, ok)
+        assert int(bad.sum()) == 0, torch.nonzero(bad)[:4].tolist()
+        if first is None:
+            first = par
+        else:
+            assert torch.equal(par, first)
+        del par
+
+
 def test_grid_full_size_trees_bit_exact():
     """2048 x 2048 road-like grid, weights U[1, 10], alpha in {0.1, 1, 10}."""
     g = synth.perturbed_grid(2048, 2048, 3)
