@@ -17,6 +17,8 @@ Approximation Algorithms for Forest Closeness Centrality", arXiv 2101.06192):
   electrical.py   electrical closeness on G (Sec. 3, Eq. 2): L^+, effective
                   resistance, the UST path-sum estimator along a BFS tree.
   wilson_oracle.c also: Wilson on G rooted at a vertex (Sec. 3 insight (iii)).
+  forest.py       forest roots and depths of sampled trees (Sec. 2, the
+                  matrix-forest theorem's rooted forests).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA path.
@@ -24,4 +26,4 @@ Every function is pinned by ``tests/test_oracle_*.py`` against facts the paper
 and the mathematics fix (closed forms, brute force, invariants, library
 routines); see the pins listed there.
 """
-from . import cg, cv, dense, electrical, enumerate, mlp, native  # noqa: F401
+from . import cg, cv, dense, electrical, enumerate, forest, mlp, native  # noqa: F401

@@ -6,24 +6,11 @@ import scipy.stats
 import torch
 
 import synth
-from oracle import dense
+from oracle import dense, forest
 
 pytestmark = pytest.mark.gpu
 
 fc = pytest.importorskip("paper_2101_06192_gb300.fc")
-
-
-def _roots_depth_cpu(par):
-    n = par.size
-    root = np.empty(n, np.int32)
-    depth = np.empty(n, np.int32)
-    for v in range(n):
-        x, d = v, 0
-        while par[x] != n:
-            x = par[x]
-            d += 1
-        root[v], depth[v] = x, d
-    return root, depth
 
 
 @pytest.mark.parametrize("kind", ["er", "ba", "grid"])
@@ -41,7 +28,7 @@ def test_roots_and_depths_match_parent_walks(kind):
     r, d = roots.cpu().numpy(), depth.cpu().numpy()
     p = par.cpu().numpy()
     for t in range(p.shape[0]):
-        rr, dd = _roots_depth_cpu(p[t])
+        rr, dd = forest.roots_and_depths_np(p[t])
         np.testing.assert_array_equal(r[t], rr)
         np.testing.assert_array_equal(d[t], dd)
     G.close()
