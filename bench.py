@@ -776,11 +776,12 @@ def run_group(args):
 
 
 def run_roots(args):
-    """Forest roots and depths of sampled trees (fc_tree_roots: pointer
-    jumping) and root
-    counts of 64 query vertices (fc_root_counts): columns of Omega from the
-    same trees, on the benchmark graph (BA n = 2^20, m = 8), 152 trees with
-    parents, inputs resident, L2 flushed before each timed call."""
+    """Forest roots and depths of sampled trees on the benchmark graph (BA
+    n = 2^20, m = 8), 152 trees: written by the sampler as vertices join the
+    tree (fc_sample_usts_forest), against sampling with parents followed by
+    pointer jumping (fc_tree_roots); and root counts of 64 query vertices
+    (fc_root_counts: columns of Omega from the same trees).  L2 flushed before
+    each timed call."""
     import numpy as np
     import torch
     import synth
@@ -789,41 +790,54 @@ def run_roots(args):
     g = synth.barabasi_albert(1 << args.n_log2, BA_M, BA_SEED)
     G = fc.Graph.from_csr(g, [ALPHA])
     T = args.roots_trees
-    par = G.sample(11, T, want_parents=True)["parents"][0].contiguous()
     queries = torch.from_numpy(np.linspace(0, g.n - 1, 64).astype(np.int64)).cuda()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        roots, depth = fc.tree_roots(par)
-        fc.root_counts(roots, queries)
-    torch.cuda.synchronize()
-    ms_roots, ms_counts = [], []
-    nvtx_push("timed")
-    for _ in range(args.steps):
+
+    def timed(fn):
         flush.zero_()
         torch.cuda.synchronize()
-        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        roots, depth = fc.tree_roots(par)
+        r = fn()
         b.record(stream)
-        fc.root_counts(roots, queries)
-        c.record(stream)
         torch.cuda.synchronize()
-        ms_roots.append(a.elapsed_time(b))
-        ms_counts.append(b.elapsed_time(c))
+        return a.elapsed_time(b), r
+
+    for _ in range(args.warmup):
+        par = G.sample(11, T, want_parents=True, with_C=False)["parents"][0].contiguous()
+        roots, depth = fc.tree_roots(par)
+        fc.root_counts(roots, queries)
+        G.sample(11, T, want_roots=True, with_C=False)
+    ms_sp, ms_roots, ms_counts, ms_fused = [], [], [], []
+    nvtx_push("timed")
+    for _ in range(args.steps):
+        t, out = timed(lambda: G.sample(11, T, want_parents=True, with_C=False))
+        ms_sp.append(t)
+        par = out["parents"][0].contiguous()
+        t, (roots, depth) = timed(lambda: fc.tree_roots(par))
+        ms_roots.append(t)
+        t, _ = timed(lambda: fc.root_counts(roots, queries))
+        ms_counts.append(t)
+        t, fused = timed(lambda: G.sample(11, T, want_roots=True, with_C=False))
+        ms_fused.append(t)
     nvtx_pop()
+    same = bool(torch.equal(fused["roots"][0], roots) and torch.equal(fused["depths"][0], depth))
     n = g.n
     t_r = statistics.median(ms_roots) / 1000.0
+    t_f = statistics.median(ms_fused) / 1000.0
     # algorithmic bytes of fc_tree_roots: parents read, roots and depths
     # written (4 B each per tree and vertex)
     alg = 12.0 * T * n
     peaks, peak_kind = load_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    line = {"metric": "tree-vertices/s (forest roots and depths)", "value": T * n / t_r,
-            "unit": "tree-vertices/s", "ms_tree_roots": 1000.0 * t_r, "ms_root_counts_64": statistics.median(ms_counts),
+    line = {"metric": "tree-vertices/s (trees sampled with forest roots and depths)", "value": T * n / t_f,
+            "unit": "tree-vertices/s", "ms_sample_with_forest": 1000.0 * t_f,
+            "ms_sample_with_parents": statistics.median(ms_sp), "ms_tree_roots": 1000.0 * t_r,
+            "ms_root_counts_64": statistics.median(ms_counts), "fused_equals_pointer_jumping": same,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "i32",
             "data": "synthetic",
-            "config": {"workload": f"BA n=2^{args.n_log2} m={BA_M}, alpha={ALPHA:g}, {T} trees with parents, 64 queries",
+            "config": {"workload": f"BA n=2^{args.n_log2} m={BA_M}, alpha={ALPHA:g}, {T} trees, 64 queries",
                        "l2": "flushed before every timed call (512 MB write)"},
             "roofline": {"bound": "hbm", "achieved": alg / t_r / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": alg / t_r / 1e9 / peak, "traffic": None, "kernel": "k_roots_jump",

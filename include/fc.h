@@ -249,6 +249,23 @@ fc_status fc_sample_usts_ex(fc_graph* g, uint64_t seed, int64_t tau, int64_t tre
                             void* stream);
 
 /*
+ * fc_sample_usts_ex with the forest of every tree (NULL skips an output):
+ *   roots    int32 [rows][n]   roots[t][v] = the root of v's tree in the rooted
+ *            spanning forest of G that tree t of G* leaves without u* (the
+ *            vertex on v's path to u* whose parent is u*); by the matrix-forest
+ *            theorem (Sec. 2) P(roots[t][v] = u) = Omega[u, v]
+ *   depths   int32 [rows][n]   the number of edges from v to its root
+ * rows and indexing as parents (n_alpha * tau rows, or tau rows of the union
+ * for a batch).  The edge-record kernel without clusters writes both as
+ * vertices join the tree, with no pass over the parents; otherwise they come
+ * from fc_tree_roots on the parents (allocated internally when parents is
+ * NULL).  Everything else as fc_sample_usts_ex.  Synchronises `stream`.
+ */
+fc_status fc_sample_usts_forest(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R,
+                                uint32_t* C, int32_t* parents, int32_t* roots, int32_t* depths, uint64_t* visits,
+                                uint64_t max_steps_per_tree, uint64_t* steps_out, void* stream);
+
+/*
  * fc_sample_usts without the synchronising error read-back, for enqueueing on
  * a stream that is being captured into a CUDA graph (the persistent sampling
  * launch, its memsets and the combinations after it become graph nodes).

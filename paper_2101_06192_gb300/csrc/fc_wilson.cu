@@ -590,12 +590,20 @@ using namespace fcx;
 
 static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R, uint32_t* C,
                              int32_t* parents, uint64_t* visits, uint64_t max_steps_per_tree, uint64_t* steps_out,
-                             void* stream, bool sync);
+                             void* stream, bool sync, int32_t* roots = nullptr, int32_t* depths = nullptr);
 
 extern "C" fc_status fc_sample_usts(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R,
                                     uint32_t* C, int32_t* parents, uint64_t max_steps_per_tree,
                                     uint64_t* steps_out, void* stream) {
   return sample_impl(g, seed, tau, tree_offset, R, C, parents, nullptr, max_steps_per_tree, steps_out, stream, true);
+}
+
+extern "C" fc_status fc_sample_usts_forest(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R,
+                                           uint32_t* C, int32_t* parents, int32_t* roots, int32_t* depths,
+                                           uint64_t* visits, uint64_t max_steps_per_tree, uint64_t* steps_out,
+                                           void* stream) {
+  return sample_impl(g, seed, tau, tree_offset, R, C, parents, visits, max_steps_per_tree, steps_out, stream, true,
+                     roots, depths);
 }
 
 extern "C" fc_status fc_sample_usts_ex(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R,
@@ -633,10 +641,22 @@ extern "C" fc_status fc_sampler_check(fc_graph* g, void* stream) {
   return FC_OK;
 }
 
+namespace {
+// device scratch released on the stream when the call returns
+struct StreamScratch {
+  void* ptr = nullptr;
+  cudaStream_t st = nullptr;
+  ~StreamScratch() {
+    if (ptr) cudaFreeAsync(ptr, st);
+  }
+};
+}  // namespace
+
 static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tree_offset, uint32_t* R, uint32_t* C,
                              int32_t* parents, uint64_t* visits, uint64_t max_steps_per_tree, uint64_t* steps_out,
-                             void* stream, bool sync) {
-  if (g == nullptr || R == nullptr || tau < 0 || tree_offset < 0 || tree_offset + tau > (int64_t(1) << 32)) {
+                             void* stream, bool sync, int32_t* roots, int32_t* depths) {
+  if (g == nullptr || R == nullptr || tau < 0 || tree_offset < 0 || tree_offset + tau > (int64_t(1) << 32) ||
+      ((roots != nullptr || depths != nullptr) && !sync)) {
     set_error("fc_sample_usts: bad argument");
     return FC_EINVAL;
   }
@@ -733,10 +753,16 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   if (g->max_trees > 0) grid = std::min<int64_t>(grid, g->max_trees);
   void* gstate = nullptr;
   uint32_t* gbits = nullptr;
+  unsigned long long* rdpack = nullptr;
+  // forest roots and depths: recorded by the edge-record kernel as vertices
+  // join the tree (no clusters), else by pointer jumping over the parents
+  const bool want_roots = roots != nullptr || depths != nullptr;
+  const bool fused_roots = want_roots && edge && cl == 1;
   if (!use_smem) {
     // keep the per-tree state within a quarter of the device memory
     const size_t words = (edge && bits != 2) ? 0 : ((size_t)nmax + 31) / 32;  // global in-tree bitmaps
-    const size_t per_tree = (size_t)nmax * sizeof(VState) + ((words * 4 + 255) & ~(size_t)255);
+    const size_t per_tree = (size_t)nmax * sizeof(VState) + ((words * 4 + 255) & ~(size_t)255) +
+                            (fused_roots ? (size_t)nmax * 8 : 0);
     const size_t cap_trees = std::max<size_t>(1, (g->device_bytes / 4) / per_tree);
     grid = std::min<int64_t>(grid, (int64_t)cap_trees);
     void* ws = nullptr;  // state (and global bitmaps) of `grid` tree slots
@@ -744,6 +770,9 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
     if (s != FC_OK) return s;
     gstate = ws;
     gbits = (uint32_t*)((char*)ws + (size_t)grid * nmax * sizeof(VState));
+    if (fused_roots)
+      rdpack = (unsigned long long*)((char*)ws + (size_t)grid * nmax * sizeof(VState) +
+                                     (size_t)grid * ((words * 4 + 255) & ~(size_t)255));
   }
   g->last_W = W;
   g->last_regs = sh.regs;
@@ -771,6 +800,16 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   p.R = R;
   p.C = C;
   p.parents = parents;
+  const size_t prow = (size_t)(batch ? tau : (int64_t)g->n_alpha * tau);  // parent rows of the call
+  StreamScratch pscr;
+  pscr.st = st;
+  p.roots = fused_roots ? roots : nullptr;
+  p.depths = fused_roots ? depths : nullptr;
+  p.rdpack = rdpack;
+  if (want_roots && !fused_roots && parents == nullptr) {  // pointer jumping needs the parents
+    FC_CK(cudaMallocAsync(&pscr.ptr, prow * (size_t)n * sizeof(int32_t), st));
+    p.parents = (int32_t*)pscr.ptr;
+  }
   p.visits = (unsigned long long*)visits;
   p.steps = steps_out;
   p.gstate = (VState*)gstate;
@@ -829,7 +868,8 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   FC_CK(cudaMemsetAsync(g->d_counter, 0, sizeof(unsigned long long), st));
   if (sync) FC_CK(cudaMemsetAsync(g->d_err, 0, sizeof(uint32_t), st));
   FC_CK(cudaMemsetAsync(g->d_stats, 0, (2 + N_CNT) * sizeof(unsigned long long), st));
-  const WilsonFn fn = edge ? wilson_edge_fn(bits, g->weighted, ring, cl > 1, sh.regs) : wilson_fn(use_smem, sh.regs);
+  const WilsonFn fn = edge ? wilson_edge_fn(bits, g->weighted, ring, cl > 1, sh.regs, fused_roots)
+                            : wilson_fn(use_smem, sh.regs);
   if (use_smem || edge) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
   if (cl > 1) {
     cudaLaunchConfig_t cfg = {};
@@ -870,6 +910,13 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   if (herr != 0) {
     set_error("fc_sample_usts: internal consistency check failed");
     return FC_ECUDA;
+  }
+  if (want_roots && !fused_roots) {
+    StreamScratch r2;
+    r2.st = st;
+    if (roots == nullptr) FC_CK(cudaMallocAsync(&r2.ptr, prow * (size_t)n * sizeof(int32_t), st));
+    const fc_status s = fc_tree_roots(p.parents, n, (int64_t)prow, roots ? roots : (int32_t*)r2.ptr, depths, st);
+    if (s != FC_OK) return s;
   }
   return FC_OK;
 }

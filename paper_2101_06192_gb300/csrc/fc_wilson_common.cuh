@@ -58,6 +58,13 @@ struct WParams {
   // only once its tree holds at least w * ramp_q vertices (or every start
   // position is handed out); 0 = every warp from the start
   uint32_t ramp_q;
+  // forest roots and depths ([rows][n] like parents, either may be null;
+  // edge-record kernel without clusters): each vertex's {root, depth} is put
+  // in rdpack ([gridDim.x][nmax], 8 bytes) when it joins the tree and copied
+  // out by the end-of-tree pass
+  int32_t* roots;
+  int32_t* depths;
+  unsigned long long* rdpack;
 };
 
 // Pop and release walks read a vertex's nxt, then free the vertex with an
@@ -143,7 +150,7 @@ typedef void (*WilsonFn)(WParams);
 // walking them, one CTA per tree or a cluster of CTAs per tree (cl; bits 0 or
 // 1), for a register cap of 48 or 64 (lower caps map to 48), and its dynamic
 // shared memory per CTA in a cluster of C CTAs.
-WilsonFn wilson_edge_fn(int bits, bool wgt, bool ring, bool cl, int regs);
+WilsonFn wilson_edge_fn(int bits, bool wgt, bool ring, bool cl, int regs, bool roots = false);
 size_t wilson_edge_smem(int W, int32_t n, int bits, bool wgt, int C);  // bits: 0 flags, 1 shared bitmap, 2 global
 
 }  // namespace fcx

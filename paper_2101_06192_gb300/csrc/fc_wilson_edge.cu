@@ -46,6 +46,10 @@ constexpr int EW_BITS = 13;
 constexpr uint32_t EW_MASK = (1u << EW_BITS) - 1u;
 constexpr uint32_t GEN_LIMIT = (1u << (39 - EW_BITS)) - 1u;
 
+__device__ __forceinline__ unsigned long long rd_pack(int32_t root, int32_t depth) {
+  return (unsigned long long)(uint32_t)root | ((unsigned long long)(uint32_t)depth << 32);
+}
+
 __device__ __forceinline__ uint32_t thr_hi(const uint4& ri) {
   const uint64_t T = (uint64_t)ri.z | ((uint64_t)ri.w << 32);
   return T >= (1ull << 53) ? 0xffffffffu : (uint32_t)(T >> 21);
@@ -94,7 +98,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // and departure totals; the bitmap is interleaved by 32-bit word over the
 // ranks; walker generations are read across the cluster (distributed shared
 // memory).  Cluster barriers separate the trees.
-template <int BITS, bool WGT, bool RINGP, bool CL, int MAXREG>
+//
+// ROOTS: forest roots and depths of every tree (the roots are the children of
+// u*), written as vertices join the tree: a path that exits to u* at its head
+// h roots all its vertices at h, one that reaches tree vertex x inherits x's
+// root, and depths count down the path to the root.  A vertex's root and
+// depth are stored before its membership becomes visible (a fence between;
+// every reader is a walker of the same CTA, so a CTA-scope fence), so a walker
+// that sees x in the tree reads x's final values.
+template <int BITS, bool WGT, bool RINGP, bool CL, int MAXREG, bool ROOTS>
 __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long sh_tree, sh_pops, sh_deps;
@@ -219,6 +231,8 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
     if (CL) cg::this_cluster().sync();
     else __syncthreads();
     const uint4* __restrict__ rinfo = p.rowinfo + (size_t)a * n;
+    // {root, depth} of this tree's vertices, packed (root low word), by local index
+    unsigned long long* RD = ROOTS ? p.rdpack + tslot * (size_t)p.nmax : nullptr;
     const uint4* __restrict__ edges = p.edges + (size_t)a * p.nnz * (WGT ? 4 : 1);
     const uint64_t* __restrict__ Brow = WGT ? p.B + (size_t)a * p.nnz : nullptr;
 
@@ -228,6 +242,8 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
     uint32_t xo = 0, xd = 0, xth = 0;  // row offset, degree and T_hi of x
     uint32_t cur = 0;                  // WGT: buffer holding x's slot thresholds
     bool rskip = false;
+    bool fexit = false;                             // ROOTS: the finished path left to u*
+    int32_t froot = 0, fdl = 0, flen = 0, fpos = 0;  // ROOTS: root, depth base, length, position
     uint32_t gen = 1, kx = 0, iters = 0, pops = 0, deps = 0;
     unsigned long long wtag = 0, cexp = 0;
     uint32_t whead = 0, wcnt = 0;  // warp-uniform: window entries [whead, wcnt) not handed out yet
@@ -446,6 +462,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
                 atomicAdd(p.R + (size_t)a * n + x, 1u);
                 if (p.C != nullptr && kx == 0u) atomicAdd(p.C + (size_t)a * n + x, 1u);
                 finished = true;
+                fexit = true;
                 break;
               }
               x = (int32_t)er.x;
@@ -579,6 +596,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             if (!nb) {
               atomicAdd(p.R + (size_t)a * n + x, 1u);
               finished = true;  // kx > 0 here: the control variate counts entry 0 only
+              fexit = true;
               break;
             }
             x = (int32_t)er.x;
@@ -599,7 +617,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             if (!rskip) {
               if (nxt_read(nc)) ADD_ST(c, 1ull - (mytag << K_BITS));
               ++pops;
-              if (RINGP) ++rh;
+              if (RINGP || ROOTS) ++rh;
             }
             rskip = false;
             c = (int32_t)nc;
@@ -619,11 +637,13 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
                 rbase = len - 1;
                 RING(rbase) = (uint32_t)x;
               } else {
-                // the path now ends at x
+                // the path now ends at x (with ROOTS the length stays exact
+                // when x lies beyond the prefix: depths count along the path)
                 int32_t pos = len;
                 for (int i = 0; i < PB; ++i)
                   if (i < len && sh_pb[i * W + me] == (uint32_t)x) pos = i;
                 if (pos < PB) len = pos + 1;
+                else if (ROOTS) len -= rh;
               }
               h = x;
               mode = E_TOP;
@@ -632,12 +652,20 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
           }
           case E_RETRACE: {
             if (!rskip) {
+              if (ROOTS) {
+                RD[c - base] = rd_pack(froot, fdl + (flen - 1 - fpos));
+                __threadfence_block();  // every reader is in this CTA (no clusters)
+              }
               if (BITS != 0) atomicOr((uint32_t*)BITW(c), 1u << (c & 31));
               else OR_ST(c, IN_TREE);
             }
             rskip = false;
-            if (RINGP ? --rh == 0 : c == rh) mode = E_IDLE;
-            else c = (int32_t)nc;
+            if (RINGP ? --rh == 0 : c == rh) {
+              mode = E_IDLE;
+            } else {
+              c = (int32_t)nc;
+              ++fpos;
+            }
             break;
           }
           case E_RELEASE: {
@@ -671,6 +699,29 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             sh_gen[me] = gen;
             // ring: slots in use in any order; prefix: the first min(len, PB)
             const int32_t held = RINGP ? len - rbase : len;
+            if (ROOTS) {
+              // root and depth base: the head's own (exit to u*) or x's, read
+              // after x was seen in the tree
+              if (fexit) {
+                froot = h;
+                fdl = 0;
+              } else {
+                const unsigned long long rx = *(volatile unsigned long long*)&RD[x - base];
+                froot = (int32_t)(uint32_t)rx;
+                fdl = (int32_t)(uint32_t)(rx >> 32) + 1;
+              }
+              flen = len;
+#pragma unroll
+              for (int i = 0; i < PB; ++i) {
+                const int32_t q = RINGP ? rbase + ((i - rbase) & (PB - 1)) : i;  // path position of slot i
+                if (q - (RINGP ? rbase : 0) < held) {
+                  const uint32_t v = sh_pb[i * W + me];
+                  RD[v - base] = rd_pack(froot, fdl + (len - 1 - q));
+                }
+              }
+              __threadfence_block();
+              fpos = RINGP ? 0 : PB - 1;  // where the walk from s (or the prefix's end) starts
+            }
 #pragma unroll
             for (int i = 0; i < PB; ++i) {
               if ((RINGP ? ((i - rbase) & (PB - 1)) : i) < held) {
@@ -698,6 +749,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
           h = -1;
           len = 0;
           rbase = 0;
+          fexit = false;
         }
       }
 
@@ -763,6 +815,14 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
       int32_t* par = p.parents + (p.num_graphs > 0 ? (size_t)tloc : (size_t)tree) * n + base;
       for (int32_t v = (int32_t)wid; v < nl; v += (int32_t)WT) par[v] = (int32_t)S[v].nxt;
     }
+    if (ROOTS) {  // the forest, copied out coalesced
+      const size_t row = (p.num_graphs > 0 ? (size_t)tloc : (size_t)tree) * (size_t)n + (size_t)base;
+      for (int32_t v = (int32_t)wid; v < nl; v += (int32_t)WT) {
+        const unsigned long long pk = RD[v];
+        if (p.roots) p.roots[row + v] = (int32_t)(uint32_t)pk;
+        if (p.depths) p.depths[row + v] = (int32_t)(uint32_t)(pk >> 32);
+      }
+    }
     if (p.visits != nullptr) {  // departures from v = its popped stack entries + the tree edge's
       unsigned long long* vis = p.visits + (size_t)a * n + base;
       for (int32_t v = (int32_t)wid; v < nl; v += (int32_t)WT) atomicAdd(&vis[v], (S[v].st & K_MASK) + 1ull);
@@ -791,7 +851,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
 
 template <int BITS, bool WGT, bool RINGP, bool CL>
 static WilsonFn edge_fn_regs(int regs) {
-  return regs <= 48 ? k_wilson_edge<BITS, WGT, RINGP, CL, 48> : k_wilson_edge<BITS, WGT, RINGP, CL, 64>;
+  return regs <= 48 ? k_wilson_edge<BITS, WGT, RINGP, CL, 48, false> : k_wilson_edge<BITS, WGT, RINGP, CL, 64, false>;
 }
 
 template <int BITS, bool WGT, bool CL>
@@ -804,7 +864,18 @@ static WilsonFn edge_fn_wgt(bool wgt, bool ring, int regs) {
   return wgt ? edge_fn_ring<BITS, true, CL>(ring, regs) : edge_fn_ring<BITS, false, CL>(ring, regs);
 }
 
-WilsonFn wilson_edge_fn(int bits, bool wgt, bool ring, bool cl, int regs) {
+// forest-root variants: 64 registers, no clusters
+template <int BITS, bool WGT>
+static WilsonFn edge_fn_roots(bool ring) {
+  return ring ? k_wilson_edge<BITS, WGT, true, false, 64, true> : k_wilson_edge<BITS, WGT, false, false, 64, true>;
+}
+
+WilsonFn wilson_edge_fn(int bits, bool wgt, bool ring, bool cl, int regs, bool roots) {
+  if (roots) {
+    if (bits == 1) return wgt ? edge_fn_roots<1, true>(ring) : edge_fn_roots<1, false>(ring);
+    if (bits == 2) return wgt ? edge_fn_roots<2, true>(ring) : edge_fn_roots<2, false>(ring);
+    return wgt ? edge_fn_roots<0, true>(ring) : edge_fn_roots<0, false>(ring);
+  }
   if (cl) return bits == 1 ? edge_fn_wgt<1, true>(wgt, ring, regs) : edge_fn_wgt<0, true>(wgt, ring, regs);
   if (bits == 1) return edge_fn_wgt<1, false>(wgt, ring, regs);
   if (bits == 2) return edge_fn_wgt<2, false>(wgt, ring, regs);

@@ -81,6 +81,7 @@ def lib():
             "fc_laplacian_solve": ([P, P, P, I32, D, I32, P, P], ctypes.c_int),
             "fc_electrical_closeness": ([P, P, P, I64, P, P, P, P, P, P], ctypes.c_int),
             "fc_sample_usts_ex": ([P, U64, I64, I64, P, P, P, P, U64, P, P], ctypes.c_int),
+            "fc_sample_usts_forest": ([P, U64, I64, I64, P, P, P, P, P, P, U64, P, P], ctypes.c_int),
             "fc_visit_diag": ([P, I32, P, I64, P, P], ctypes.c_int),
             "fc_destroy": ([P], None),
             "fc_status_str": ([ctypes.c_int], ctypes.c_char_p),
@@ -319,9 +320,10 @@ class Graph:
 
     def sample(self, seed: int, tau: int, tree_offset: int = 0, R=None, C=None, with_C: bool = True,
                want_parents: bool = False, want_steps: bool = False, max_steps_per_tree: int = 0,
-               visits=None, want_visits: bool = False, stream=None):
-        """fc_sample_usts (fc_sample_usts_ex when visit totals are wanted).  R, C
-        and visits accumulate (allocated zeroed when not given)."""
+               visits=None, want_visits: bool = False, want_roots: bool = False, stream=None):
+        """fc_sample_usts (fc_sample_usts_ex when visit totals are wanted,
+        fc_sample_usts_forest when forest roots and depths are).  R, C and
+        visits accumulate (allocated zeroed when not given)."""
         dev = torch.device("cuda", torch.cuda.current_device())
         na, n = self.n_alpha, self.n
         if R is None:
@@ -336,8 +338,16 @@ class Graph:
         steps = torch.zeros(nrow * tau, dtype=torch.int64, device=dev) if want_steps else None
         if visits is None and want_visits:
             visits = torch.zeros(na * n, dtype=torch.int64, device=dev)
+        roots = torch.empty(na * tau * n, dtype=torch.int32, device=dev) if want_roots else None
+        depths = torch.empty(na * tau * n, dtype=torch.int32, device=dev) if want_roots else None
         if visits is not None:
             _dev_tensor(visits, torch.int64, na * n, "visits")
+        if want_roots:
+            _check(lib().fc_sample_usts_forest(self._h, int(seed) & (2**64 - 1), int(tau), int(tree_offset), _ptr(R),
+                                               _ptr(C), _ptr(parents), _ptr(roots), _ptr(depths), _ptr(visits),
+                                               int(max_steps_per_tree), _ptr(steps), _stream(stream)),
+                   "fc_sample_usts_forest")
+        elif visits is not None:
             _check(lib().fc_sample_usts_ex(self._h, int(seed) & (2**64 - 1), int(tau), int(tree_offset), _ptr(R),
                                            _ptr(C), _ptr(parents), _ptr(visits), int(max_steps_per_tree),
                                            _ptr(steps), _stream(stream)), "fc_sample_usts_ex")
@@ -348,6 +358,9 @@ class Graph:
         out = {"R": R, "C": C, "visits": visits}
         if want_parents:
             out["parents"] = parents.view(na, tau, n)
+        if want_roots:
+            out["roots"] = roots.view(na, tau, n)
+            out["depths"] = depths.view(na, tau, n)
         if want_steps:
             out["steps"] = steps.view(getattr(self, "num_graphs", 0) or na, tau)
         return out
