@@ -1150,6 +1150,9 @@ def main():
     colidx_d = torch.from_numpy(g.colidx).to(dev)
     rowptr_h = torch.from_numpy(g.rowptr).pin_memory()
     colidx_h = torch.from_numpy(g.colidx).pin_memory()
+    # the results read back in the end-to-end steps land in pinned host buffers
+    clo_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    top_h = torch.empty(TOPK, dtype=torch.int32).pin_memory()
     R = torch.zeros(n, dtype=torch.int32, device=dev)
     C = torch.zeros(n, dtype=torch.int32, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -1185,7 +1188,10 @@ def main():
         G.close()
         last_diag[0] = diag
         if host_inputs:
-            return clo.cpu(), top.cpu()
+            clo_h.copy_(clo, non_blocking=True)
+            top_h.copy_(top, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            return clo_h, top_h
         return clo, top
 
     def barrier():

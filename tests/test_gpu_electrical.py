@@ -307,3 +307,33 @@ def test_full_size_ba_hub_pivot_bit_exact():
     exp = sum(el.fixed_point(el.path_sums_np(g, root, bpar, binv, p)) for p in ref["parents"])
     np.testing.assert_array_equal(acc.cpu().numpy(), exp)
     G.close()
+
+
+def test_full_size_ba_hub_benchmark_shape_bit_exact():
+    """The electrical benchmark's sampler launch at full size: BA n = 2^20,
+    m = 8 rooted at its largest hub, the automatic rooted shape (128 walkers
+    per tree, tree membership as state flags, one CTA per tree, reverse
+    breadth-first start order, the walker ramp), 152 trees at once: parents,
+    step counts and visit totals equal the oracle's."""
+    import concurrent.futures as cf
+    g = synth.barabasi_albert(1 << 20, 8, 2)
+    root = int(np.argmax(g.degrees()))
+    G = fc.Graph.rooted(g, root)
+    G.set_cluster(1)
+    tau = 152
+    out = G.sample(4242, tau, want_parents=True, want_steps=True, want_visits=True, with_C=False)
+    assert G.last_kernel() == 2 and G.last_cluster() == 1
+    assert G.last_shape()["walkers_per_tree"] == 128
+    cuts = np.linspace(0, tau, 17).astype(int)
+    with cf.ThreadPoolExecutor(max_workers=16) as ex:
+        parts = list(ex.map(lambda ab: native.wilson_rooted(g, root, seed=4242, tau=int(ab[1] - ab[0]),
+                                                            tree_offset=int(ab[0]), want_visits=True),
+                            [(a, b) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]))
+    par = out["parents"][0].cpu().numpy()
+    np.testing.assert_array_equal(par, np.concatenate([p["parents"] for p in parts]))
+    steps = np.concatenate([p["steps"] for p in parts])
+    np.testing.assert_array_equal(out["steps"][0].cpu().numpy().astype(np.uint64), steps + 1)
+    exp = np.sum([p["visits"] for p in parts], axis=0, dtype=np.uint64)
+    exp[root] = tau
+    np.testing.assert_array_equal(out["visits"].cpu().numpy().astype(np.uint64), exp)
+    G.close()
