@@ -445,10 +445,32 @@ __device__ __forceinline__ void tile_load(const TileArgs<V>& a, int64_t t, TileI
   }
 }
 
+// Folded form (FP32 inner CG): a tile finishes q_v = diag_v p_v - alpha s_v
+// of every row that lies inside it, and every tile adds its rows' terms of
+// p.q to a per-lane partial: p_v q_v for rows inside, and for a row that
+// crosses tiles the linear pieces p_v diag_v p_v (in the tile where it
+// starts) and -alpha p_v times the tile's partial (in every tile it touches).
+struct Fold {
+  const float* diag;
+  float alpha;
+  float* q;
+};
+
 // One tile of s = W x, by one whole warp, from its loaded indices.
-template <typename V>
+template <typename V, bool FOLD = false>
 __device__ void tile_finish(const TileArgs<V>& a, const V* __restrict__ x, int64_t t, const TileIn& ti,
-                            int32_t* __restrict__ soff) {
+                            int32_t* __restrict__ soff, const Fold& fo = Fold{}, float* pq = nullptr) {
+  // a row's sum is complete: store it, or (folded) finish q and p.q
+  auto put_row = [&](int32_t v, V sv) {
+    if (FOLD) {
+      const float pv = (float)x[v];
+      const float qv = pv * fo.diag[v] - fo.alpha * (float)sv;
+      fo.q[v] = qv;
+      *pq = fmaf(pv, qv, *pq);
+    } else {
+      a.s[v] = sv;
+    }
+  };
   const int lane = threadIdx.x & 31;
   const int64_t E0 = t * TL;
   const int ne = (int)std::min<int64_t>(TL, a.nnz - E0);
@@ -490,7 +512,7 @@ __device__ void tile_finish(const TileArgs<V>& a, const V* __restrict__ x, int64
               ef = true;
               first = false;
             } else {
-              a.s[rs + cur] = acc;
+              put_row(rs + cur, acc);
             }
             acc = 0;
             ++cur;
@@ -534,7 +556,7 @@ __device__ void tile_finish(const TileArgs<V>& a, const V* __restrict__ x, int64
               ef = true;
               first = false;
             } else if (beg < nxt) {
-              a.s[rs + cur] = acc;
+              put_row(rs + cur, acc);
             }
             acc = 0;
             ++cur;
@@ -567,13 +589,26 @@ __device__ void tile_finish(const TileArgs<V>& a, const V* __restrict__ x, int64
   if (cnt > 0) {
     if (ef) {
       const V tot = (lane > 0 && kp == rf ? Sp : (V)0) + pf;
-      if (rf == 0 && before) a.head[t] = tot;
-      else a.s[rs + rf] = tot;
+      if (rf == 0 && before) {
+        a.head[t] = tot;
+        if (FOLD) *pq = fmaf(-fo.alpha * (float)x[rs], (float)tot, *pq);
+      } else {
+        put_row(rs + rf, tot);
+      }
     }
-    if (rl != rf && el) a.s[rs + rl] = pl;
+    if (rl != rf && el) put_row(rs + rl, pl);
     if (le0 + cnt == ne && !el) {  // the tile's last row goes on into the next tile
-      if (rl == 0 && before) a.head[t] = S;
-      else a.tail[t] = S;
+      if (rl == 0 && before) {
+        a.head[t] = S;
+        if (FOLD) *pq = fmaf(-fo.alpha * (float)x[rs], (float)S, *pq);
+      } else {
+        a.tail[t] = S;
+        if (FOLD) {
+          const int32_t v = rs + rl;
+          const float pv = (float)x[v];
+          *pq = fmaf(pv, pv * fo.diag[v] - fo.alpha * (float)S, *pq);
+        }
+      }
     }
   }
   __syncwarp();
@@ -581,14 +616,15 @@ __device__ void tile_finish(const TileArgs<V>& a, const V* __restrict__ x, int64
 
 // The tiles t0, t0 + stride, ... of one warp, each tile's indices loaded
 // while the previous tile is summed.
-template <typename V>
+template <typename V, bool FOLD = false>
 __device__ __forceinline__ void tile_loop(const TileArgs<V>& a, const V* __restrict__ x, int64_t ntiles, int64_t t0,
-                                          int64_t stride, int32_t* __restrict__ soff) {
+                                          int64_t stride, int32_t* __restrict__ soff, const Fold& fo = Fold{},
+                                          float* pq = nullptr) {
   TileIn cur, nxt;
   if (t0 < ntiles) tile_load(a, t0, cur);
   for (int64_t t = t0; t < ntiles; t += stride) {
     if (t + stride < ntiles) tile_load(a, t + stride, nxt);
-    tile_finish(a, x, t, cur, soff);
+    tile_finish<V, FOLD>(a, x, t, cur, soff, fo, pq);
     cur = nxt;
   }
 }
@@ -612,15 +648,21 @@ __device__ __forceinline__ V row_total(const TileArgs<V>& a, int64_t v) {
 
 // the span bitmap: bit v set when row v is empty or its entries fall in
 // more than one tile
-__global__ void k_span_bits(int32_t n, const int64_t* __restrict__ rowptr, uint32_t* __restrict__ span) {
+__global__ void k_span_bits(int32_t n, const int64_t* __restrict__ rowptr, uint32_t* __restrict__ span,
+                            uint32_t* __restrict__ nempty) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool f = false;
+  bool f = false, e = false;
   if (v < n) {
     const int64_t e0 = rowptr[v], e1 = rowptr[v + 1];
-    f = e1 <= e0 || e0 / TL != (e1 - 1) / TL;
+    e = e1 <= e0;
+    f = e || e0 / TL != (e1 - 1) / TL;
   }
   const uint32_t bits = __ballot_sync(0xffffffffu, f);
-  if ((threadIdx.x & 31) == 0 && v < n) span[v >> 5] = bits;
+  const uint32_t empties = __ballot_sync(0xffffffffu, e);
+  if ((threadIdx.x & 31) == 0 && v < n) {
+    span[v >> 5] = bits;
+    if (empties) atomicAdd(nempty, (uint32_t)__popc(empties));
+  }
 }
 
 // FP64 s = W x by tiles (the residual of the refinement loop)
@@ -703,7 +745,13 @@ __device__ __forceinline__ void block_fixed_sum2(const double* a, const double* 
   sb = slot[1];
 }
 
-__global__ void __launch_bounds__(SV_T, 4) k_cg1(CG1 c) {
+// FOLD (graphs without empty rows): phase A also finishes q and the p.q
+// partials, and B1 disappears (three grid barriers per iteration); measured on
+// GB300 with 80 registers (3 CTAs per SM; 64 spill): BA 2^20 4.35 -> 4.09 ms
+// per solve, 2048^2 grid unchanged (10.7 ms: the tile phase takes longer by
+// the per-row loads of p and the diagonal that B1 did in bulk)
+template <bool FOLD>
+__global__ void __launch_bounds__(SV_T, FOLD ? 3 : 4) k_cg1(CG1 c) {
   cgr::grid_group grid = cgr::this_grid();
   __shared__ TileSmem sm;
   __shared__ double slots[4];
@@ -723,13 +771,19 @@ __global__ void __launch_bounds__(SV_T, 4) k_cg1(CG1 c) {
   float4* q4w = reinterpret_cast<float4*>(c.in.q);
   double rz = c.rz0;
   int it = 0;
+  const Fold fo{c.diag32, c.alpha, c.in.q};
   while (it < c.max_it) {
+    float pqf = 0.0f;
+    if (FOLD) {
+      // A: q = diag p - alpha W p for the rows inside a tile, p.q partials
+      tile_loop<float, true>(c.ta, c.in.p, c.ntiles, (int64_t)blockIdx.x * TL_W + wid, (int64_t)G * TL_W,
+                             sm.off[wid], fo, &pqf);
+    } else {
     // A: s = W p
     tile_loop(c.ta, c.in.p, c.ntiles, (int64_t)blockIdx.x * TL_W + wid, (int64_t)G * TL_W, sm.off[wid]);
     grid.sync();
     // B1: q = diag p - alpha s (rows marked in the span bitmap from their
     // tile partials)
-    float pqf = 0.0f;
     for (int64_t i = gtid; i < n4; i += gstride) {
       const float4 p = p4[i], dg = g4[i];
       float4 sv = s4[i];
@@ -753,6 +807,7 @@ __global__ void __launch_bounds__(SV_T, 4) k_cg1(CG1 c) {
       c.in.q[v] = qv;
       pqf = fmaf(pv, qv, pqf);
     }
+    }
     double pq = pqf, unused = 0.0;
     block_sum2(pq, unused);
     if (threadIdx.x == 0) c.part[blockIdx.x] = pq;
@@ -763,8 +818,19 @@ __global__ void __launch_bounds__(SV_T, 4) k_cg1(CG1 c) {
     // B2: d += a p, r -= a q
     float rzf = 0.0f, rrf = 0.0f;
     for (int64_t i = gtid; i < n4; i += gstride) {
-      const float4 p = p4[i], q = q4[i];
+      const float4 p = p4[i];
+      float4 q = q4[i];
       float4 r = r4[i], d = d4[i];
+      if (FOLD) {  // rows that cross tiles: q from their tile partials
+        const uint32_t mk = (c.ta.span[i >> 3] >> ((i & 7) * 4)) & 0xFu;
+        if (mk) {
+          const float4 dg = g4[i];
+          if (mk & 1u) q.x = p.x * dg.x - c.alpha * row_total_span(c.ta, 4 * i);
+          if (mk & 2u) q.y = p.y * dg.y - c.alpha * row_total_span(c.ta, 4 * i + 1);
+          if (mk & 4u) q.z = p.z * dg.z - c.alpha * row_total_span(c.ta, 4 * i + 2);
+          if (mk & 8u) q.w = p.w * dg.w - c.alpha * row_total_span(c.ta, 4 * i + 3);
+        }
+      }
       d.x += a * p.x; d.y += a * p.y; d.z += a * p.z; d.w += a * p.w;
       r.x -= a * q.x; r.y -= a * q.y; r.z -= a * q.z; r.w -= a * q.w;
       d4[i] = d;
@@ -777,7 +843,10 @@ __global__ void __launch_bounds__(SV_T, 4) k_cg1(CG1 c) {
     }
     for (int64_t v = 4 * n4 + gtid; v < n; v += gstride) {
       c.in.d[v] += a * c.in.p[v];
-      const float rv = c.in.r[v] - a * c.in.q[v];
+      const float qv = FOLD && ((c.ta.span[v >> 5] >> (v & 31)) & 1u)
+                           ? c.in.p[v] * c.diag32[v] - c.alpha * row_total_span(c.ta, v)
+                           : c.in.q[v];
+      const float rv = c.in.r[v] - a * qv;
       c.in.r[v] = rv;
       rzf = fmaf(rv, c.prec ? rv * c.prec[v] : rv, rzf);
       rrf = fmaf(rv, rv, rrf);
@@ -1067,13 +1136,14 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
   TileArgs<float> t32{};
   void* tile_mem = nullptr;
   int tile_grid = 0;
+  bool fold = false;  // q and p.q in the tile phase (graphs without empty rows)
   int cg1_grid = 0;
   double* cg1_part = nullptr;
   if (tiles) {
     const size_t nt = (size_t)std::max<int64_t>(ntiles, 1);
     // [s32 n4][s64 n4][head64 nt][tail64 nt][head32 nt][tail32 nt][row0 nt][row1 nt][meta nt TL_T][span]
     const size_t nsw = ((size_t)n + 31) / 32;
-    const size_t bytes = np4 * 12 + nt * 16 + nt * 8 + nt * 8 + nt * TL_T * 4 + nsw * 4;
+    const size_t bytes = np4 * 12 + nt * 16 + nt * 8 + nt * 8 + nt * TL_T * 4 + nsw * 4 + 16;
     FC_CK(cudaMallocAsync(&tile_mem, bytes, st));
     t32.s = (float*)tile_mem;  // 16-byte aligned: B1 reads it four-wide
     t64.s = (double*)(t32.s + np4);
@@ -1085,6 +1155,7 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
     int32_t* row1 = row0 + nt;
     uint32_t* meta = (uint32_t*)(row1 + nt);
     uint32_t* span = meta + nt * TL_T;
+    uint32_t* nempty = span + nsw;  // rows without entries
     const bool vec = ((uintptr_t)g->colidx % 16 == 0) && (g->w == nullptr || (uintptr_t)g->w % 16 == 0);
     t64.nnz = g->nnz;
     t64.rowptr = g->rowptr;
@@ -1111,13 +1182,18 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
           g->nnz, g->rowptr, ntiles, row0, row1, meta);
       FC_LAUNCHED();
     }
-    k_span_bits<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, g->rowptr, span);
+    FC_CK(cudaMemsetAsync(nempty, 0, sizeof(uint32_t), st));
+    k_span_bits<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, g->rowptr, span, nempty);
     FC_LAUNCHED();
+    uint32_t h_nempty = 1;
+    FC_CK(cudaMemcpyAsync(&h_nempty, nempty, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    FC_CK(cudaStreamSynchronize(st));
+    fold = h_nempty == 0;
     int coop = 0, per_sm = 0, nsm = 0;
     FC_CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device));
     FC_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device));
     tile_grid = (int)std::max<int64_t>(1, std::min<int64_t>((ntiles + TL_W - 1) / TL_W, (int64_t)8 * nsm));
-    FC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg1, SV_T, 0));
+    FC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fold ? k_cg1<true> : k_cg1<false>, SV_T, 0));
     if (coop && per_sm > 0) {
       cg1_grid = std::min(per_sm, 8) * nsm;
       FC_CK(cudaMallocAsync((void**)&cg1_part, (3 * (size_t)cg1_grid + 1) * sizeof(double), st));
@@ -1199,7 +1275,8 @@ static fc_status solve_impl(fc_graph* g, int32_t alpha_idx, const double* b, dou
       c.max_it = max_iter - used;
       c.iters_out = (int*)(cg1_part + 3 * cg1_grid);
       void* args[] = {&c};
-      FC_CK(cudaLaunchCooperativeKernel((void*)k_cg1, dim3(cg1_grid), dim3(SV_T), args, 0, st));
+      FC_CK(cudaLaunchCooperativeKernel(fold ? (void*)k_cg1<true> : (void*)k_cg1<false>, dim3(cg1_grid),
+                                        dim3(SV_T), args, 0, st));
       FC_LAUNCHED();
       int done = 0;
       FC_CK(cudaMemcpyAsync(&done, c.iters_out, sizeof(int), cudaMemcpyDeviceToHost, st));
