@@ -211,8 +211,8 @@ struct fc_graph {
   int32_t last_kernel = 0;     // kernel of the last launch (1 or 2)
   int32_t last_W = 0, last_regs = 0, last_grid = 0;  // shape of the last launch
   // the launch-shape search's last inputs and result (reused while they repeat)
-  int64_t shape_key[10] = {};
-  int64_t shape_val[4] = {};
+  int64_t shape_key[12] = {};
+  int64_t shape_val[6] = {};
   bool shape_cached = false;
   // scratch owned by the graph
   void* ws = nullptr;          // sampler per-tree state

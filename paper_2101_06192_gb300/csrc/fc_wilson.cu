@@ -697,29 +697,6 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   // the state words (fc_set_sampler_bitmap; with global tree state forced by
   // the shape, flags); a global-memory bitmap runs without clusters.
   int cl = 1, bits = 0;
-  if (edge) {
-    const int wmin_e = g->walkers > 0 ? g->walkers : 32;
-    auto fits_c = [&](int c) {
-      return wilson_edge_smem(wmin_e, nmax, 1, g->weighted, c) + 64 <= (size_t)dev_smem_optin;
-    };
-    int c_util = 1;
-    while (c_util < 8 && total * (int64_t)(c_util * 2) <= (int64_t)nsm) c_util *= 2;
-    cl = g->cluster > 0 ? g->cluster : c_util;
-    if (g->bitmap_mode == 0) {
-      // rooted graphs: state flags, so that several small CTAs share an SM
-      bits = (g->root < 0 && g->smem_mode != 1 && fits_c(cl)) ? 1 : 0;
-    } else {
-      bits = g->bitmap_mode - 1;
-      if (bits == 1 && g->cluster == 0)
-        while (cl < 8 && !fits_c(cl)) cl *= 2;  // split the bitmap over a larger cluster
-      if (bits == 1 && !fits_c(cl)) {
-        set_error("fc_sample_usts: the in-tree bitmap does not fit in the shared memory of the cluster");
-        return FC_EINVAL;
-      }
-      if (bits == 2) cl = 1;
-    }
-  }
-  const bool sbits = bits == 1;
   // measured on GB300: popping short cycles from the ring gains 9% on a
   // road-like grid (mean degree 3.7, pops 44% of departures); the prefix
   // buffer stays 6% faster on BA m = 8 (pops 5%)
@@ -728,24 +705,66 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   // of the order of a millisecond): its result is kept for repeated launches
   // with the same inputs.
   Shape sh;
-  {
-    const int64_t key[10] = {nmax, total, use_smem, edge, bits, ring, cl, g->walkers, g->regs, g->weighted};
-    if (g->shape_cached && std::equal(key, key + 10, g->shape_key)) {
-      sh.W = (int)g->shape_val[0];
-      sh.regs = (int)g->shape_val[1];
-      sh.per_sm = (int)g->shape_val[2];
-      sh.slots = g->shape_val[3];
+  const int64_t key[12] = {nmax,      total,     use_smem, edge,        g->bitmap_mode, ring,
+                           g->cluster, g->walkers, g->regs, g->weighted, g->root >= 0,  g->smem_mode};
+  if (g->shape_cached && std::equal(key, key + 12, g->shape_key)) {
+    sh.W = (int)g->shape_val[0];
+    sh.regs = (int)g->shape_val[1];
+    sh.per_sm = (int)g->shape_val[2];
+    sh.slots = g->shape_val[3];
+    cl = (int)g->shape_val[4];
+    bits = (int)g->shape_val[5];
+  } else {
+    if (edge) {
+      const int wmin_e = g->walkers > 0 ? g->walkers : 32;
+      auto fits_c = [&](int c) {
+        return wilson_edge_smem(wmin_e, nmax, 1, g->weighted, c) + 64 <= (size_t)dev_smem_optin;
+      };
+      // rooted graphs: state flags, so that several small CTAs share an SM
+      auto auto_bits = [&](int c) { return (g->root < 0 && g->smem_mode != 1 && fits_c(c)) ? 1 : 0; };
+      int c_util = 1;
+      while (c_util < 8 && total * (int64_t)(c_util * 2) <= (int64_t)nsm) c_util *= 2;
+      cl = g->cluster > 0 ? g->cluster : c_util;
+      if (g->bitmap_mode == 0) {
+        bits = auto_bits(cl);
+      } else {
+        bits = g->bitmap_mode - 1;
+        if (bits == 1 && g->cluster == 0)
+          while (cl < 8 && !fits_c(cl)) cl *= 2;  // split the bitmap over a larger cluster
+        if (bits == 1 && !fits_c(cl)) {
+          set_error("fc_sample_usts: the in-tree bitmap does not fit in the shared memory of the cluster");
+          return FC_EINVAL;
+        }
+        if (bits == 2) cl = 1;
+      }
+      fc_status r = choose_shape(g, nmax, total, use_smem, edge, bits, ring, cl, nsm, dev_smem_optin, &sh);
+      if (r != FC_OK) return r;
+      // clusters are placed within one GPC, so fewer clusters of 8 are
+      // resident than SMs / 8 (15 on GB300's 152 SMs): an automatic cluster
+      // is halved until every tree of the launch is in flight at once
+      // (measured on GB300, R-MAT n = 2^22, 16 trees: 9.3 ms on clusters of
+      // 4 against 18.4 ms in two waves of clusters of 8)
+      while (g->cluster == 0 && g->bitmap_mode == 0 && cl > 1 && sh.slots < total) {
+        cl /= 2;
+        bits = auto_bits(cl);
+        sh = Shape();
+        r = choose_shape(g, nmax, total, use_smem, edge, bits, ring, cl, nsm, dev_smem_optin, &sh);
+        if (r != FC_OK) return r;
+      }
     } else {
       const fc_status r = choose_shape(g, nmax, total, use_smem, edge, bits, ring, cl, nsm, dev_smem_optin, &sh);
       if (r != FC_OK) return r;
-      std::copy(key, key + 10, g->shape_key);
-      g->shape_val[0] = sh.W;
-      g->shape_val[1] = sh.regs;
-      g->shape_val[2] = sh.per_sm;
-      g->shape_val[3] = sh.slots;
-      g->shape_cached = true;
     }
+    std::copy(key, key + 12, g->shape_key);
+    g->shape_val[0] = sh.W;
+    g->shape_val[1] = sh.regs;
+    g->shape_val[2] = sh.per_sm;
+    g->shape_val[3] = sh.slots;
+    g->shape_val[4] = cl;
+    g->shape_val[5] = bits;
+    g->shape_cached = true;
   }
+  const bool sbits = bits == 1;
   const int W = sh.W;
   const size_t shb = edge ? wilson_edge_smem(W, nmax, bits, g->weighted, cl) : smem_bytes(W, nmax, use_smem);
   // trees in flight (each on cl CTAs)

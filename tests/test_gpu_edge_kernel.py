@@ -211,3 +211,16 @@ def test_automatic_cluster_for_few_trees():
     _check(G, g, [1.0], seed=3, tau=300)  # enough trees: one CTA each
     assert G.last_cluster() == 1
     G.close()
+
+
+def test_automatic_cluster_keeps_every_tree_in_flight():
+    """16 trees: 16 x 8 CTAs fit the SM count, but clusters are placed within a
+    GPC and fewer clusters of 8 are resident; the automatic cluster is halved
+    until the whole launch runs in one wave.  Trees still equal the oracle's."""
+    g = synth.barabasi_albert(50_000, 4, 2)
+    G = fc.Graph.from_csr(g, [1.0])
+    _check(G, g, [1.0], seed=5, tau=16)
+    cl = G.last_cluster()
+    assert cl in (4, 8), cl
+    assert G.last_shape()["ctas"] == 16 * cl, (G.last_shape(), cl)
+    G.close()
