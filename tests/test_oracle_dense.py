@@ -176,6 +176,74 @@ def test_eta_bound_gives_kappa_eps_over_3():
     assert math.isclose(eta * math.sqrt(alpha * (c + 2) * vol) * 2, kappa * eps / 3, rel_tol=1e-12)
 
 
+def _max_over_sign_vectors(M):
+    """max of x^T M x over x in {-1, +1}^n (brute force; x and -x agree)."""
+    n = M.shape[0]
+    best = -np.inf
+    for bits in range(2 ** (n - 1)):
+        x = np.array([1.0 if (bits >> i) & 1 else -1.0 for i in range(n - 1)] + [1.0])
+        best = max(best, float(x @ M @ x))
+    return best
+
+
+def _bipartite_weighted_grid():
+    rng = np.random.default_rng(5)
+    u, v = [], []
+    for r in range(3):
+        for c in range(4):
+            i = 4 * r + c
+            if c < 3:
+                u.append(i), v.append(i + 1)
+            if r < 2:
+                u.append(i), v.append(i + 4)
+    return synth.from_edges(12, u, v, rng.uniform(0.5, 3.0, len(u)))
+
+
+@pytest.mark.parametrize("name,g,bipartite", [
+    ("cycle8", synth.cycle(8), True),
+    ("path7", synth.path(7), True),
+    ("grid3x4_weighted", _bipartite_weighted_grid(), True),
+    ("cycle9", synth.cycle(9), False),
+    ("complete6", synth.complete(6), False),
+    ("er11", synth.random_small(11, 0.4, 3, True), False),
+])
+@pytest.mark.parametrize("alpha", [0.3, 2.0])
+def test_eta_against_the_tight_norm_equivalence(name, g, bipartite, alpha):
+    """Proof of Thm. 1: with L' = alpha L + I and c = n / (alpha vol), every x has
+    ||x||_inf <= ||x||_{L'} <= sqrt(alpha (c + 2) vol) ||x||_inf, and eta makes the
+    solver's max-norm error eta sqrt(alpha (c + 2) vol) ||x||_inf <= kappa eps / 3 for
+    ||x||_inf <= 2.  The upper constant is checked here as what it is, the maximum
+    of x^T L' x over the cube (a convex function peaks at a vertex, so at a sign
+    vector), found by brute force: equal to alpha (c + 2) vol on bipartite graphs
+    (x the 2-colouring: every edge term is 4 w), below it otherwise; the lower one
+    as the smallest eigenvalue of L' (= 1).  eta is then pinned by that maximum,
+    not by its own formula."""
+    n = g.n
+    Lp = alpha * dense.laplacian(g) + np.eye(n)
+    vol = float(dense.laplacian(g).trace())  # sum of weighted degrees
+    top = _max_over_sign_vectors(Lp)
+    c = n / (alpha * vol)
+    if bipartite:
+        assert math.isclose(top, alpha * (c + 2) * vol, rel_tol=1e-12)
+    else:
+        assert top < alpha * (c + 2) * vol * (1 - 1e-9)
+    assert math.isclose(float(np.linalg.eigvalsh(Lp)[0]), 1.0, rel_tol=0, abs_tol=1e-12)
+    eps, kappa = 0.1, 0.5
+    eta = dense.eta_for(eps, kappa, alpha, n, vol)
+    worst = eta * math.sqrt(top) * 2.0  # ||x||_inf = 2, the proof's bound on x
+    if bipartite:
+        assert math.isclose(worst, kappa * eps / 3, rel_tol=1e-12)
+    else:
+        assert worst < kappa * eps / 3
+    # a relative L'-norm error of eta, in the direction that maximises the max
+    # norm, stays within that budget (max over unit-L'-norm e of |e_i| is
+    # sqrt((L'^-1)_ii), Cauchy-Schwarz)
+    x = dense.pivot_solution(g, alpha)[:n]
+    x_norm = math.sqrt(float(x @ Lp @ x))
+    e_inf = eta * x_norm * math.sqrt(float(np.max(np.diag(np.linalg.inv(Lp)))))
+    assert e_inf <= kappa * eps / 3 * float(np.max(np.abs(x))) / 2.0 + 1e-15
+
+
 def test_top_k_ties_and_order():
     d = np.array([0.3, 0.1, 0.2, 0.1, 0.5])
     assert dense.top_k(d, 3).tolist() == [1, 3, 2]
