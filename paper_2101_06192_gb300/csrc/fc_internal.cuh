@@ -210,10 +210,14 @@ struct fc_graph {
   int32_t last_cluster = 0;    // CTAs per tree of the last launch
   int32_t last_kernel = 0;     // kernel of the last launch (1 or 2)
   int32_t last_W = 0, last_regs = 0, last_grid = 0;  // shape of the last launch
-  // the launch-shape search's last inputs and result (reused while they repeat)
-  int64_t shape_key[12] = {};
-  int64_t shape_val[6] = {};
-  bool shape_cached = false;
+  // results of the launch-shape search for the last SHAPE_SLOTS distinct inputs
+  // (launches of a few alternating tree counts, such as a run that samples up
+  // to increasing checkpoints, reuse them), replaced round-robin
+  static constexpr int SHAPE_SLOTS = 8;
+  int64_t shape_key[SHAPE_SLOTS][12] = {};
+  int64_t shape_val[SHAPE_SLOTS][6] = {};
+  bool shape_used[SHAPE_SLOTS] = {};
+  int32_t shape_next = 0;
   // scratch owned by the graph
   void* ws = nullptr;          // sampler per-tree state
   size_t ws_bytes = 0;

@@ -701,19 +701,23 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   // road-like grid (mean degree 3.7, pops 44% of departures); the prefix
   // buffer stays 6% faster on BA m = 8 (pops 5%)
   const bool ring = edge && (g->pops_mode == 2 || (g->pops_mode == 0 && g->nnz < 8 * (int64_t)g->n));
-  // The search queries the occupancy of up to 32 candidate shapes (a host cost
-  // of the order of a millisecond): its result is kept for repeated launches
-  // with the same inputs.
+  // The search queries the occupancy of up to 32 candidate shapes per cluster
+  // size (a host cost of milliseconds, which a launch waits for): its results
+  // are kept for launches with the same inputs.
   Shape sh;
   const int64_t key[12] = {nmax,      total,     use_smem, edge,        g->bitmap_mode, ring,
                            g->cluster, g->walkers, g->regs, g->weighted, g->root >= 0,  g->smem_mode};
-  if (g->shape_cached && std::equal(key, key + 12, g->shape_key)) {
-    sh.W = (int)g->shape_val[0];
-    sh.regs = (int)g->shape_val[1];
-    sh.per_sm = (int)g->shape_val[2];
-    sh.slots = g->shape_val[3];
-    cl = (int)g->shape_val[4];
-    bits = (int)g->shape_val[5];
+  int hit_slot = -1;
+  for (int q = 0; q < fc_graph::SHAPE_SLOTS; ++q)
+    if (g->shape_used[q] && std::equal(key, key + 12, g->shape_key[q])) hit_slot = q;
+  if (hit_slot >= 0) {
+    const int64_t* v = g->shape_val[hit_slot];
+    sh.W = (int)v[0];
+    sh.regs = (int)v[1];
+    sh.per_sm = (int)v[2];
+    sh.slots = v[3];
+    cl = (int)v[4];
+    bits = (int)v[5];
   } else {
     if (edge) {
       const int wmin_e = g->walkers > 0 ? g->walkers : 32;
@@ -755,14 +759,12 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
       const fc_status r = choose_shape(g, nmax, total, use_smem, edge, bits, ring, cl, nsm, dev_smem_optin, &sh);
       if (r != FC_OK) return r;
     }
-    std::copy(key, key + 12, g->shape_key);
-    g->shape_val[0] = sh.W;
-    g->shape_val[1] = sh.regs;
-    g->shape_val[2] = sh.per_sm;
-    g->shape_val[3] = sh.slots;
-    g->shape_val[4] = cl;
-    g->shape_val[5] = bits;
-    g->shape_cached = true;
+    const int q = g->shape_next;
+    g->shape_next = (q + 1) % fc_graph::SHAPE_SLOTS;
+    std::copy(key, key + 12, g->shape_key[q]);
+    const int64_t v[6] = {sh.W, sh.regs, sh.per_sm, sh.slots, cl, bits};
+    std::copy(v, v + 6, g->shape_val[q]);
+    g->shape_used[q] = true;
   }
   const bool sbits = bits == 1;
   const int W = sh.W;
