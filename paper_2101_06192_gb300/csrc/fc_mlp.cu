@@ -36,38 +36,68 @@ __device__ __forceinline__ double p_of(const uint4& ri) {
   return (double)T * 0x1.0p-53;
 }
 
-// Sum over neighbours of their degree.  Each thread takes a run of FT_RUN
-// CSR entries (finding its first row by binary search) and adds the
-// neighbours' degrees into its current row's total, flushing with an integer
-// atomic whenever the row changes: a hub row is shared by many threads
-// instead of being walked by one group (R-MAT hubs have 10^5 entries).  The
-// totals are integers, so the order of the additions does not matter.
-constexpr int FT_RUN = 64;
+// Sum over neighbours of their degree, s2[v] = sum over w in N(v) of deg(w).
+// A warp takes chunks of NDS_CHUNK consecutive CSR entries and walks each in
+// steps of 32: lane i reads entry e0 + i (coalesced column indices), finds its
+// row among the 32 row ends that follow the step's first row (a binary search
+// over the warp's registers; an entry beyond them, after empty rows, searches
+// the row pointers itself), and the lanes of one row add their neighbours'
+// degrees with a segmented warp sum whose last lane adds the total to s2 (one
+// atomic per row segment, so a hub row is shared by many warps).  The totals
+// are integers: any order of the additions gives the same result.
+constexpr int NDS_CHUNK = 32 * 32;
+constexpr unsigned NDS_FULL = 0xffffffffu;
+__device__ __forceinline__ int32_t row_of_entry(const int64_t* __restrict__ rowptr, int32_t lo, int32_t hi,
+                                                int64_t e) {
+  // the row v in [lo, hi] with rowptr[v] <= e < rowptr[v + 1] (the last such v: rows may be empty)
+  while (lo < hi) {
+    const int32_t mid = lo + (hi - lo + 1) / 2;
+    if (rowptr[mid] <= e) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 __global__ void k_nbr_deg_sum(int32_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
                               const int32_t* __restrict__ colidx, const int32_t* __restrict__ deg,
                               unsigned long long* __restrict__ s2) {
-  const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * FT_RUN;
-  if (e0 >= nnz) return;
-  const int64_t e1 = e0 + FT_RUN < nnz ? e0 + FT_RUN : nnz;
-  int32_t lo = 0, hi = n - 1;  // the row v with rowptr[v] <= e0 < rowptr[v + 1]
-  while (lo < hi) {
-    const int32_t mid = lo + (hi - lo + 1) / 2;
-    if (rowptr[mid] <= e0) lo = mid;
-    else hi = mid - 1;
-  }
-  int32_t v = lo;
-  int64_t end = rowptr[v + 1];
-  unsigned long long acc = 0;
-  for (int64_t e = e0; e < e1; ++e) {
-    while (e >= end) {
-      if (acc) atomicAdd(&s2[v], acc);
-      acc = 0;
-      ++v;
-      end = rowptr[v + 1];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c0 = warp * NDS_CHUNK; c0 < nnz; c0 += nwarps * NDS_CHUNK) {
+    const int64_t c1 = c0 + NDS_CHUNK < nnz ? c0 + NDS_CHUNK : nnz;
+    int32_t r = row_of_entry(rowptr, 0, n - 1, c0);  // row of the step's first entry (warp-uniform)
+    for (int64_t e0 = c0; e0 < c1; e0 += 32) {
+      const int64_t e = e0 + lane;
+      const bool ok = e < c1;
+      unsigned long long val = ok ? (unsigned long long)deg[colidx[e]] : 0ull;
+      // end of row r + k in lane k; the count of ends <= e is the lane's row offset
+      const int32_t rk = r + 1 + lane;
+      const int64_t endk = rk <= n ? rowptr[rk] : INT64_MAX;
+      int32_t row = r;
+      if (__shfl_sync(NDS_FULL, endk, 0) <= e0 + 31) {  // the step crosses a row end
+        int32_t cnt = 0;
+#pragma unroll
+        for (int b = 16; b >= 1; b >>= 1) {
+          const int64_t probe = __shfl_sync(NDS_FULL, endk, cnt + b - 1);
+          if (probe <= e) cnt += b;
+        }
+        if (__shfl_sync(NDS_FULL, endk, cnt) <= e) ++cnt;
+        row = cnt < 32 ? r + cnt : row_of_entry(rowptr, r + 32, n - 1, e);
+      }
+      // segmented inclusive sum over lanes of the same row (rows do not decrease with the lane)
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long ov = __shfl_up_sync(NDS_FULL, val, d);
+        const int32_t orow = __shfl_up_sync(NDS_FULL, row, d);
+        if (lane >= d && orow == row) val += ov;
+      }
+      const int32_t nrow = __shfl_down_sync(NDS_FULL, row, 1);
+      const bool nok = __shfl_down_sync(NDS_FULL, ok ? 1 : 0, 1) != 0;
+      if (ok && val != 0ull && (lane == 31 || !nok || nrow != row)) atomicAdd(&s2[row], val);
+      r = __shfl_sync(NDS_FULL, row, 31);
     }
-    acc += (unsigned long long)deg[colidx[e]];
   }
-  if (acc) atomicAdd(&s2[v], acc);
 }
 
 __global__ void k_features(int32_t n, double alpha_s, const double* __restrict__ alpha_v,
@@ -256,9 +286,10 @@ extern "C" fc_status fc_vertex_features(fc_graph* g, int32_t alpha_idx, float* X
   unsigned long long* s2 = nullptr;
   FC_CK(cudaMallocAsync((void**)&s2, (size_t)g->n * sizeof(unsigned long long), st));
   FC_CK(cudaMemsetAsync(s2, 0, (size_t)g->n * sizeof(unsigned long long), st));
-  const int64_t runs = (g->nnz + FT_RUN - 1) / FT_RUN;
-  if (runs > 0) {
-    k_nbr_deg_sum<<<(unsigned)((runs + 255) / 256), 256, 0, st>>>(g->n, g->nnz, g->rowptr, g->colidx, g->deg, s2);
+  const int64_t chunks = (g->nnz + NDS_CHUNK - 1) / NDS_CHUNK;  // one warp each, 8 warps per block
+  if (chunks > 0) {
+    const unsigned nb = (unsigned)std::min<int64_t>((chunks + 7) / 8, 152 * 8);
+    k_nbr_deg_sum<<<nb, 256, 0, st>>>(g->n, g->nnz, g->rowptr, g->colidx, g->deg, s2);
     FC_LAUNCHED();
   }
   const unsigned fb = (unsigned)std::min<int64_t>(((int64_t)g->n + 255) / 256, 152 * 16);

@@ -31,9 +31,17 @@ def _from_oracle(g):
     return np.concatenate([g["W1"].ravel(), g["b1"], g["w2"], g["b2"]])
 
 
-@pytest.mark.parametrize("weighted,alpha", [(False, 1.0), (True, 0.4)])
-def test_features_match_oracle(weighted, alpha):
-    g = synth.barabasi_albert(3000, 3, 2, weighted=weighted)
+@pytest.mark.parametrize("kind,weighted,alpha", [("ba", False, 1.0), ("ba", True, 0.4), ("rmat", False, 1.0),
+                                                  ("star", False, 2.0), ("sparse", True, 0.7)])
+def test_features_match_oracle(kind, weighted, alpha):
+    """Features against the oracle; the neighbour-degree sums walk the CSR in
+    warp steps of 32 entries, so the graphs include hub rows spanning many
+    steps (R-MAT, a star of 5000 leaves) and runs of empty rows (isolated
+    vertices of R-MAT and of a sparse random graph)."""
+    g = {"ba": lambda: synth.barabasi_albert(3000, 3, 2, weighted=weighted),
+         "rmat": lambda: synth.rmat(13, 8, 3),
+         "star": lambda: synth.star(5001),
+         "sparse": lambda: synth.random_small(3000, 0.0004, 6, weighted)}[kind]()
     G = fc.Graph.from_csr(g, [alpha])
     X = G.features().cpu().numpy()
     np.testing.assert_allclose(X, mlp.features(g, alpha), rtol=2e-6, atol=2e-6)
