@@ -389,11 +389,9 @@ fc_status fc_forest_farness(fc_graph* g, int32_t alpha_idx, const uint32_t* R, c
  *   - n must be <= 4194304 (2^22); larger graphs get FC_EINVAL.
  *   - The graph's device must be the current device; batches of graphs
  *     (fc_build_batch) are rejected with FC_EINVAL.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) and caches it for the life of the process; make
- *     that first call before any stream capture begins.  The cache assumes
- *     the device's primary context is not reset (cudaDeviceReset) while the
- *     library is loaded.
+ *   - Each call looks up the array's address on the current device
+ *     (cudaGetSymbolAddress, a host-side lookup; nothing is cached) and only
+ *     launches kernels, so the call can be captured into a CUDA graph.
  *   - All calls share the one array: calls whose work overlaps on the GPU
  *     (different streams, or several host threads) race and give wrong
  *     results.  Serialise them (one stream, or events).

@@ -2,7 +2,6 @@
 // (Eq. 3), forest closeness (Def. 2), exact u*-selection probabilities, and
 // the top-k ranking (Sec. 6.1).
 #include <algorithm>
-#include <mutex>
 #include <vector>
 
 #include "fc_internal.cuh"
@@ -348,29 +347,19 @@ extern "C" fc_status fc_top_k(const double* diag, int32_t n, int32_t k, int32_t*
 // Allocation-free variant of fc_forest_farness.  The per-block partial sums
 // and the trace live in a file-scope device array instead of stream-ordered
 // pool memory.  Host code must not pass the array's name to a kernel (on the
-// host it is only a stand-in symbol), so its device address is looked up once
-// per device with cudaGetSymbolAddress and cached.
+// host it is only a stand-in symbol), so its device address on the current
+// device is looked up with cudaGetSymbolAddress at every call (a host-side
+// lookup; nothing cached, so a reset device or a reloaded module is no issue).
 // ---------------------------------------------------------------------------
 namespace fcx {
 constexpr int32_t NOALLOC_MAX_N = 1 << 22;
 constexpr int64_t NOALLOC_MAX_BLOCKS = (NOALLOC_MAX_N + RED_THREADS - 1) / RED_THREADS;
 static __device__ __align__(256) double g_noalloc_partials[NOALLOC_MAX_BLOCKS + 1];
 
-static std::mutex g_noalloc_mu;
-static double* g_noalloc_ptr[64] = {};
-
-static fc_status noalloc_scratch(int device, double** out) {
-  if (device < 0 || device >= 64) {
-    set_error("fc_forest_farness_noalloc: device index out of range");
-    return FC_EINVAL;
-  }
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (g_noalloc_ptr[device] == nullptr) {
-    void* p = nullptr;
-    FC_CK(cudaGetSymbolAddress(&p, g_noalloc_partials));
-    g_noalloc_ptr[device] = (double*)p;
-  }
-  *out = g_noalloc_ptr[device];
+static fc_status noalloc_scratch(double** out) {
+  void* p = nullptr;
+  FC_CK(cudaGetSymbolAddress(&p, g_noalloc_partials));
+  *out = (double*)p;
   return FC_OK;
 }
 }  // namespace fcx
@@ -400,7 +389,7 @@ extern "C" fc_status fc_forest_farness_noalloc(fc_graph* g, int32_t alpha_idx, c
     return FC_EINVAL;
   }
   double* partial = nullptr;
-  const fc_status s = noalloc_scratch(dev, &partial);
+  const fc_status s = noalloc_scratch(&partial);
   if (s != FC_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   const int32_t n = g->n;

@@ -63,6 +63,39 @@ def test_noalloc_matches_pool_version_on_two_calls_in_a_row():
     G.close()
 
 
+def test_noalloc_inside_a_captured_cuda_graph():
+    """The call launches kernels only (no allocation, no host read), so it can be
+    captured: a CUDA graph holding fc_forest_farness_noalloc, replayed after new
+    counts are written into its input buffer, gives the pool version's results
+    at each replay."""
+    L = fc.lib()
+    g = synth.barabasi_albert(20_000, 3, 6)
+    G = fc.Graph.from_csr(g, [1.0])
+    tau = 64
+    n = g.n
+    G.sample(1, tau)  # warm-up outside the capture (launch shape, scratch)
+    R = torch.zeros(n, dtype=torch.int32, device="cuda")
+    outs = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in range(3)]
+    cg = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(cg, stream=s):
+            stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+            rc = L.fc_forest_farness_noalloc(G._h, 0, _p(R), None, None, None, tau, _p(outs[0]), _p(outs[1]),
+                                             _p(outs[2]), stream)
+            assert rc == fc.FC_OK
+    torch.cuda.current_stream().wait_stream(s)
+    for sd in (21, 22):
+        R.copy_(G.sample(sd, tau, with_C=False)["R"])
+        cg.replay()
+        torch.cuda.synchronize()
+        ref = _run(L.fc_forest_farness, G, R, None, None, None, tau)
+        for a, b in zip([o.cpu().numpy() for o in outs], ref):
+            np.testing.assert_allclose(a, b, rtol=1e-9, atol=0)
+    G.close()
+
+
 def test_noalloc_rejects_graphs_beyond_its_capacity():
     L = fc.lib()
     n = (1 << 22) + 1
