@@ -527,7 +527,7 @@ static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool 
     if (edge && regs < 48) regs = 48;
     const WilsonFn fn = edge ? wilson_edge_fn(bits, g->weighted, ring, cl > 1, regs) : wilson_fn(smem, regs);
     for (int W = (g->walkers > 0 ? g->walkers : wcap); W >= 32; W -= 32) {
-      const size_t shb = edge ? wilson_edge_smem(W, n, bits, g->weighted, cl) : smem_bytes(W, n, smem);
+      const size_t shb = edge ? wilson_edge_smem(W, n, bits, g->weighted, cl, ring) : smem_bytes(W, n, smem);
       if (shb + 64 > (size_t)smem_optin) {
         if (g->walkers > 0) break;
         continue;
@@ -537,7 +537,7 @@ static fc_status choose_shape(const fc_graph* g, int32_t n, int64_t total, bool 
       // 20% slower than one just below it (the L1 left for register spills
       // shrinks); automatic shapes stay below the step when they can
       if (sbits && g->walkers == 0 && shb > SBITS_CARVEOUT &&
-          wilson_edge_smem(32, n, 1, g->weighted, cl) <= SBITS_CARVEOUT)
+          wilson_edge_smem(32, n, 1, g->weighted, cl, ring) <= SBITS_CARVEOUT)
         continue;
       if (edge) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
       if (smem) FC_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
@@ -722,7 +722,7 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
     if (edge) {
       const int wmin_e = g->walkers > 0 ? g->walkers : 32;
       auto fits_c = [&](int c) {
-        return wilson_edge_smem(wmin_e, nmax, 1, g->weighted, c) + 64 <= (size_t)dev_smem_optin;
+        return wilson_edge_smem(wmin_e, nmax, 1, g->weighted, c, ring) + 64 <= (size_t)dev_smem_optin;
       };
       // rooted graphs: state flags, so that several small CTAs share an SM
       auto auto_bits = [&](int c) { return (g->root < 0 && g->smem_mode != 1 && fits_c(c)) ? 1 : 0; };
@@ -768,7 +768,7 @@ static fc_status sample_impl(fc_graph* g, uint64_t seed, int64_t tau, int64_t tr
   }
   const bool sbits = bits == 1;
   const int W = sh.W;
-  const size_t shb = edge ? wilson_edge_smem(W, nmax, bits, g->weighted, cl) : smem_bytes(W, nmax, use_smem);
+  const size_t shb = edge ? wilson_edge_smem(W, nmax, bits, g->weighted, cl, ring) : smem_bytes(W, nmax, use_smem);
   // trees in flight (each on cl CTAs)
   int64_t grid = std::min<int64_t>(total, std::max<int64_t>(1, sh.slots));
   if (g->max_trees > 0) grid = std::min<int64_t>(grid, g->max_trees);

@@ -151,6 +151,6 @@ typedef void (*WilsonFn)(WParams);
 // 1), for a register cap of 48 or 64 (lower caps map to 48), and its dynamic
 // shared memory per CTA in a cluster of C CTAs.
 WilsonFn wilson_edge_fn(int bits, bool wgt, bool ring, bool cl, int regs, bool roots = false);
-size_t wilson_edge_smem(int W, int32_t n, int bits, bool wgt, int C);  // bits: 0 flags, 1 shared bitmap, 2 global
+size_t wilson_edge_smem(int W, int32_t n, int bits, bool wgt, int C, bool ring);  // bits: 0 flags, 1 shared bitmap, 2 global
 
 }  // namespace fcx

@@ -45,6 +45,9 @@ enum { E_IDLE = 0, E_START, E_THR, E_CLAIM, E_CLAIM2, E_TOP, E_POP, E_RETRACE, E
 constexpr int EW_BITS = 13;
 constexpr uint32_t EW_MASK = (1u << EW_BITS) - 1u;
 constexpr uint32_t GEN_LIMIT = (1u << (39 - EW_BITS)) - 1u;
+// parked restarts (RINGP): no parked path / parked, a window start to be taken first
+constexpr uint32_t NO_PARK = 0xffffffffu;
+constexpr uint32_t PARK_FRESH = 0x80000000u;
 
 __device__ __forceinline__ unsigned long long rd_pack(int32_t root, int32_t depth) {
   return (unsigned long long)(uint32_t)root | ((unsigned long long)(uint32_t)depth << 32);
@@ -123,8 +126,15 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
   uint4* sh_wri = (uint4*)(smem_raw + (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15));
   uint4* sh_wst = sh_wri + W;  // BITS = 0 only
   uint32_t* sh_wv = (uint32_t*)(sh_wri + (BITS == 0 ? 2 : 1) * W);
+  // RINGP: a path given up under wait-die, parked while its walker takes other
+  // start vertices: [W] owner tag of the vertex it met, [W] its start vertex
+  // (NO_PARK: none), [W] the vertex it met (sh_wv + W is 16-byte aligned: W is
+  // a multiple of 32)
+  unsigned long long* sh_ptag = (unsigned long long*)(sh_wv + W);
+  uint32_t* sh_ps = (uint32_t*)(sh_ptag + W);
+  uint32_t* sh_px = sh_ps + W;
   // [2][W][12] slot-threshold high words of each walker's current / next vertex (WGT)
-  uint32_t* sh_thr = (uint32_t*)(((uintptr_t)(sh_wv + W) + 15) & ~(uintptr_t)15);
+  uint32_t* sh_thr = (uint32_t*)(((uintptr_t)(RINGP ? (void*)(sh_px + W) : (void*)(sh_wv + W)) + 15) & ~(uintptr_t)15);
   // in-tree bitmap [ceil(n / 32)] (BITS = 1: shared memory, 2: this CTA's global region)
   volatile uint32_t* sh_bits = BITS == 1 ? (volatile uint32_t*)(sh_thr + (WGT ? 2 * 12 * W : 0))
                                          : (volatile uint32_t*)(p.gbits + (size_t)blockIdx.x * p.words);
@@ -221,6 +231,7 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
       for (int32_t q = (int32_t)wid; q < ((nl + 31) >> 5); q += (int32_t)WT) sh_bits[q] = 0u;
     first_tree = false;
     sh_gen[me] = 1u;
+    if (RINGP) sh_ps[me] = NO_PARK;
     if (me == 0) {
       sh_next = 0;
       sh_tsize = 0;
@@ -275,7 +286,23 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
 
       // ---- start vertices: hand out the window; a dry window is refilled by
       // copies issued with this iteration's memory operations ----
-      const bool need = !fin && mode == E_IDLE;
+      bool need = !fin && mode == E_IDLE;
+      // RINGP: a parked path is looked at again (E_WAIT: has the walker it met
+      // moved on?) once its walker has taken one other start vertex, or when no
+      // other start vertex is left
+      uint32_t pv = NO_PARK;
+      if (RINGP && need) {
+        pv = sh_ps[me];
+        if (pv != NO_PARK && !(pv & PARK_FRESH)) {
+          s = (int32_t)pv;
+          x = (int32_t)sh_px[me];
+          wtag = sh_ptag[me];
+          mode = E_WAIT;
+          need = false;
+        } else if (pv != NO_PARK) {
+          sh_ps[me] = pv & ~PARK_FRESH;  // a window start first
+        }
+      }
       const unsigned want = __ballot_sync(FULL, need);
       bool refill = false;  // warp-uniform
       if (want) {
@@ -294,7 +321,14 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
             rbase = 0;
             mode = WGT ? E_THR : E_CLAIM;
           } else if (wdone) {
-            mode = E_DONE;
+            if (RINGP && pv != NO_PARK) {  // nothing else left: wait for the parked path
+              s = (int32_t)(pv & ~PARK_FRESH);
+              x = (int32_t)sh_px[me];
+              wtag = sh_ptag[me];
+              mode = E_WAIT;
+            } else {
+              mode = E_DONE;
+            }
           }
         }
         whead = nw >= na ? wcnt : whead + nw;
@@ -567,6 +601,12 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
                 c = s;
                 rh = rbase;  // vertices left to free
                 mode = E_RELEASE;
+              } else if (!wdone && sh_ps[me] == NO_PARK) {
+                // park the path and take other start vertices meanwhile
+                sh_ps[me] = (uint32_t)s | PARK_FRESH;
+                sh_px[me] = (uint32_t)x;
+                sh_ptag[me] = wtag;
+                mode = E_IDLE;
               } else {
                 mode = E_WAIT;
               }
@@ -670,14 +710,32 @@ __global__ void __launch_bounds__(1024) __maxnreg__(MAXREG) k_wilson_edge(WParam
           }
           case E_RELEASE: {
             if (nxt_read(nc)) ADD_ST(c, 0ull - (mytag << K_BITS));
-            if (RINGP ? --rh == 0 : c == rh) mode = E_WAIT;
-            else c = (int32_t)nc;
+            if (RINGP ? --rh == 0 : c == rh) {
+              if (RINGP && !wdone && sh_ps[me] == NO_PARK) {  // park (see the release above)
+                sh_ps[me] = (uint32_t)s | PARK_FRESH;
+                sh_px[me] = (uint32_t)x;
+                sh_ptag[me] = wtag;
+                mode = E_IDLE;
+              } else {
+                mode = E_WAIT;
+              }
+            } else {
+              c = (int32_t)nc;
+            }
             break;
           }
           case E_WAIT: {
             CNT(CNT_WAIT);
             const uint32_t ww = (uint32_t)(wtag & EW_MASK);
-            if ((old >> K_BITS) == wtag && GEN_OF(ww) == (uint32_t)(wtag >> EW_BITS)) break;
+            const bool parked = RINGP && sh_ps[me] == (uint32_t)s;  // the wait of a parked path
+            if ((old >> K_BITS) == wtag && GEN_OF(ww) == (uint32_t)(wtag >> EW_BITS)) {
+              if (parked && !wdone) {  // still in the way: other start vertices first
+                sh_ps[me] = (uint32_t)s | PARK_FRESH;
+                mode = E_IDLE;
+              }
+              break;
+            }
+            if (parked) sh_ps[me] = NO_PARK;
             x = s;
             mode = E_START;
             break;
@@ -882,9 +940,11 @@ WilsonFn wilson_edge_fn(int bits, bool wgt, bool ring, bool cl, int regs, bool r
   return edge_fn_wgt<0, false>(wgt, ring, regs);
 }
 
-size_t wilson_edge_smem(int W, int32_t n, int bits, bool wgt, int C) {
-  // the start window keeps state records only when membership is a state flag
-  const size_t base = (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15) + (size_t)W * (16 + (bits == 0 ? 16 : 0) + 4);
+size_t wilson_edge_smem(int W, int32_t n, int bits, bool wgt, int C, bool ring) {
+  // the start window keeps state records only when membership is a state flag;
+  // ring variants keep a parked path per walker
+  const size_t base = (((size_t)W * 4 * (1 + PB) + 15) & ~(size_t)15) +
+                      (size_t)W * (16 + (bits == 0 ? 16 : 0) + 4 + (ring ? 16 : 0));
   const size_t words = ((size_t)n + 31) / 32;
   return ((base + 15) & ~(size_t)15) + (wgt ? (size_t)W * 2 * 12 * 4 : 0) +
          (bits == 1 ? ((words + (size_t)C - 1) / (size_t)C) * 4 : 0);
